@@ -1,0 +1,326 @@
+"""FP64 oracle for the RK4 time step of the extended dNLSE (PHOENIX).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``): never imported by the
+product path.
+
+What it computes, in the paper's order and notation:
+
+* Eq. (PULSE_psi), Sec. V, with coherent drive E = 0 and the noise dW applied
+  separately after each step (``noise``):
+      dpsi_c/dt = -(i/hbar) [ -(hbar^2/2m) Lap psi_c + (V + g|psi_c|^2
+                  + g_x|psi_o|^2 + g_r n_c) psi_c + J_c psi_o ]
+                  + (1/2)(R n_c - gamma_c) psi_c
+  for c in {+} (scalar) or {+, -} (spinor; o is the other component), with
+  J_+ = Delta_LT (d_x - i d_y)^2 and J_- = Delta_LT (d_x + i d_y)^2.
+  Eq. (1) is the case without reservoir and spinor.
+* Eq. (PULSE_res): dn_c/dt = P_c - (gamma_r + R|psi_c|^2) n_c.
+* Laplacian: the 5-point central-difference stencil of Sec. III.B.6
+  (performance-modelling subsection).  (d_x -/+ i d_y)^2 = Dxx - Dyy -/+ 2i Dxy,
+  with 3-point Dxx, Dyy and the 4-corner Dxy (reading: the paper gives no
+  discretisation for the TE-TM term).
+* RK4: Eqs. (rk4_K1)-(rk4_final) applied to the joint state (psi, n); the
+  time derivative f is read as dpsi/dt (the printed "f = -(i/hbar) d_t psi"
+  is garbled; Listing 2 adds g|psi|^2 (-i psi)/hbar and -gamma psi/2 to it).
+* Boundary conditions (Sec. V, symbols paragraph): x and y independently
+  periodic (wrap) or zero (psi = 0 outside the grid).
+
+Arrays: psi (ncomp, ny, nx) complex128, n / P (ncomp, ny, nx) float64,
+V (ny, nx) float64; x is the fastest index, site = j*nx + i.
+"""
+from dataclasses import dataclass, field, replace
+import numpy as np
+
+from . import noise as _noise
+
+HBAR = 0.6582119569  # meV ps (CODATA 2018 value of hbar in these units)
+
+PERIODIC = 0
+ZERO = 1
+
+
+@dataclass
+class Params:
+    nx: int
+    ny: int
+    lx: float                 # um
+    ly: float                 # um
+    bc_x: int = PERIODIC
+    bc_y: int = PERIODIC
+    spinor: bool = False
+    reservoir: bool = False
+    kappa: float = 0.67       # hbar^2/2m, meV um^2
+    g: float = 0.0            # meV um^2
+    g_x: float = 0.0
+    g_r: float = 0.0
+    R: float = 0.0            # ps^-1 um^2
+    gamma_c: float = 0.0      # ps^-1
+    gamma_r: float = 0.0      # ps^-1
+    delta_lt: float = 0.0     # meV um^2
+    dt: float = 0.0           # ps
+    noise_var: float = 0.0    # E|xi|^2 added per site per step
+    seed: int = 0
+    instance: int = 0
+
+    @property
+    def dx(self):
+        return self.lx / self.nx
+
+    @property
+    def dy(self):
+        return self.ly / self.ny
+
+    @property
+    def ncomp(self):
+        return 2 if self.spinor else 1
+
+    def with_(self, **kw):
+        return replace(self, **kw)
+
+
+def shift(a, di, dj, p):
+    """b[..., j, i] = a[..., j+dj, i+di] with the boundary condition of p."""
+    b = a
+    if di:
+        if p.bc_x == PERIODIC:
+            b = np.roll(b, -di, axis=-1)
+        else:
+            c = np.zeros_like(b)
+            if di > 0:
+                c[..., :, :-di] = b[..., :, di:]
+            else:
+                c[..., :, -di:] = b[..., :, :di]
+            b = c
+    if dj:
+        if p.bc_y == PERIODIC:
+            b = np.roll(b, -dj, axis=-2)
+        else:
+            c = np.zeros_like(b)
+            if dj > 0:
+                c[..., :-dj, :] = b[..., dj:, :]
+            else:
+                c[..., -dj:, :] = b[..., :dj, :]
+            b = c
+    return b
+
+
+def d_xx(a, p):
+    return (shift(a, 1, 0, p) + shift(a, -1, 0, p) - 2.0 * a) / p.dx ** 2
+
+
+def d_yy(a, p):
+    return (shift(a, 0, 1, p) + shift(a, 0, -1, p) - 2.0 * a) / p.dy ** 2
+
+
+def laplacian(a, p):
+    """5-point stencil (Sec. III.B.6):
+    [a(i+1,j)+a(i-1,j)-2a(i,j)]/dx^2 + [a(i,j+1)+a(i,j-1)-2a(i,j)]/dy^2."""
+    return d_xx(a, p) + d_yy(a, p)
+
+
+def d_xy(a, p):
+    """[a(i+1,j+1) - a(i+1,j-1) - a(i-1,j+1) + a(i-1,j-1)] / (4 dx dy)."""
+    return (shift(a, 1, 1, p) - shift(a, 1, -1, p) - shift(a, -1, 1, p)
+            + shift(a, -1, -1, p)) / (4.0 * p.dx * p.dy)
+
+
+def tetm(a, sign, p):
+    """(d_x + sign*i d_y)^2 a = Dxx a - Dyy a + sign*2i Dxy a."""
+    return d_xx(a, p) - d_yy(a, p) + sign * 2j * d_xy(a, p)
+
+
+def hamiltonian_apply(psi, n, V, p):
+    """H psi_c of Eq. (PULSE_psi), the bracket multiplied by -(i/hbar)
+    (including the coupling J_c psi_o), per component."""
+    out = np.empty_like(psi)
+    dens = np.abs(psi) ** 2
+    for c in range(p.ncomp):
+        loc = p.g * dens[c]
+        if V is not None:
+            loc = loc + V
+        if p.spinor:
+            loc = loc + p.g_x * dens[1 - c]
+        if p.reservoir:
+            loc = loc + p.g_r * n[c]
+        h = -p.kappa * laplacian(psi[c], p) + loc * psi[c]
+        if p.spinor and p.delta_lt != 0.0:
+            # J_+ = Delta_LT (d_x - i d_y)^2 acts on psi_-;
+            # J_- = Delta_LT (d_x + i d_y)^2 acts on psi_+.
+            sign = -1.0 if c == 0 else 1.0
+            h = h + p.delta_lt * tetm(psi[1 - c], sign, p)
+        out[c] = h
+    return out
+
+
+def rhs(psi, n, P, V, p):
+    """Time derivatives (f_psi, f_n) of Eqs. (PULSE_psi)/(PULSE_res), E = 0,
+    without dW.  f_n is None without a reservoir."""
+    h = hamiltonian_apply(psi, n, V, p)
+    f_psi = -1j / HBAR * h
+    for c in range(p.ncomp):
+        gain = -0.5 * p.gamma_c
+        if p.reservoir:
+            gain = gain + 0.5 * p.R * n[c]
+        f_psi[c] = f_psi[c] + gain * psi[c]
+    f_n = None
+    if p.reservoir:
+        f_n = np.empty_like(n)
+        dens = np.abs(psi) ** 2
+        for c in range(p.ncomp):
+            f_n[c] = P[c] - (p.gamma_r + p.R * dens[c]) * n[c]
+    return f_psi, f_n
+
+
+def rk4_step(psi, n, P, V, p):
+    """One deterministic RK4 step, Eqs. (rk4_K1)-(rk4_final):
+    K1 = f(y), K2 = f(y + dt/2 K1), K3 = f(y + dt/2 K2), K4 = f(y + dt K3),
+    y' = y + (K1 + 2K2 + 2K3 + K4) dt / 6, on y = (psi, n)."""
+    dt = p.dt
+    k1p, k1n = rhs(psi, n, P, V, p)
+    k2p, k2n = rhs(psi + 0.5 * dt * k1p,
+                   None if n is None else n + 0.5 * dt * k1n, P, V, p)
+    k3p, k3n = rhs(psi + 0.5 * dt * k2p,
+                   None if n is None else n + 0.5 * dt * k2n, P, V, p)
+    k4p, k4n = rhs(psi + dt * k3p,
+                   None if n is None else n + dt * k3n, P, V, p)
+    psi_new = psi + (k1p + 2.0 * k2p + 2.0 * k3p + k4p) * dt / 6.0
+    n_new = None
+    if n is not None:
+        n_new = n + (k1n + 2.0 * k2n + 2.0 * k3n + k4n) * dt / 6.0
+    return psi_new, n_new
+
+
+def add_noise(psi, step, p, fp32_state=False):
+    """psi_c += xi_c(seed, step, instance, site) after the deterministic step
+    (reading: operator splitting with fixed variance per step)."""
+    if p.noise_var == 0.0:
+        return psi
+    re, im = _noise.noise_field(p.seed, step, p.instance, p.ncomp, p.ny, p.nx,
+                                p.noise_var)
+    if fp32_state:
+        return (psi.real.astype(np.float32) + re) + 1j * (
+            psi.imag.astype(np.float32) + im)
+    return psi + (re.astype(np.float64) + 1j * im.astype(np.float64))
+
+
+def run(psi, n, P, V, p, nsteps, step0=0):
+    """nsteps RK4 steps (with noise after each) starting at step index step0.
+    Returns (psi, n) in FP64."""
+    psi = np.array(psi, dtype=np.complex128)
+    n = None if n is None else np.array(n, dtype=np.float64)
+    P = None if P is None else np.asarray(P, dtype=np.float64)
+    V = None if V is None else np.asarray(V, dtype=np.float64)
+    if p.reservoir:
+        if n is None:
+            n = np.zeros((p.ncomp, p.ny, p.nx))
+        if P is None:
+            P = np.zeros((p.ncomp, p.ny, p.nx))
+        elif P.shape[0] != p.ncomp:
+            P = np.broadcast_to(P, (p.ncomp, p.ny, p.nx))
+    for k in range(nsteps):
+        psi, n = rk4_step(psi, n, P, V, p)
+        psi = add_noise(psi, step0 + k, p)
+    return psi, n
+
+
+# ---------------------------------------------------------------- reductions
+
+def norm(psi, p):
+    """N = dV sum_c sum_sites |psi_c|^2."""
+    return p.dx * p.dy * float(np.sum(np.abs(psi) ** 2))
+
+
+def energy(psi, n, V, p):
+    """Discrete energy functional whose derivative d E / d psi_c^* is
+    dV * (H psi_c) of ``hamiltonian_apply`` (reservoir treated as a frozen
+    potential g_r n_c):
+    E = dV sum [ sum_c ( Re(psi_c^* (-kappa Lap psi_c)) + (V + g_r n_c)|psi_c|^2
+                 + (g/2)|psi_c|^4 ) + g_x |psi_+|^2 |psi_-|^2
+                 + Re(psi_+^* J_+ psi_- + psi_-^* J_- psi_+) ]."""
+    dens = np.abs(psi) ** 2
+    tot = 0.0
+    for c in range(p.ncomp):
+        kin = np.real(np.conj(psi[c]) * (-p.kappa * laplacian(psi[c], p)))
+        loc = 0.5 * p.g * dens[c] ** 2
+        if V is not None:
+            loc = loc + V * dens[c]
+        if p.reservoir:
+            loc = loc + p.g_r * n[c] * dens[c]
+        tot += float(np.sum(kin + loc))
+    if p.spinor:
+        tot += float(np.sum(p.g_x * dens[0] * dens[1]))
+        if p.delta_lt != 0.0:
+            cross = (np.conj(psi[0]) * p.delta_lt * tetm(psi[1], -1.0, p)
+                     + np.conj(psi[1]) * p.delta_lt * tetm(psi[0], 1.0, p))
+            tot += float(np.sum(np.real(cross)))
+    return p.dx * p.dy * tot
+
+
+def residual(psi, n, P, V, p):
+    """Steady-state residual (reading: a stationary condensate rotates as
+    exp(-i mu t / hbar), so the global phase rotation is removed):
+        K = f_psi(psi, n),  omega* = -Im<psi, K> / ||psi||^2,
+        r_psi = ||K + i omega* psi|| / ||psi||   (ps^-1),
+        r_n   = ||f_n|| / ||n||.
+    <a, b> = sum_c sum_sites conj(a) b.  Returns (r_psi, r_n, omega*)."""
+    K, fn = rhs(psi, n, P, V, p)
+    spp = float(np.sum(np.abs(psi) ** 2))
+    if spp == 0.0:
+        r_psi, omega = 0.0, 0.0
+    else:
+        omega = -float(np.imag(np.sum(np.conj(psi) * K))) / spp
+        r_psi = float(np.sqrt(np.sum(np.abs(K + 1j * omega * psi) ** 2) / spp))
+    r_n = 0.0
+    if p.reservoir:
+        snn = float(np.sum(n ** 2))
+        sff = float(np.sum(fn ** 2))
+        r_n = (float(np.sqrt(sff / snn)) if snn > 0.0
+               else (0.0 if sff == 0.0 else float("inf")))
+    return r_psi, r_n, omega
+
+
+# ------------------------------------------------------------------ stability
+
+def linear_spectral_radius(p):
+    """Largest |eigenvalue| (meV) of the linear Hermitian part
+    -kappa Lap (+ Delta_LT J) on the grid's Fourier modes (brute force).
+    Periodic axes: k = 2 pi m / N; zero axes: Dirichlet modes k = pi m/(N+1)
+    (reading: for TE-TM with zero BC the Dirichlet modes are used as an
+    approximation).  K^2 = (2 - 2 cos k d)/d^2, s = sin(k d)/d; the TE-TM
+    block at k has eigenvalues kappa(Kx^2+Ky^2) +- Delta_LT *
+    sqrt((Kx^2 - Ky^2)^2 + 4 sx^2 sy^2)."""
+    def modes(N, bc):
+        if bc == PERIODIC:
+            return 2.0 * np.pi * np.arange(N) / N
+        return np.pi * np.arange(1, N + 1) / (N + 1)
+    # kx, ky below are the dimensionless phases k*dx, k*dy of each mode
+    kx = modes(p.nx, p.bc_x)[None, :]
+    ky = modes(p.ny, p.bc_y)[:, None]
+    Kx2 = (2.0 - 2.0 * np.cos(kx)) / p.dx ** 2
+    Ky2 = (2.0 - 2.0 * np.cos(ky)) / p.dy ** 2
+    lam = p.kappa * (Kx2 + Ky2)
+    if p.spinor and p.delta_lt != 0.0:
+        sx = np.sin(kx) / p.dx
+        sy = np.sin(ky) / p.dy
+        off = abs(p.delta_lt) * np.sqrt((Kx2 - Ky2) ** 2 + 4.0 * sx ** 2 * sy ** 2)
+        lam = np.maximum(np.abs(lam + off), np.abs(lam - off))
+    return float(np.max(np.abs(lam)))
+
+
+RK4_IMAG_AXIS_LIMIT = 2.0 * np.sqrt(2.0)  # |R(iy)| <= 1 iff |y| <= 2 sqrt 2
+
+
+def stability_dt_max(p):
+    """Largest dt for which RK4 is stable on the linear Hermitian part:
+    dt_max = 2 sqrt(2) hbar / lambda_max (reading: the nonlinear, potential
+    and loss terms are excluded)."""
+    lam = linear_spectral_radius(p)
+    if lam == 0.0:
+        return float("inf")
+    return RK4_IMAG_AXIS_LIMIT * HBAR / lam
+
+
+def pump_threshold(p):
+    """Homogeneous condensation threshold P_thr = gamma_c gamma_r / R from
+    Eq. (PULSE_res) at psi -> 0 (n = P/gamma_r) and Eq. (PULSE_psi) gain
+    R n = gamma_c."""
+    return p.gamma_c * p.gamma_r / p.R

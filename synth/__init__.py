@@ -1,0 +1,203 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module is shared by the tests, the benchmark and the oracle-driven
+checks.  It holds none of the method's arithmetic: only grids, pump and
+initial-state profiles, random draws and parameter tables.  Two derived
+numbers per workload (the time step at half the RK4 stability limit and the
+pump threshold) are read from ``constants.json``, which
+``synth/derive_constants.py`` writes by calling the oracle.
+
+Workloads (sizes and physics as stated for each; the paper's own parameter
+files are not available, so these stand in for them):
+
+* ``conservative_64``  -- scalar Eq. (1) without loss, 64x64, 20 um, periodic,
+  psi0 = 5 exp(-r^2/3^2) + complex normal noise (std 1e-2 per quadrature).
+* ``reservoir_1024``   -- scalar + reservoir, 1024x1024, 100 um, periodic, ring
+  pump of radius 20 um and width 3 um at 1.5 P_thr, psi0 = noise, n0 = 0.
+* ``spinor_2048``      -- TE-TM spinor + reservoir, 2048x2048, 200 um, Gaussian
+  pump of waist 10 um at 1.5 P_thr on both components, per-step noise.
+* ``ensemble``         -- 256 reservoir instances, 64 each at 128^2 .. 1024^2,
+  100 um, ring pumps at U[0.8, 3] P_thr.
+* ``steady_256``       -- 256x256, 128 um, sums of 1-4 Gaussian pumps.
+"""
+import json
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+PERIODIC = 0
+ZERO = 1
+
+# Shared physical parameters of the driven-dissipative workloads
+# (meV um^2 for kappa, g, g_r, delta_lt; ps^-1 um^2 for R; ps^-1 for rates).
+KAPPA = 0.67
+G_C = 6e-3
+G_R = 2 * G_C
+R_GAIN = 0.01
+GAMMA_C = 0.15
+GAMMA_R = 1.5 * GAMMA_C
+
+
+def load_constants():
+    with open(os.path.join(_HERE, "constants.json")) as f:
+        return json.load(f)
+
+
+def coords(n, length):
+    """Cell positions -L/2 + i*L/n (origin at the grid centre)."""
+    return -0.5 * length + np.arange(n) * (length / n)
+
+
+def mesh(nx, ny, lx, ly):
+    x = coords(nx, lx)
+    y = coords(ny, ly)
+    return np.meshgrid(x, y)  # X[j, i], Y[j, i]
+
+
+def gaussian(nx, ny, lx, ly, amp, w, cx=0.0, cy=0.0):
+    X, Y = mesh(nx, ny, lx, ly)
+    return amp * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / w ** 2)
+
+
+def ring(nx, ny, lx, ly, amp, radius, width):
+    X, Y = mesh(nx, ny, lx, ly)
+    r = np.sqrt(X ** 2 + Y ** 2)
+    return amp * np.exp(-((r - radius) ** 2) / width ** 2)
+
+
+def complex_normal(shape, std, seed):
+    """Complex normal field, std per quadrature, numpy PCG64 stream `seed`."""
+    rng = np.random.default_rng(seed)
+    re = rng.normal(0.0, std, shape)
+    im = rng.normal(0.0, std, shape)
+    return re + 1j * im
+
+
+def base_params(nx, ny, lx, ly, **kw):
+    p = dict(nx=nx, ny=ny, lx=lx, ly=ly, bc_x=PERIODIC, bc_y=PERIODIC,
+             spinor=False, reservoir=False, kappa=KAPPA, g=0.0, g_x=0.0,
+             g_r=0.0, R=0.0, gamma_c=0.0, gamma_r=0.0, delta_lt=0.0, dt=0.0,
+             noise_var=0.0, seed=0)
+    p.update(kw)
+    return p
+
+
+def reservoir_physics():
+    return dict(reservoir=True, g=G_C, g_r=G_R, R=R_GAIN, gamma_c=GAMMA_C,
+                gamma_r=GAMMA_R)
+
+
+def conservative_64(seed=1):
+    c = load_constants()["conservative_64"]
+    p = base_params(64, 64, 20.0, 20.0, g=6e-3, dt=c["dt"])
+    psi0 = (gaussian(64, 64, 20.0, 20.0, 5.0, 3.0)
+            + complex_normal((64, 64), 1e-2, seed))[None]
+    return dict(name="conservative_64", params=p, psi0=psi0, n0=None, P=None,
+                V=None, steps=1000)
+
+
+def reservoir_grid(n, length=100.0, pump_factor=1.5, seed=2, dt=None,
+                   const_key=None):
+    """Scalar driven-dissipative GP + reservoir with the ring pump."""
+    c = load_constants()
+    key = const_key or ("reservoir_%d_L%g" % (n, length))
+    if dt is None:
+        dt = c[key]["dt"]
+    pthr = c["pump_threshold"]
+    p = base_params(n, n, length, length, dt=dt, **reservoir_physics())
+    P = ring(n, n, length, length, pump_factor * pthr, 20.0, 3.0)[None]
+    psi0 = complex_normal((1, n, n), 1e-2, seed)
+    n0 = np.zeros((1, n, n))
+    return dict(name="reservoir_%d" % n, params=p, psi0=psi0, n0=n0, P=P,
+                V=None, steps=10000)
+
+
+def reservoir_1024(seed=2):
+    return reservoir_grid(1024, seed=seed, const_key="reservoir_1024_L100")
+
+
+def spinor_grid(n, length=200.0, seed=3, const_key=None):
+    """TE-TM spinor + reservoir, Gaussian pump waist 10 um at 1.5 P_thr."""
+    c = load_constants()
+    key = const_key or ("spinor_%d_L%g" % (n, length))
+    pthr = c["pump_threshold"]
+    p = base_params(n, n, length, length, spinor=True, delta_lt=0.025,
+                    noise_var=1e-3, seed=seed, dt=c[key]["dt"],
+                    **reservoir_physics())
+    P = gaussian(n, n, length, length, 1.5 * pthr, 10.0)[None]
+    psi0 = complex_normal((2, n, n), 1e-2, seed)
+    n0 = np.zeros((2, n, n))
+    return dict(name="spinor_%d" % n, params=p, psi0=psi0, n0=n0, P=P, V=None,
+                steps=20000)
+
+
+def spinor_2048(seed=3):
+    return spinor_grid(2048, const_key="spinor_2048_L200")
+
+
+def ensemble(count_per_size=64, sizes=(128, 256, 512, 1024), seed0=1000):
+    """Uneven-grid ensemble: pump peaks ~ U[0.8, 3] P_thr, seeds seed0+i."""
+    c = load_constants()
+    pthr = c["pump_threshold"]
+    rng = np.random.default_rng(seed0 - 1)
+    out = []
+    i = 0
+    for n in sizes:
+        for _ in range(count_per_size):
+            factor = float(rng.uniform(0.8, 3.0))
+            p = base_params(n, n, 100.0, 100.0,
+                            dt=c["reservoir_%d_L100" % n]["dt"],
+                            **reservoir_physics())
+            P = ring(n, n, 100.0, 100.0, factor * pthr, 20.0, 3.0)[None]
+            psi0 = complex_normal((1, n, n), 1e-2, seed0 + i)
+            out.append(dict(name="ens_%d" % i, params=p, psi0=psi0,
+                            n0=np.zeros((1, n, n)), P=P, V=None, steps=5000,
+                            pump_factor=factor))
+            i += 1
+    return out
+
+
+def random_gaussian_pumps(n=256, length=128.0, count=1, seed=5000):
+    """count pump images, each a sum of 1-4 Gaussians exp(-|r-c|^2/w^2) with
+    w ~ U[3, 15] um, peak ~ U[1, 3] P_thr, centres within L/2 - 2w."""
+    pthr = load_constants()["pump_threshold"]
+    imgs = np.empty((count, n, n))
+    for k in range(count):
+        rng = np.random.default_rng(seed + k)
+        m = int(rng.integers(1, 5))
+        img = np.zeros((n, n))
+        for _ in range(m):
+            w = float(rng.uniform(3.0, 15.0))
+            amp = float(rng.uniform(1.0, 3.0)) * pthr
+            lim = 0.5 * length - 2.0 * w
+            cx, cy = rng.uniform(-lim, lim, size=2)
+            img += gaussian(n, n, length, length, amp, w, cx, cy)
+        imgs[k] = img
+    return imgs
+
+
+def steady_256(seed=5000):
+    c = load_constants()["steady_256_L128"]
+    p = base_params(256, 256, 128.0, 128.0, dt=c["dt"], **reservoir_physics())
+    P = random_gaussian_pumps(256, 128.0, 1, seed)[:, None][0]
+    psi0 = complex_normal((1, 256, 256), 1e-2, seed)
+    return dict(name="steady_256", params=p, psi0=psi0,
+                n0=np.zeros((1, 256, 256)), P=P, V=None, steps=200000)
+
+
+def random_state(ncomp, ny, nx, seed, amp=1.0, reservoir=True, smooth=False):
+    """Generic random test state: psi (complex), n >= 0, P >= 0, V."""
+    rng = np.random.default_rng(seed)
+    psi = amp * (rng.normal(size=(ncomp, ny, nx)) + 1j * rng.normal(size=(ncomp, ny, nx)))
+    if smooth:
+        # smooth by repeated neighbour averaging (periodic) -- a pure input
+        # shaping step, not part of the method
+        for _ in range(6):
+            psi = 0.2 * (psi + np.roll(psi, 1, -1) + np.roll(psi, -1, -1)
+                         + np.roll(psi, 1, -2) + np.roll(psi, -1, -2))
+    n = rng.uniform(0.0, 2.0, size=(ncomp, ny, nx)) if reservoir else None
+    P = rng.uniform(0.0, 5.0, size=(ncomp, ny, nx)) if reservoir else None
+    V = rng.uniform(-1.0, 1.0, size=(ny, nx))
+    return psi, n, P, V

@@ -1,0 +1,148 @@
+"""Pins of the oracle's noise generator (oracle/noise.py).  CPU only.
+
+* Philox4x32-10 against an independent implementation: Triton's
+  ``tl.philox`` executed by Triton's CPU interpreter (same published
+  algorithm; key = (seed lo, seed hi), counter words passed explicitly).
+* own ln / cos / sin against libm within stated bounds.
+* Gaussian statistics: mean, E|xi|^2, E xi^2, neighbour and step correlation.
+"""
+import json
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+from oracle import noise, gp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+_TRITON_SCRIPT = textwrap.dedent(r"""
+    import os, json, sys
+    os.environ["TRITON_INTERPRET"] = "1"
+    import numpy as np, torch, triton, triton.language as tl
+
+    @triton.jit
+    def k(c0p, c1p, c2p, c3p, out, seed, N: tl.constexpr):
+        o = tl.arange(0, N)
+        c0 = tl.load(c0p + o); c1 = tl.load(c1p + o)
+        c2 = tl.load(c2p + o); c3 = tl.load(c3p + o)
+        a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
+        tl.store(out + o * 4 + 0, a); tl.store(out + o * 4 + 1, b)
+        tl.store(out + o * 4 + 2, c); tl.store(out + o * 4 + 3, d)
+
+    cfg = json.loads(sys.argv[1])
+    N = len(cfg["c0"])
+    t = lambda v: torch.tensor(np.array(v, dtype=np.uint32).view(np.int32))
+    out = torch.zeros(N * 4, dtype=torch.int32)
+    k[(1,)](t(cfg["c0"]), t(cfg["c1"]), t(cfg["c2"]), t(cfg["c3"]), out,
+            cfg["seed"], N)
+    print(json.dumps(out.numpy().view(np.uint32).reshape(N, 4).tolist()))
+""")
+
+
+def test_philox_matches_triton_interpreter():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(123)
+    N = 32
+    c = rng.integers(0, 2 ** 32, size=(4, N), dtype=np.uint64)
+    c[:, 0] = 0
+    c[:, 1] = 0xFFFFFFFF
+    seed = int(rng.integers(0, 2 ** 63))
+    cfg = dict(c0=c[0].tolist(), c1=c[1].tolist(), c2=c[2].tolist(),
+               c3=c[3].tolist(), seed=seed)
+    r = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT, json.dumps(cfg)],
+                       capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, TRITON_INTERPRET="1"))
+    if r.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + r.stderr[-300:])
+    ref = np.array(json.loads(r.stdout.strip().splitlines()[-1]), dtype=np.uint64)
+    w = noise.philox4x32_10(c[0].astype(np.uint32), c[1].astype(np.uint32),
+                            c[2].astype(np.uint32), c[3].astype(np.uint32),
+                            seed & 0xFFFFFFFF, seed >> 32)
+    mine = np.stack(w, axis=1).astype(np.uint64)
+    assert np.array_equal(mine, ref)
+
+
+def test_uniform_open_interval_exact():
+    w = np.array([0, 1, 511, 512, 0xFFFFFFFF, 0x80000000], dtype=np.uint32)
+    u = noise.uniform_open01(w)
+    assert u.dtype == np.float32
+    exact = (2 * (w.astype(np.int64) >> 9) + 1) / 2.0 ** 24
+    assert np.array_equal(u.astype(np.float64), exact)
+    assert u.min() > 0 and u.max() < 1
+
+
+def test_ln_accuracy():
+    rng = np.random.default_rng(0)
+    w = rng.integers(0, 2 ** 32, size=200000, dtype=np.uint64).astype(np.uint32)
+    u = noise.uniform_open01(w)
+    u = np.concatenate([u, np.float32([2.0 ** -24, 1 - 2.0 ** -24, 0.5,
+                                       np.sqrt(0.5), 0.70710677, 0.7071068])])
+    mine = noise.ln_f32(u).astype(np.float64)
+    ref = np.log(u.astype(np.float64))
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    err = np.abs(mine - ref) / ulp
+    assert err.max() <= 4.0, err.max()
+
+
+def test_cos_sin_accuracy():
+    rng = np.random.default_rng(1)
+    w = rng.integers(0, 2 ** 32, size=200000, dtype=np.uint64).astype(np.uint32)
+    u = noise.uniform_open01(w)
+    u = np.concatenate([u, np.float32([2.0 ** -24, 0.25, 0.5, 0.75, 1 - 2.0 ** -24])])
+    c, s = noise.cos_sin_2pi_f32(u)
+    th = 2 * np.pi * u.astype(np.float64)
+    # the float32 argument 2 pi u carries ~1e-7 relative rounding of pi/2
+    assert np.max(np.abs(c - np.cos(th))) < 1.5e-6
+    assert np.max(np.abs(s - np.sin(th))) < 1.5e-6
+    assert np.max(np.abs(c.astype(np.float64) ** 2 + s.astype(np.float64) ** 2 - 1)) < 1e-6
+
+
+def test_gaussian_statistics():
+    var = 1e-3
+    re, im = noise.noise_field(seed=3, step=7, instance=0, ncomp=2, ny=256,
+                               nx=256, var=var)
+    xi = re.astype(np.float64) + 1j * im.astype(np.float64)
+    n = xi.size
+    se = var / np.sqrt(n)
+    assert abs(np.mean(xi.real)) < 5 * np.sqrt(var / 2 / n)
+    assert abs(np.mean(xi.imag)) < 5 * np.sqrt(var / 2 / n)
+    assert abs(np.mean(np.abs(xi) ** 2) - var) < 6 * se
+    assert abs(np.mean(xi ** 2)) < 6 * se                     # <dW dW> = 0
+    # no site-to-site correlation (x neighbours), no component correlation
+    assert abs(np.mean(xi[..., 1:] * np.conj(xi[..., :-1]))) < 6 * se
+    assert abs(np.mean(xi[0] * np.conj(xi[1]))) < 6 * se
+    # no step-to-step correlation
+    re2, im2 = noise.noise_field(3, 8, 0, 2, 256, 256, var)
+    xi2 = re2 + 1j * im2.astype(np.float64)
+    assert abs(np.mean(xi * np.conj(xi2))) < 6 * se
+    # kurtosis of a Gaussian quadrature = 3
+    q = xi.real.ravel() / np.sqrt(var / 2)
+    assert abs(np.mean(q ** 4) - 3.0) < 0.1
+
+
+def test_noise_keyed_by_counter():
+    """Different seed / instance / step give unrelated fields; the same key
+    reproduces the same bits (resume is bit-exact)."""
+    a = noise.noise_field(9, 2 ** 33 + 5, 4, 1, 8, 8, 1.0)
+    b = noise.noise_field(9, 2 ** 33 + 5, 4, 1, 8, 8, 1.0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for other in (noise.noise_field(10, 2 ** 33 + 5, 4, 1, 8, 8, 1.0),
+                  noise.noise_field(9, 5, 4, 1, 8, 8, 1.0),
+                  noise.noise_field(9, 2 ** 33 + 5, 5, 1, 8, 8, 1.0)):
+        assert not np.any(other[0] == a[0])
+
+
+def test_noise_enters_after_deterministic_step():
+    """With every coefficient zero, one step from psi = 0 gives exactly xi."""
+    p = gp.Params(nx=8, ny=6, lx=1.0, ly=1.0, kappa=0.0, spinor=True,
+                  noise_var=2e-3, seed=77, dt=0.1)
+    psi0 = np.zeros((2, 6, 8), complex)
+    psi, _ = gp.run(psi0, None, None, None, p, 1, step0=41)
+    re, im = noise.noise_field(77, 41, 0, 2, 6, 8, 2e-3)
+    assert np.array_equal(psi.real, re.astype(np.float64))
+    assert np.array_equal(psi.imag, im.astype(np.float64))
