@@ -1,0 +1,382 @@
+"""Benchmark of the fused RK4 dNLSE step on GB300.
+
+One bench step = one full run of the driven-dissipative reservoir workload
+(1024x1024 grid, 100 um periodic box, ring pump of radius 20 um / width 3 um at
+1.5 P_thr, initial noise 1e-2, 10^4 RK4 steps at half the stability limit) plus
+the FP64 norm/energy and steady-state-residual reductions, through the C ABI.
+
+Prints ONE JSON line (rank 0).  Metric: RK4 site-updates/s (whole job).
+  value      device-timed (CUDA events on the solver's stream), inputs resident
+  e2e        same metric through the C ABI with pinned host buffers, H2D/D2H
+             copies inside the timed region (host wall clock)
+  roofline   dominant kernel (the fused RK4 step): algorithmic bytes / average
+             launch time against the measured HBM copy bandwidth
+  cpu_baseline  the FP64 numpy oracle timed on a bounded sample (rank 0, N=1)
+
+--impl reference times the oracle itself on the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (different
+seeds); value = all ranks' site-updates / max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RK4_STEPS = 10000
+BYTES_PER_SITE = {  # algorithmic bytes per site per RK4 step (read + write once)
+    (32, "reservoir"): 28, (64, "reservoir"): 56,
+    (32, "conservative"): 16, (64, "conservative"): 32,
+    (32, "spinor"): 52, (64, "spinor"): 104,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="phx", choices=["phx", "reference"])
+    ap.add_argument("--workload", default="reservoir_1024",
+                    choices=["reservoir_1024", "spinor_2048", "conservative_64"])
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--rk4-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(name, seed_offset=0):
+    import synth
+    if name == "reservoir_1024":
+        cfg = synth.reservoir_1024(seed=2 + seed_offset)
+        kind = "reservoir"
+        desc = ("driven-dissipative GP + reservoir, 1024x1024, 100 um periodic, ring "
+                "pump r=20 um w=3 um at 1.5 P_thr, psi0 noise 1e-2, dt = half RK4 limit")
+    elif name == "spinor_2048":
+        cfg = synth.spinor_grid(2048, seed=3 + seed_offset, const_key="spinor_2048_L200")
+        kind = "spinor"
+        desc = ("TE-TM spinor GP + reservoir, 2048x2048, 200 um periodic, Gaussian pump "
+                "w=10 um at 1.5 P_thr, Philox noise var 1e-3 per step")
+    else:
+        cfg = synth.conservative_64(seed=1 + seed_offset)
+        kind = "conservative"
+        desc = "conservative GP 64x64, 20 um periodic, Gaussian amp 5 w 3 um + noise"
+    return cfg, kind, desc
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2411_18341_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name, precision):
+    """DRAM bytes per launch of the fused step kernel from the committed ncu
+    summary, if it was captured from the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "rk4_step_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    key = "%s_fp%d" % (workload_name, precision)
+    e = rec.get(key)
+    if not e or e.get("kernel_sources") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """Samples nvidia-smi clocks during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join("/tmp", "phx_clocks_%d.csv" % os.getpid())
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(name, cfg, budget_s=15.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import gp
+    p = gp.Params(**cfg["params"])
+    psi, n = np.array(cfg["psi0"], complex), cfg["n0"]
+    P = None if cfg["P"] is None else np.broadcast_to(cfg["P"], (p.ncomp, p.ny, p.nx))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        psi, n = gp.run(psi, n, P, None, p, 1, step0=steps)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s or steps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    sites = p.nx * p.ny
+    return {"value": sites * steps / dt, "unit": "site-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "%d RK4 steps of the %dx%d %s workload (numpy FP64, 1 thread), %.1f s"
+                      % (steps, p.nx, p.ny, name, dt)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cfg, kind, desc = workload(args.workload)
+    from oracle import gp
+    p = gp.Params(**cfg["params"])
+    psi, n = np.array(cfg["psi0"], complex), cfg["n0"]
+    P = None if cfg["P"] is None else np.broadcast_to(cfg["P"], (p.ncomp, p.ny, p.nx))
+    per = 1 if p.nx * p.ny >= 1 << 20 else 20
+    for w in range(args.warmup):
+        gp.run(psi, n, P, None, p, 1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        psi, n = gp.run(psi, n, P, None, p, per, step0=k * per)
+    el = time.perf_counter() - t0
+    val = p.nx * p.ny * per * args.steps / el
+    line = {"metric": "RK4 site-updates/s", "impl": "reference", "value": val,
+            "unit": "site-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc,
+                       "grid": "%dx%d" % (p.nx, p.ny), "sample_rk4_steps_per_step": per},
+            "cpu_baseline": {"value": val, "unit": "site-updates/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "%d RK4 steps per bench step of the %s workload"
+                                       % (per, args.workload)},
+            "e2e": {"value": val, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+
+    import torch
+    import paper_2411_18341_gb300 as phx
+    from paper_2411_18341_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    cfg, kind, desc = workload(args.workload, seed_offset=rank)
+    rk4_steps = args.rk4_steps or (RK4_STEPS if args.workload != "conservative_64" else 1000)
+    if args.workload == "spinor_2048" and args.rk4_steps is None:
+        rk4_steps = 2000
+    prec = args.precision
+    real = torch.float32 if prec == 32 else torch.float64
+    cplx = torch.complex64 if prec == 32 else torch.complex128
+    d = cfg["params"]
+    nx, ny = d["nx"], d["ny"]
+    nc = 2 if d["spinor"] else 1
+    sites = nx * ny
+    stream = torch.cuda.Stream(device=dev)
+    h = phx.phx_create(phx.params_from_dict(d, precision=prec, stream=stream.cuda_stream))
+
+    # resident inputs on the device
+    psi0_d = torch.tensor(np.ascontiguousarray(cfg["psi0"]), dtype=cplx, device=dev)
+    n0_d = None if cfg["n0"] is None else torch.tensor(cfg["n0"], dtype=real, device=dev)
+    P_d = None if cfg["P"] is None else torch.tensor(cfg["P"][0], dtype=real, device=dev)
+    if P_d is not None:
+        phx.phx_set_pump(h, P_d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step(ev_k0=None, ev_k1=None):
+        phx.phx_set_state(h, psi0_d, n0_d)
+        if ev_k0 is not None:
+            ev_k0.record(stream)
+        phx.phx_step_n(h, rk4_steps)
+        if ev_k1 is not None:
+            ev_k1.record(stream)
+        phx.phx_norm_energy(h)
+        phx.phx_residual(h)
+
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    launches0 = phx.phx_launch_count()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # L2 flush between timed steps (not timed)
+        a, b, k0, k1 = ev[k]
+        a.record(stream)
+        one_step(k0, k1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    launches = phx.phx_launch_count() - launches0
+    barrier(pg)
+    clk = clocks.stop() if clocks else None
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    kern_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    ms = float(np.mean(step_ms))
+    ms = max_over_ranks(pg, ms)
+    value = world * sites * rk4_steps / (ms * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers
+    psi_h = torch.tensor(np.ascontiguousarray(cfg["psi0"]), dtype=cplx).pin_memory()
+    n_h = None if cfg["n0"] is None else torch.tensor(cfg["n0"], dtype=real).pin_memory()
+    P_h = None if cfg["P"] is None else torch.tensor(cfg["P"][0], dtype=real).pin_memory()
+    out_psi = torch.empty_like(psi_h).pin_memory()
+    out_n = None if n_h is None else torch.empty_like(n_h).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        if P_h is not None:
+            phx.phx_set_pump(h, P_h)
+        phx.phx_set_state(h, psi_h, n_h)
+        phx.phx_step_n(h, rk4_steps)
+        phx.phx_norm_energy(h)
+        phx.phx_residual(h)
+        phx.phx_get_state(h, out_psi, out_n)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(pg, (time.perf_counter() - t0) / e2e_steps)
+    esz = 4 if prec == 32 else 8
+    h2d = sites * nc * 2 * esz + (0 if n_h is None else sites * nc * esz) + \
+        (0 if P_h is None else sites * esz)
+    d2h = sites * nc * 2 * esz + (0 if n_h is None else sites * nc * esz) + 2 * 8 + 8 * 8
+
+    pk, pk_kind = peaks()
+    bps = BYTES_PER_SITE[(prec, kind)]
+    kern_s = float(np.mean(kern_ms)) * 1e-3 / rk4_steps
+    achieved = bps * sites / kern_s / 1e9
+    traffic = recorded_traffic(args.workload, prec)
+    line = {
+        "metric": "RK4 site-updates/s",
+        "value": value, "unit": "site-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc,
+                   "grid": "%dx%d" % (nx, ny), "rk4_steps_per_step": rk4_steps,
+                   "per_step": "set_state + %d fused RK4 steps + FP64 norm/energy + "
+                               "FP64 residual" % rk4_steps,
+                   "l2": "256 MB buffer written between timed steps; the %.0f MB state "
+                         "stays L2-resident within a step" % (
+                             (2 * sites * nc * 2 * esz + (2 * sites * nc * esz if n_h is not None else 0)
+                              + (sites * esz if P_h is not None else 0)) / 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": world * sites * rk4_steps / e2e_s, "unit": "site-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     "traffic": traffic,
+                     "kernel": "rk4_step (fused, one launch per RK4 step)",
+                     "algorithmic_bytes_per_site": bps,
+                     "avg_launch_us": kern_s * 1e6,
+                     "peak_source": pk_kind},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, cfg)
+    phx.phx_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

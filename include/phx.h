@@ -1,0 +1,180 @@
+/*
+ * phx.h -- C ABI of the GB300 RK4 solver for the 2D driven-dissipative
+ * Gross-Pitaevskii / dissipative nonlinear Schroedinger equation (dNLSE)
+ * of PHOENIX (arXiv 2411.18341).
+ *
+ * What one step computes (all citations are to the paper):
+ *   Eq. (PULSE_psi), Sec. V, with coherent drive E = 0:
+ *     dpsi_c/dt = -(i/hbar)[ -(hbar^2/2m) Lap psi_c + (V + g|psi_c|^2
+ *                 + g_x|psi_o|^2 + g_r n_c) psi_c + J_c psi_o ]
+ *                 + (1/2)(R n_c - gamma_c) psi_c  (+ dW)
+ *     c in {+} (scalar, Eq. 1) or {+,-} (spinor), o = other component,
+ *     J_+ = Delta_LT (d_x - i d_y)^2, J_- = Delta_LT (d_x + i d_y)^2.
+ *   Eq. (PULSE_res): dn_c/dt = P_c - (gamma_r + R|psi_c|^2) n_c.
+ *   Lap: the 5-point central-difference stencil of Sec. III.B.6; the TE-TM
+ *   operator uses 3-point second differences and the 4-corner mixed
+ *   difference.  Time step: RK4, Eqs. (rk4_K1)-(rk4_final).  Boundary
+ *   conditions: x and y independently periodic or zero (Sec. V).
+ *   Noise dW: after each deterministic step psi_c += xi_c with xi a complex
+ *   Gaussian of E|xi|^2 = noise_var from Philox4x32-10 keyed by
+ *   (seed, step, instance, site) (Salmon et al., SC'11), so runs and
+ *   resumes are reproducible bit for bit.
+ *
+ * Conventions
+ *   - Every call returns a phx_status; on error the handle's state is left
+ *     as it was and phx_last_error() holds a message.
+ *   - Arrays are row-major ny x nx with x fastest; site = j*nx + i.
+ *     psi: ncomp planes of interleaved complex (re, im) values; n, P: ncomp
+ *     planes of reals; V: one plane.  Element type is float for
+ *     precision 32 and double for precision 64.
+ *   - `on_device` = 1: the pointer is CUDA device memory of the handle's
+ *     device; 0: host memory (pinned or pageable).  Inputs are copied;
+ *     the caller keeps ownership of every pointer it passes.
+ *   - Work is queued on params.stream (a cudaStream_t; NULL = legacy default
+ *     stream).  Calls that return values to the host synchronise that stream.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef PHX_H
+#define PHX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PHX_ABI_VERSION 1
+
+typedef enum phx_status {
+  PHX_OK = 0,
+  PHX_EINVAL = 1,      /* bad argument (null pointer, size, dt above the RK4 limit, ...) */
+  PHX_ENOMEM = 2,      /* device or host allocation failed */
+  PHX_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  PHX_ENONFINITE = 4,  /* a reduction found NaN or Inf in the state */
+  PHX_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+  PHX_ESTATE = 6,      /* call not valid in the handle's current state */
+  PHX_ENODEV = 7       /* no CUDA device of compute capability 10.x */
+} phx_status;
+
+enum { PHX_BC_PERIODIC = 0, PHX_BC_ZERO = 1 };
+
+/* Parameters of one problem instance (Eqs. PULSE_psi / PULSE_res).
+ * Units: lengths um, energies meV, times ps. */
+typedef struct phx_params {
+  uint32_t struct_size;      /* = sizeof(phx_params); set by phx_params_init */
+  int32_t nx, ny;            /* grid points, >= 1 each */
+  double lx, ly;             /* domain lengths; dx = lx/nx, dy = ly/ny */
+  int32_t bc_x, bc_y;        /* PHX_BC_PERIODIC or PHX_BC_ZERO */
+  int32_t precision;         /* 32 or 64: stencil arithmetic and storage */
+  int32_t spinor;            /* 0: scalar psi; 1: two components psi_+, psi_- */
+  int32_t reservoir;         /* 0/1: evolve n_c with Eq. (PULSE_res) */
+  int32_t tile;              /* 0 = automatic tile shape; otherwise a tile id */
+  double hbar2_over_2m;      /* hbar^2/2m, meV um^2 */
+  double g, g_x, g_r;        /* meV um^2 */
+  double R;                  /* ps^-1 um^2 */
+  double gamma_c, gamma_r;   /* ps^-1 */
+  double delta_lt;           /* TE-TM splitting Delta_LT, meV um^2 (spinor only) */
+  double dt;                 /* RK4 step, ps; rejected above the stability limit */
+  double noise_var;          /* E|xi|^2 added per site and step; 0 = off */
+  uint64_t seed;             /* Philox key */
+  uint32_t instance;         /* Philox counter word 1 (ensemble member id) */
+  uint32_t reserved;
+  void* stream;              /* cudaStream_t */
+} phx_params;
+
+typedef struct phx_handle phx_handle;
+
+/* Fill *p with defaults: 64x64, 1x1 um, periodic, fp32, scalar, no
+ * reservoir, hbar^2/2m = 0.67, all other coefficients 0, stream NULL.
+ * EINVAL if p is NULL. */
+phx_status phx_params_init(phx_params* p);
+
+/* Largest stable RK4 step for the linear Hermitian part of the equations
+ * (stencil and TE-TM; nonlinear, potential and loss terms excluded):
+ * dt_max = 2 sqrt(2) hbar / lambda_max, 2 sqrt(2) being the extent of the RK4
+ * region on the imaginary axis (Eqs. rk4_K1-final).  Host-only; EINVAL on
+ * bad parameters. */
+phx_status phx_stability_dt(const phx_params* p, double* dt_max);
+
+/* Validate p, allocate the device state on the current CUDA device and
+ * zero it (psi = 0, n = 0, P = 0, V absent, step 0, t = 0).
+ * EINVAL: bad sizes, BC, precision, spinor-only terms on a scalar problem,
+ * dt <= 0 or dt > phx_stability_dt.  ENODEV: no sm_10x device.
+ * ENOMEM / ECUDA on allocation failure.  *out is NULL on error. */
+phx_status phx_create(const phx_params* p, phx_handle** out);
+
+/* Copy the pump P_+ (and P_-; NULL means P_- = P_+) into the handle
+ * (Eq. PULSE_res).  ESTATE if the handle has no reservoir. */
+phx_status phx_set_pump(phx_handle* h, const void* P_plus, const void* P_minus,
+                        int on_device);
+
+/* Copy the external potential V (Eq. PULSE_psi); V = NULL removes it. */
+phx_status phx_set_potential(phx_handle* h, const void* V, int on_device);
+
+/* Copy psi (ncomp planes of complex) and n (ncomp planes; ignored / may be
+ * NULL without a reservoir, NULL with a reservoir keeps n) into the handle.
+ * psi may be NULL to keep psi. */
+phx_status phx_set_state(phx_handle* h, const void* psi, const void* n,
+                         int on_device);
+
+/* Copy the current psi and n (either may be NULL) out of the handle;
+ * synchronises the stream. */
+phx_status phx_get_state(phx_handle* h, void* psi, void* n, int on_device);
+
+/* Queue nsteps >= 0 RK4 steps (Eqs. rk4_K1-final, plus noise when
+ * noise_var > 0).  Asynchronous on the stream; advances the step counter
+ * and the FP64 simulated time t += dt on the device. */
+phx_status phx_step_n(phx_handle* h, int64_t nsteps);
+
+/* FP64 norm N = dx dy sum_c |psi_c|^2 and energy
+ * E = dx dy sum [ sum_c ( Re psi_c^*(-hbar^2/2m Lap psi_c)
+ *     + (V + g_r n_c)|psi_c|^2 + (g/2)|psi_c|^4 ) + g_x|psi_+|^2|psi_-|^2
+ *     + Re(psi_+^* J_+ psi_- + psi_-^* J_- psi_+) ],
+ * the functional whose derivative dE/dpsi_c^* is the bracket of
+ * Eq. (PULSE_psi).  Synchronises; ENONFINITE if the state holds NaN/Inf. */
+phx_status phx_norm_energy(phx_handle* h, double* norm, double* energy);
+
+/* Steady-state residual in FP64: K = dpsi/dt of Eq. (PULSE_psi) without
+ * noise, omega = -Im<psi,K>/||psi||^2, r_psi = ||K + i omega psi||/||psi||
+ * (ps^-1; the global phase rotation of a stationary condensate removed),
+ * r_n = ||dn/dt|| / ||n|| (0 without a reservoir).  Any output pointer may be
+ * NULL.  Synchronises; ENONFINITE on NaN/Inf. */
+phx_status phx_residual(phx_handle* h, double* r_psi, double* r_n,
+                        double* omega);
+
+/* Step counter and FP64 simulated time (t accumulated on the device). */
+phx_status phx_time(phx_handle* h, int64_t* step, double* t);
+
+/* Overwrite the step counter and time (checkpoint restore). */
+phx_status phx_set_time(phx_handle* h, int64_t step, double t);
+
+/* Replace the stream used by later calls. */
+phx_status phx_set_stream(phx_handle* h, void* stream);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t phx_launch_count(void);
+
+/* Message of the last error on h (h = NULL: last error of a call without a
+ * handle on this thread).  Never NULL. */
+const char* phx_last_error(const phx_handle* h);
+
+/* Static name of a status code. */
+const char* phx_status_string(phx_status s);
+
+/* Free the handle and its device memory.  NULL-safe. */
+void phx_destroy(phx_handle* h);
+
+/* Generate the noise field xi_c(seed, step, instance, site) that a step
+ * with these keys adds, as float32 (re, im) pairs in out_device
+ * [ncomp][ny][nx][2] (device memory, caller-owned).  Asynchronous on stream.
+ * Lets callers and tests inspect the exact bits the step kernel adds. */
+phx_status phx_noise_sample(uint64_t seed, int64_t step, uint32_t instance,
+                            int32_t ncomp, int32_t nx, int32_t ny,
+                            double noise_var, float* out_device, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHX_H */

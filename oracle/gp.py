@@ -324,3 +324,41 @@ def pump_threshold(p):
     Eq. (PULSE_res) at psi -> 0 (n = P/gamma_r) and Eq. (PULSE_psi) gain
     R n = gamma_c."""
     return p.gamma_c * p.gamma_r / p.R
+
+
+def step_at_sites(psi, n, P, V, p, sites_ji, step, radius=5):
+    """One RK4 step (plus noise) evaluated only at the given (j, i) sites of
+    a large grid.  A step's output at a site depends on the inputs within
+    distance 4 (one cell per stage), so each site is computed on its own
+    window of radius `radius` >= 5 evolved with zero boundaries: along a
+    periodic axis the window wraps; along a zero axis it is cut at the domain
+    edge (cells outside the domain stay zero at every stage).
+    Returns (psi_c[sites], n_c[sites]) with shape (ncomp, nsites)."""
+    nc = p.ncomp
+    out_psi = np.empty((nc, len(sites_ji)), complex)
+    out_n = np.empty((nc, len(sites_ji))) if p.reservoir else None
+    Pb = np.broadcast_to(P, (nc, p.ny, p.nx)) if p.reservoir else None
+
+    def axis(c, N, bc):
+        if bc == PERIODIC:
+            return np.arange(c - radius, c + radius + 1) % N, radius
+        lo, hi = max(c - radius, 0), min(c + radius, N - 1)
+        return np.arange(lo, hi + 1), c - lo
+
+    for k, (j, i) in enumerate(sites_ji):
+        jj, cj = axis(j, p.ny, p.bc_y)
+        ii, ci = axis(i, p.nx, p.bc_x)
+        q = p.with_(nx=len(ii), ny=len(jj), lx=len(ii) * p.dx, ly=len(jj) * p.dy,
+                    bc_x=ZERO, bc_y=ZERO, noise_var=0.0)
+        win = lambda a: a[..., jj[:, None], ii[None, :]]
+        a, b = rk4_step(win(psi), win(n) if p.reservoir else None,
+                        win(Pb) if p.reservoir else None,
+                        win(V) if V is not None else None, q)
+        out_psi[:, k] = a[:, cj, ci]
+        if p.reservoir:
+            out_n[:, k] = b[:, cj, ci]
+    if p.noise_var != 0.0:
+        sites = np.array([j * p.nx + i for j, i in sites_ji])
+        re, im = _noise.noise_at(p.seed, step, p.instance, sites, nc, p.noise_var)
+        out_psi = out_psi + (re.astype(np.float64) + 1j * im.astype(np.float64))
+    return out_psi, out_n

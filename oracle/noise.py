@@ -173,3 +173,20 @@ def noise_field(seed, step, instance, ncomp, ny, nx, var):
     if ncomp == 2:
         re[1], im[1] = box_muller_f32(w2, w3, sc)
     return re, im
+
+
+def noise_at(seed, step, instance, sites, ncomp, var):
+    """Noise for arbitrary global site indices (uint32 array): float32 arrays
+    re, im of shape (ncomp,) + sites.shape."""
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    step = int(step) & 0xFFFFFFFFFFFFFFFF
+    sites = np.asarray(sites).astype(np.uint64).astype(U32)
+    w0, w1, w2, w3 = philox4x32_10(sites, U32(instance), U32(step & 0xFFFFFFFF),
+                                   U32(step >> 32), seed & 0xFFFFFFFF, seed >> 32)
+    sc = noise_scale(var)
+    re = np.empty((ncomp,) + sites.shape, F32)
+    im = np.empty((ncomp,) + sites.shape, F32)
+    re[0], im[0] = box_muller_f32(w0, w1, sc)
+    if ncomp == 2:
+        re[1], im[1] = box_muller_f32(w2, w3, sc)
+    return re, im

@@ -1,0 +1,283 @@
+"""GB300 RK4 solver for the 2D driven-dissipative Gross-Pitaevskii / dNLSE
+(PHOENIX, arXiv 2411.18341): Python binding of the C ABI in include/phx.h.
+
+The binding only marshals arguments: every step of the computation runs in
+the CUDA kernels of ``_build/libphx.so``.  Importing works without a GPU (the
+library loads; nothing is computed); any compute call on a machine without
+an sm_103a device returns PHX_ENODEV, and a missing library raises at load.
+
+Functions carry the C names (``phx_create``, ``phx_set_pump``, ``phx_step_n``,
+``phx_norm_energy``, ``phx_destroy``, ...).  Arrays may be numpy arrays (host)
+or torch tensors (host or CUDA); complex arrays are interleaved (re, im).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libphx.so")
+
+PHX_OK = 0
+STATUS = {0: "PHX_OK", 1: "PHX_EINVAL", 2: "PHX_ENOMEM", 3: "PHX_ECUDA",
+          4: "PHX_ENONFINITE", 5: "PHX_ETIMEOUT", 6: "PHX_ESTATE",
+          7: "PHX_ENODEV"}
+BC_PERIODIC = 0
+BC_ZERO = 1
+
+
+class PhxError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+        self.message = message
+
+
+class phx_params(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("spinor", ctypes.c_int32),
+        ("reservoir", ctypes.c_int32), ("tile", ctypes.c_int32),
+        ("hbar2_over_2m", ctypes.c_double),
+        ("g", ctypes.c_double), ("g_x", ctypes.c_double), ("g_r", ctypes.c_double),
+        ("R", ctypes.c_double),
+        ("gamma_c", ctypes.c_double), ("gamma_r", ctypes.c_double),
+        ("delta_lt", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("noise_var", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("instance", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+_SIGS = {
+    "phx_params_init": (ctypes.c_int, [ctypes.POINTER(phx_params)]),
+    "phx_stability_dt": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.POINTER(ctypes.c_double)]),
+    "phx_create": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.POINTER(ctypes.c_void_p)]),
+    "phx_set_pump": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "phx_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "phx_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "phx_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "phx_step_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "phx_norm_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "phx_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "phx_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
+    "phx_set_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
+    "phx_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "phx_launch_count": (ctypes.c_uint64, []),
+    "phx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "phx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "phx_destroy": (None, [ctypes.c_void_p]),
+    "phx_noise_sample": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libphx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libphx.so is not built (%s); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st, h=None):
+    if st != PHX_OK:
+        msg = lib().phx_last_error(h).decode(errors="replace")
+        raise PhxError(st, msg)
+
+
+def _ptr(a, dtype_real, expect_complex, expect_elems):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, 0, None
+    try:
+        import torch
+        is_t = isinstance(a, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_t = False
+    if is_t:
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        want = {(np.float32, False): torch.float32, (np.float64, False): torch.float64,
+                (np.float32, True): torch.complex64, (np.float64, True): torch.complex128}
+        if a.dtype != want[(dtype_real, expect_complex)]:
+            raise TypeError("tensor dtype %s, expected %s" % (a.dtype, want[(dtype_real, expect_complex)]))
+        if a.numel() != expect_elems:
+            raise ValueError("tensor has %d elements, expected %d" % (a.numel(), expect_elems))
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    arr = np.asarray(a)
+    want = {(np.float32, False): np.float32, (np.float64, False): np.float64,
+            (np.float32, True): np.complex64, (np.float64, True): np.complex128}[(dtype_real, expect_complex)]
+    if arr.dtype != want or not arr.flags.c_contiguous:
+        raise TypeError("array must be C-contiguous %s (got %s)" % (np.dtype(want), arr.dtype))
+    if arr.size != expect_elems:
+        raise ValueError("array has %d elements, expected %d" % (arr.size, expect_elems))
+    return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+# ---------------------------------------------------------------- C-ABI calls
+
+def phx_params_init(**kw):
+    p = phx_params()
+    _check(lib().phx_params_init(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k == "kappa":
+            k = "hbar2_over_2m"
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = int(v)
+        setattr(p, k, v)
+    return p
+
+
+def phx_stability_dt(p):
+    out = ctypes.c_double()
+    _check(lib().phx_stability_dt(ctypes.byref(p), ctypes.byref(out)))
+    return out.value
+
+
+class Handle:
+    """Owns a phx_handle*; remembers sizes for argument checks."""
+
+    def __init__(self, ptr, p):
+        self.ptr = ptr
+        self.nx, self.ny = p.nx, p.ny
+        self.ncomp = 2 if p.spinor else 1
+        self.reservoir = bool(p.reservoir)
+        self.real = np.float32 if p.precision == 32 else np.float64
+
+    @property
+    def as_parameter(self):
+        return self.ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().phx_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def phx_create(p):
+    out = ctypes.c_void_p()
+    _check(lib().phx_create(ctypes.byref(p), ctypes.byref(out)))
+    return Handle(out, p)
+
+
+def phx_set_pump(h, P_plus, P_minus=None):
+    n = h.nx * h.ny
+    a, dev_a, ka = _ptr(P_plus, h.real, False, n)
+    b, dev_b, kb = _ptr(P_minus, h.real, False, n)
+    if b is not None and dev_a != dev_b:
+        raise ValueError("P_plus and P_minus must both be host or both device")
+    _check(lib().phx_set_pump(h.ptr, a, b, dev_a), h.ptr)
+
+
+def phx_set_potential(h, V):
+    a, dev, k = _ptr(V, h.real, False, h.nx * h.ny)
+    _check(lib().phx_set_potential(h.ptr, a, dev), h.ptr)
+
+
+def phx_set_state(h, psi, n=None):
+    m = h.ncomp * h.nx * h.ny
+    a, dev_a, ka = _ptr(psi, h.real, True, m)
+    b, dev_b, kb = _ptr(n, h.real, False, m)
+    if a is not None and b is not None and dev_a != dev_b:
+        raise ValueError("psi and n must both be host or both device")
+    dev = dev_a if a is not None else dev_b
+    _check(lib().phx_set_state(h.ptr, a, b, dev), h.ptr)
+
+
+def phx_get_state(h, psi_out=None, n_out=None):
+    """Fill psi_out / n_out (numpy or torch, preallocated)."""
+    m = h.ncomp * h.nx * h.ny
+    a, dev_a, ka = _ptr(psi_out, h.real, True, m)
+    b, dev_b, kb = _ptr(n_out, h.real, False, m)
+    if a is not None and b is not None and dev_a != dev_b:
+        raise ValueError("outputs must both be host or both device")
+    dev = dev_a if a is not None else dev_b
+    _check(lib().phx_get_state(h.ptr, a, b, dev), h.ptr)
+
+
+def phx_step_n(h, nsteps):
+    _check(lib().phx_step_n(h.ptr, int(nsteps)), h.ptr)
+
+
+def phx_norm_energy(h):
+    N, E = ctypes.c_double(), ctypes.c_double()
+    _check(lib().phx_norm_energy(h.ptr, ctypes.byref(N), ctypes.byref(E)), h.ptr)
+    return N.value, E.value
+
+
+def phx_residual(h):
+    r, rn, om = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().phx_residual(h.ptr, ctypes.byref(r), ctypes.byref(rn), ctypes.byref(om)), h.ptr)
+    return r.value, rn.value, om.value
+
+
+def phx_time(h):
+    s, t = ctypes.c_int64(), ctypes.c_double()
+    _check(lib().phx_time(h.ptr, ctypes.byref(s), ctypes.byref(t)), h.ptr)
+    return s.value, t.value
+
+
+def phx_set_time(h, step, t):
+    _check(lib().phx_set_time(h.ptr, int(step), float(t)), h.ptr)
+
+
+def phx_set_stream(h, stream):
+    _check(lib().phx_set_stream(h.ptr, ctypes.c_void_p(int(stream) if stream else 0)), h.ptr)
+
+
+def phx_launch_count():
+    return int(lib().phx_launch_count())
+
+
+def phx_last_error(h=None):
+    return lib().phx_last_error(h.ptr if h is not None else None).decode(errors="replace")
+
+
+def phx_destroy(h):
+    if h.ptr:
+        lib().phx_destroy(h.ptr)
+        h.ptr = None
+
+
+def phx_noise_sample(seed, step, instance, ncomp, nx, ny, noise_var, out, stream=0):
+    """out: float32 CUDA tensor with ncomp*ny*nx*2 elements."""
+    if out.numel() != ncomp * nx * ny * 2 or not out.is_cuda:
+        raise ValueError("out must be a CUDA float32 tensor of ncomp*ny*nx*2 elements")
+    _check(lib().phx_noise_sample(int(seed), int(step), int(instance), int(ncomp), int(nx),
+                                  int(ny), float(noise_var), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(int(stream) if stream else 0)))
+
+
+# ------------------------------------------------------------- conveniences
+
+PARAM_KEYS = ("nx", "ny", "lx", "ly", "bc_x", "bc_y", "spinor", "reservoir",
+              "kappa", "g", "g_x", "g_r", "R", "gamma_c", "gamma_r", "delta_lt",
+              "dt", "noise_var", "seed", "instance")
+
+
+def params_from_dict(d, precision=32, stream=None, tile=0):
+    kw = {k: d[k] for k in PARAM_KEYS if k in d}
+    kw["spinor"] = int(bool(kw.get("spinor", 0)))
+    kw["reservoir"] = int(bool(kw.get("reservoir", 0)))
+    return phx_params_init(precision=precision, stream=stream or 0, tile=tile, **kw)

@@ -1,0 +1,589 @@
+// C ABI of the RK4 dNLSE solver: parameter validation, device buffers,
+// uploads with ghost-ring fill, step scheduling and FP64 reductions.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/phx.h"
+#include "phx_internal.h"
+
+namespace phx {
+unsigned long long launch_total();
+}
+
+using namespace phx;
+
+struct phx_handle {
+  phx_params p;
+  ModelKey m;
+  Geometry geo;
+  size_t esize = 0;          // bytes per real
+  void* psi[2] = {nullptr, nullptr};
+  void* n[2] = {nullptr, nullptr};
+  void* P = nullptr;
+  long long P_stride = 0;    // elements between P_+ and P_- planes (0 = shared)
+  void* V = nullptr;
+  bool has_V = false;
+  DevClock* clock = nullptr;
+  double* partials = nullptr;
+  double* red_dev = nullptr;
+  double* red_host = nullptr;  // pinned
+  int cur = 0;                 // buffer holding the current state
+  int parity = 0;              // clock slot of the current step
+  long long host_step = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+phx_status fail(phx_handle* h, phx_status s, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_err = msg;
+  return s;
+}
+
+phx_status cuda_fail(phx_handle* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                  cudaGetErrorString(e) + ")";
+  return fail(h, e == cudaErrorMemoryAllocation ? PHX_ENOMEM : PHX_ECUDA, m);
+}
+
+#define PHX_CK(h, expr)                                    \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) return cuda_fail((h), _e, #expr); \
+  } while (0)
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+// Largest |eigenvalue| of the linear Hermitian operator -kappa Lap (+ TE-TM)
+// over the grid's modes: periodic axis phases 2 pi m/N, zero axis Dirichlet
+// phases pi m/(N+1).  K^2 = (2 - 2cos a)/d^2, s^2 = sin^2(a)/d^2; the TE-TM
+// 2x2 block at a mode has eigenvalues kappa(Kx^2+Ky^2) +- Delta
+// sqrt((Kx^2-Ky^2)^2 + 4 sx^2 sy^2).
+double spectral_radius(const phx_params& p) {
+  auto axis = [](int N, int bc, double d, std::vector<double>& K2,
+                 std::vector<double>& s2) {
+    const double pi = 3.14159265358979323846;
+    if (bc == PHX_BC_PERIODIC) {
+      for (int m = 0; m <= N / 2; ++m) {  // phases m and N-m coincide in K2, s2
+        double a = 2.0 * pi * m / N;
+        K2.push_back((2.0 - 2.0 * std::cos(a)) / (d * d));
+        s2.push_back(std::sin(a) * std::sin(a) / (d * d));
+      }
+    } else {
+      for (int m = 1; m <= N; ++m) {
+        double a = pi * m / (N + 1);
+        K2.push_back((2.0 - 2.0 * std::cos(a)) / (d * d));
+        s2.push_back(std::sin(a) * std::sin(a) / (d * d));
+      }
+    }
+  };
+  std::vector<double> kx, sx, ky, sy;
+  double dx = p.lx / p.nx, dy = p.ly / p.ny;
+  axis(p.nx, p.bc_x, dx, kx, sx);
+  axis(p.ny, p.bc_y, dy, ky, sy);
+  const double kap = p.hbar2_over_2m;
+  if (!(p.spinor && p.delta_lt != 0.0)) {
+    double mx = 0, my = 0;
+    for (double v : kx) mx = std::fmax(mx, v);
+    for (double v : ky) my = std::fmax(my, v);
+    return std::fabs(kap) * (mx + my);
+  }
+  const double D = std::fabs(p.delta_lt);
+  double best = 0.0;
+  for (size_t j = 0; j < ky.size(); ++j)
+    for (size_t i = 0; i < kx.size(); ++i) {
+      double lam = kap * (kx[i] + ky[j]);
+      double dd = kx[i] - ky[j];
+      double off = D * std::sqrt(dd * dd + 4.0 * sx[i] * sy[j]);
+      best = std::fmax(best, std::fmax(std::fabs(lam + off), std::fabs(lam - off)));
+    }
+  return best;
+}
+
+phx_status validate(const phx_params* p, double* dtmax_out) {
+  if (!p) return fail(nullptr, PHX_EINVAL, "params is NULL");
+  if (p->struct_size != sizeof(phx_params))
+    return fail(nullptr, PHX_EINVAL, "params.struct_size mismatch (call phx_params_init)");
+  if (p->nx < 1 || p->ny < 1) return fail(nullptr, PHX_EINVAL, "nx, ny must be >= 1");
+  if ((long long)p->nx * p->ny > (1ll << 31) - 1)
+    return fail(nullptr, PHX_EINVAL, "nx*ny must be < 2^31");
+  if (!(p->lx > 0) || !(p->ly > 0) || !is_finite(p->lx) || !is_finite(p->ly))
+    return fail(nullptr, PHX_EINVAL, "lx, ly must be positive and finite");
+  if ((p->bc_x != PHX_BC_PERIODIC && p->bc_x != PHX_BC_ZERO) ||
+      (p->bc_y != PHX_BC_PERIODIC && p->bc_y != PHX_BC_ZERO))
+    return fail(nullptr, PHX_EINVAL, "bc_x, bc_y must be PHX_BC_PERIODIC or PHX_BC_ZERO");
+  if (p->precision != 32 && p->precision != 64)
+    return fail(nullptr, PHX_EINVAL, "precision must be 32 or 64");
+  if ((p->spinor != 0 && p->spinor != 1) || (p->reservoir != 0 && p->reservoir != 1))
+    return fail(nullptr, PHX_EINVAL, "spinor and reservoir must be 0 or 1");
+  const double c[] = {p->hbar2_over_2m, p->g, p->g_x, p->g_r, p->R, p->gamma_c,
+                      p->gamma_r, p->delta_lt, p->dt, p->noise_var};
+  for (double v : c)
+    if (!is_finite(v)) return fail(nullptr, PHX_EINVAL, "coefficients must be finite");
+  if (p->hbar2_over_2m < 0) return fail(nullptr, PHX_EINVAL, "hbar2_over_2m must be >= 0");
+  if (!p->spinor && (p->g_x != 0.0 || p->delta_lt != 0.0))
+    return fail(nullptr, PHX_EINVAL, "g_x and delta_lt need spinor = 1");
+  if (p->noise_var < 0) return fail(nullptr, PHX_EINVAL, "noise_var must be >= 0");
+  double lam = spectral_radius(*p);
+  double dtmax = lam > 0 ? 2.0 * std::sqrt(2.0) * HBAR / lam : INFINITY;
+  if (dtmax_out) *dtmax_out = dtmax;
+  return PHX_OK;
+}
+
+void free_all(phx_handle* h) {
+  if (!h) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int b = 0; b < 2; ++b) {
+    if (h->psi[b]) cudaFree(h->psi[b]);
+    if (h->n[b]) cudaFree(h->n[b]);
+  }
+  if (h->P) cudaFree(h->P);
+  if (h->V) cudaFree(h->V);
+  if (h->clock) cudaFree(h->clock);
+  if (h->partials) cudaFree(h->partials);
+  if (h->red_dev) cudaFree(h->red_dev);
+  if (h->red_host) cudaFreeHost(h->red_host);
+  cudaSetDevice(prev);
+}
+
+// Copy a user array (ncomp planes of ny x nx elements of `elem` bytes) into
+// the padded interior of `dst`, then refresh the ghost ring.
+phx_status upload(phx_handle* h, void* dst, const void* src, int nplanes,
+                  size_t elem, int on_device) {
+  const Geometry& g = h->geo;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int c = 0; c < nplanes; ++c) {
+    char* d = static_cast<char*>(dst) +
+              ((size_t)c * g.plane + (size_t)HALO * g.pitch + HALO) * elem;
+    const char* s = static_cast<const char*>(src) + (size_t)c * g.nx * g.ny * elem;
+    PHX_CK(h, cudaMemcpy2DAsync(d, (size_t)g.pitch * elem, s, (size_t)g.nx * elem,
+                                (size_t)g.nx * elem, g.ny, kind, h->stream));
+  }
+  PHX_CK(h, launch_fill_ghosts(dst, (int)elem, nplanes, g, h->stream));
+  return PHX_OK;
+}
+
+phx_status download(phx_handle* h, void* dst, const void* src, int nplanes,
+                    size_t elem, int on_device) {
+  const Geometry& g = h->geo;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int c = 0; c < nplanes; ++c) {
+    const char* s = static_cast<const char*>(src) +
+                    ((size_t)c * g.plane + (size_t)HALO * g.pitch + HALO) * elem;
+    char* d = static_cast<char*>(dst) + (size_t)c * g.nx * g.ny * elem;
+    PHX_CK(h, cudaMemcpy2DAsync(d, (size_t)g.nx * elem, s, (size_t)g.pitch * elem,
+                                (size_t)g.nx * elem, g.ny, kind, h->stream));
+  }
+  return PHX_OK;
+}
+
+Coeffs make_coeffs(const phx_params& p) {
+  Coeffs k;
+  const double dx = p.lx / p.nx, dy = p.ly / p.ny;
+  const double kh = p.hbar2_over_2m / HBAR;
+  k.ax = -kh / (dx * dx);
+  k.ay = -kh / (dy * dy);
+  k.a0 = 2.0 * kh * (1.0 / (dx * dx) + 1.0 / (dy * dy));
+  k.g = p.g / HBAR;
+  k.gx = p.g_x / HBAR;
+  k.gr = p.g_r / HBAR;
+  k.inv_hbar = 1.0 / HBAR;
+  k.half_R = 0.5 * p.R;
+  k.half_gc = 0.5 * p.gamma_c;
+  k.R = p.R;
+  k.gamma_r = p.gamma_r;
+  k.tx = p.delta_lt / (HBAR * dx * dx);
+  k.ty = p.delta_lt / (HBAR * dy * dy);
+  k.txy = p.delta_lt / (2.0 * HBAR * dx * dy);
+  k.dt = p.dt;
+  return k;
+}
+
+ReduceArgs make_reduce_args(const phx_handle* h) {
+  ReduceArgs r;
+  const phx_params& p = h->p;
+  const double dx = p.lx / p.nx, dy = p.ly / p.ny;
+  r.geo = h->geo;
+  r.psi = h->psi[h->cur];
+  r.n = h->m.reservoir ? h->n[h->cur] : nullptr;
+  r.P = h->P;
+  r.P_comp_stride = h->P_stride;
+  r.V = h->has_V ? h->V : nullptr;
+  r.idx2 = 1.0 / (dx * dx);
+  r.idy2 = 1.0 / (dy * dy);
+  r.ixy4 = 1.0 / (4.0 * dx * dy);
+  r.kappa = p.hbar2_over_2m;
+  r.g = p.g;
+  r.g_x = p.g_x;
+  r.g_r = p.g_r;
+  r.delta_lt = p.delta_lt;
+  r.R = p.R;
+  r.gamma_c = p.gamma_c;
+  r.gamma_r = p.gamma_r;
+  r.precision = p.precision;
+  r.ncomp = h->m.ncomp;
+  r.reservoir = h->m.reservoir;
+  r.tetm = h->m.tetm;
+  return r;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    cudaGetDevice(&now);
+    if (prev >= 0 && now != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+phx_status phx_params_init(phx_params* p) {
+  if (!p) return fail(nullptr, PHX_EINVAL, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->struct_size = sizeof(phx_params);
+  p->nx = 64;
+  p->ny = 64;
+  p->lx = 1.0;
+  p->ly = 1.0;
+  p->bc_x = PHX_BC_PERIODIC;
+  p->bc_y = PHX_BC_PERIODIC;
+  p->precision = 32;
+  p->hbar2_over_2m = 0.67;
+  return PHX_OK;
+}
+
+phx_status phx_stability_dt(const phx_params* p, double* dt_max) {
+  if (!dt_max) return fail(nullptr, PHX_EINVAL, "dt_max is NULL");
+  return validate(p, dt_max);
+}
+
+phx_status phx_create(const phx_params* p, phx_handle** out) {
+  if (!out) return fail(nullptr, PHX_EINVAL, "out is NULL");
+  *out = nullptr;
+  double dtmax = 0;
+  phx_status st = validate(p, &dtmax);
+  if (st != PHX_OK) return st;
+  if (!(p->dt > 0.0)) return fail(nullptr, PHX_EINVAL, "dt must be > 0");
+  if (p->dt > dtmax * (1.0 + 1e-12)) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "dt = %.6g ps exceeds the RK4 stability limit %.6g ps",
+                  p->dt, dtmax);
+    return fail(nullptr, PHX_EINVAL, buf);
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, PHX_ENODEV, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return fail(nullptr, PHX_ENODEV, cudaGetErrorString(e));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(nullptr, PHX_ENODEV, "kernels are built for sm_103a (GB300); device is sm_" +
+                                         std::to_string(prop.major * 10 + prop.minor));
+
+  phx_handle* h = new (std::nothrow) phx_handle();
+  if (!h) return fail(nullptr, PHX_ENOMEM, "host allocation failed");
+  h->p = *p;
+  h->device = dev;
+  h->stream = static_cast<cudaStream_t>(p->stream);
+  h->m.precision = p->precision;
+  h->m.ncomp = p->spinor ? 2 : 1;
+  h->m.reservoir = p->reservoir;
+  h->m.tetm = (p->spinor && p->delta_lt != 0.0) ? 1 : 0;
+  h->esize = p->precision == 32 ? 4 : 8;
+  Geometry& g = h->geo;
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.pitch = ((p->nx + 2 * HALO + PITCH_ALIGN - 1) / PITCH_ALIGN) * PITCH_ALIGN;
+  g.prow = p->ny + 2 * HALO;
+  g.plane = (long long)g.pitch * g.prow;
+  g.bc_x = p->bc_x;
+  g.bc_y = p->bc_y;
+
+  auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+    cudaError_t r = cudaMalloc(ptr, bytes);
+    if (r != cudaSuccess) return r;
+    return cudaMemsetAsync(*ptr, 0, bytes, h->stream);
+  };
+  const int nc = h->m.ncomp;
+  const size_t cplx = 2 * h->esize, real = h->esize;
+  cudaError_t ce = cudaSuccess;
+  for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
+    ce = alloc(&h->psi[b], (size_t)nc * g.plane * cplx);
+    if (ce == cudaSuccess && h->m.reservoir) ce = alloc(&h->n[b], (size_t)nc * g.plane * real);
+  }
+  if (ce == cudaSuccess && h->m.reservoir) {
+    ce = alloc(&h->P, (size_t)nc * g.plane * real);
+    h->P_stride = (nc == 2) ? g.plane : 0;
+  }
+  if (ce == cudaSuccess) ce = alloc((void**)&h->clock, sizeof(DevClock));
+  if (ce == cudaSuccess)
+    ce = alloc((void**)&h->partials, reduce_partials_len(g) * sizeof(double));
+  if (ce == cudaSuccess) ce = alloc((void**)&h->red_dev, 8 * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&h->red_host, 8 * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(ce);
+    free_all(h);
+    delete h;
+    return fail(nullptr, ce == cudaErrorMemoryAllocation ? PHX_ENOMEM : PHX_ECUDA, msg);
+  }
+  *out = h;
+  return PHX_OK;
+}
+
+phx_status phx_set_pump(phx_handle* h, const void* P_plus, const void* P_minus,
+                        int on_device) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  if (!h->m.reservoir) return fail(h, PHX_ESTATE, "set_pump needs reservoir = 1");
+  if (!P_plus) return fail(h, PHX_EINVAL, "P_plus is NULL");
+  DeviceGuard dg(h->device);
+  const Geometry& g = h->geo;
+  phx_status st = upload(h, h->P, P_plus, 1, h->esize, on_device);
+  if (st != PHX_OK) return st;
+  if (h->m.ncomp == 2) {
+    if (P_minus) {
+      char* d1 = static_cast<char*>(h->P) + (size_t)g.plane * h->esize;
+      st = upload(h, d1, P_minus, 1, h->esize, on_device);
+      if (st != PHX_OK) return st;
+      h->P_stride = g.plane;
+    } else {
+      h->P_stride = 0;  // both components read plane 0
+    }
+  }
+  return PHX_OK;
+}
+
+phx_status phx_set_potential(phx_handle* h, const void* V, int on_device) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  DeviceGuard dg(h->device);
+  if (!V) {
+    h->has_V = false;
+    return PHX_OK;
+  }
+  if (!h->V) {
+    size_t bytes = (size_t)h->geo.plane * h->esize;
+    PHX_CK(h, cudaMalloc(&h->V, bytes));
+    PHX_CK(h, cudaMemsetAsync(h->V, 0, bytes, h->stream));
+  }
+  phx_status st = upload(h, h->V, V, 1, h->esize, on_device);
+  if (st != PHX_OK) return st;
+  h->has_V = true;
+  return PHX_OK;
+}
+
+phx_status phx_set_state(phx_handle* h, const void* psi, const void* n, int on_device) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  DeviceGuard dg(h->device);
+  if (psi) {
+    phx_status st = upload(h, h->psi[h->cur], psi, h->m.ncomp, 2 * h->esize, on_device);
+    if (st != PHX_OK) return st;
+  }
+  if (n && h->m.reservoir) {
+    phx_status st = upload(h, h->n[h->cur], n, h->m.ncomp, h->esize, on_device);
+    if (st != PHX_OK) return st;
+  }
+  return PHX_OK;
+}
+
+phx_status phx_get_state(phx_handle* h, void* psi, void* n, int on_device) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  DeviceGuard dg(h->device);
+  if (psi) {
+    phx_status st = download(h, psi, h->psi[h->cur], h->m.ncomp, 2 * h->esize, on_device);
+    if (st != PHX_OK) return st;
+  }
+  if (n) {
+    if (!h->m.reservoir) return fail(h, PHX_ESTATE, "no reservoir in this handle");
+    phx_status st = download(h, n, h->n[h->cur], h->m.ncomp, h->esize, on_device);
+    if (st != PHX_OK) return st;
+  }
+  PHX_CK(h, cudaStreamSynchronize(h->stream));
+  return PHX_OK;
+}
+
+phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(h, PHX_EINVAL, "nsteps must be >= 0");
+  DeviceGuard dg(h->device);
+  const Coeffs k = make_coeffs(h->p);
+  NoiseKey nz;
+  nz.seed = h->p.seed;
+  nz.instance = h->p.instance;
+  nz.on = h->p.noise_var > 0.0;
+  nz.scale = (float)std::sqrt(h->p.noise_var / 2.0);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    cudaError_t e;
+    if (h->m.precision == 32) {
+      StepArgs<float> a;
+      a.geo = h->geo;
+      a.psi_in = static_cast<const float2*>(h->psi[h->cur]);
+      a.psi_out = static_cast<float2*>(h->psi[h->cur ^ 1]);
+      a.n_in = static_cast<const float*>(h->n[h->cur]);
+      a.n_out = static_cast<float*>(h->n[h->cur ^ 1]);
+      a.P = static_cast<const float*>(h->P);
+      a.P_comp_stride = h->P_stride;
+      a.V = h->has_V ? static_cast<const float*>(h->V) : nullptr;
+      a.k = k;
+      a.noise = nz;
+      a.clock = h->clock;
+      a.parity = h->parity;
+      e = launch_rk4_step_f32(h->m, a, h->stream, h->p.tile);
+    } else {
+      StepArgs<double> a;
+      a.geo = h->geo;
+      a.psi_in = static_cast<const double2*>(h->psi[h->cur]);
+      a.psi_out = static_cast<double2*>(h->psi[h->cur ^ 1]);
+      a.n_in = static_cast<const double*>(h->n[h->cur]);
+      a.n_out = static_cast<double*>(h->n[h->cur ^ 1]);
+      a.P = static_cast<const double*>(h->P);
+      a.P_comp_stride = h->P_stride;
+      a.V = h->has_V ? static_cast<const double*>(h->V) : nullptr;
+      a.k = k;
+      a.noise = nz;
+      a.clock = h->clock;
+      a.parity = h->parity;
+      e = launch_rk4_step_f64(h->m, a, h->stream, h->p.tile);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "rk4 step launch");
+    h->cur ^= 1;
+    h->parity ^= 1;
+    h->host_step += 1;
+  }
+  return PHX_OK;
+}
+
+phx_status phx_norm_energy(phx_handle* h, double* norm, double* energy) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  DeviceGuard dg(h->device);
+  ReduceArgs r = make_reduce_args(h);
+  PHX_CK(h, launch_norm_energy(r, h->partials, h->red_dev, h->stream));
+  PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 2 * sizeof(double),
+                            cudaMemcpyDeviceToHost, h->stream));
+  PHX_CK(h, cudaStreamSynchronize(h->stream));
+  const double dV = (h->p.lx / h->p.nx) * (h->p.ly / h->p.ny);
+  double N = dV * h->red_host[0], E = dV * h->red_host[1];
+  if (norm) *norm = N;
+  if (energy) *energy = E;
+  if (!is_finite(N) || !is_finite(E)) return fail(h, PHX_ENONFINITE, "state holds NaN or Inf");
+  return PHX_OK;
+}
+
+phx_status phx_residual(phx_handle* h, double* r_psi, double* r_n, double* omega) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  DeviceGuard dg(h->device);
+  ReduceArgs r = make_reduce_args(h);
+  PHX_CK(h, launch_residual(r, h->partials, h->red_dev, h->stream));
+  PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 8 * sizeof(double),
+                            cudaMemcpyDeviceToHost, h->stream));
+  PHX_CK(h, cudaStreamSynchronize(h->stream));
+  const double* o = h->red_host;
+  double rp = o[0] > 0.0 ? std::sqrt(o[5] / o[0]) : 0.0;
+  double rn = 0.0;
+  if (h->m.reservoir) rn = o[4] > 0.0 ? std::sqrt(o[3] / o[4]) : (o[3] == 0.0 ? 0.0 : INFINITY);
+  if (r_psi) *r_psi = rp;
+  if (r_n) *r_n = rn;
+  if (omega) *omega = o[6];
+  for (int q = 0; q < 7; ++q)
+    if (!is_finite(o[q])) return fail(h, PHX_ENONFINITE, "state holds NaN or Inf");
+  return PHX_OK;
+}
+
+phx_status phx_time(phx_handle* h, int64_t* step, double* t) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  DeviceGuard dg(h->device);
+  DevClock c;
+  PHX_CK(h, cudaMemcpyAsync(&c, h->clock, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+  PHX_CK(h, cudaStreamSynchronize(h->stream));
+  if (step) *step = c.step[h->parity];
+  if (t) *t = c.t[h->parity];
+  return PHX_OK;
+}
+
+phx_status phx_set_time(phx_handle* h, int64_t step, double t) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  if (step < 0 || !is_finite(t)) return fail(h, PHX_EINVAL, "step must be >= 0 and t finite");
+  DeviceGuard dg(h->device);
+  DevClock c;
+  c.step[0] = c.step[1] = step;
+  c.t[0] = c.t[1] = t;
+  PHX_CK(h, cudaMemcpyAsync(h->clock, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+  PHX_CK(h, cudaStreamSynchronize(h->stream));
+  h->host_step = step;
+  return PHX_OK;
+}
+
+phx_status phx_set_stream(phx_handle* h, void* stream) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->p.stream = stream;
+  return PHX_OK;
+}
+
+uint64_t phx_launch_count(void) { return phx::launch_total(); }
+
+const char* phx_last_error(const phx_handle* h) {
+  if (h) return h->err.c_str();
+  return g_err.c_str();
+}
+
+const char* phx_status_string(phx_status s) {
+  switch (s) {
+    case PHX_OK: return "PHX_OK";
+    case PHX_EINVAL: return "PHX_EINVAL";
+    case PHX_ENOMEM: return "PHX_ENOMEM";
+    case PHX_ECUDA: return "PHX_ECUDA";
+    case PHX_ENONFINITE: return "PHX_ENONFINITE";
+    case PHX_ETIMEOUT: return "PHX_ETIMEOUT";
+    case PHX_ESTATE: return "PHX_ESTATE";
+    case PHX_ENODEV: return "PHX_ENODEV";
+  }
+  return "PHX_UNKNOWN";
+}
+
+void phx_destroy(phx_handle* h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+phx_status phx_noise_sample(uint64_t seed, int64_t step, uint32_t instance,
+                            int32_t ncomp, int32_t nx, int32_t ny,
+                            double noise_var, float* out_device, void* stream) {
+  if (!out_device) return fail(nullptr, PHX_EINVAL, "out_device is NULL");
+  if (ncomp != 1 && ncomp != 2) return fail(nullptr, PHX_EINVAL, "ncomp must be 1 or 2");
+  if (nx < 1 || ny < 1 || (long long)nx * ny > (1ll << 31) - 1)
+    return fail(nullptr, PHX_EINVAL, "bad nx, ny");
+  if (!(noise_var >= 0) || !is_finite(noise_var)) return fail(nullptr, PHX_EINVAL, "bad noise_var");
+  float scale = (float)std::sqrt(noise_var / 2.0);
+  cudaError_t e = launch_noise_sample(seed, step, instance, ncomp, nx, ny, scale,
+                                      out_device, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "noise sample launch");
+  return PHX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Internal declarations shared by the host runtime and the kernels.
+// Device layout of every field: ncomp planes of (ny + 2*HALO) rows x pitch
+// columns, domain site (i, j) stored at row j + HALO, column i + HALO.  The
+// HALO-wide ghost ring holds periodic images (periodic axis) or zeros (zero
+// axis), so that a tile with a depth-HALO halo is one rectangular box.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace phx {
+
+constexpr int HALO = 4;       // RK4 needs a depth-4 halo (one cell per stage)
+constexpr int PITCH_ALIGN = 32;
+constexpr double HBAR = 0.6582119569;  // meV ps (CODATA 2018)
+constexpr int BC_PERIODIC = 0;
+constexpr int BC_ZERO = 1;
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+// Step counter and FP64 simulated time, double-buffered by step parity so a
+// launch can read slot p and write slot p^1 without a grid-wide barrier.
+struct DevClock {
+  long long step[2];
+  double t[2];
+};
+
+struct Geometry {
+  int nx, ny;        // domain
+  int pitch;         // padded row length (elements)
+  int prow;          // padded rows = ny + 2*HALO
+  long long plane;   // pitch * prow
+  int bc_x, bc_y;
+};
+
+// Coefficients of one RK4 step, pre-scaled by 1/hbar (units ps^-1).
+struct Coeffs {
+  double ax, ay, a0;      // -(k/h)/dx^2, -(k/h)/dy^2, 2(k/h)(1/dx^2 + 1/dy^2)
+  double g, gx, gr;       // g/h, g_x/h, g_r/h
+  double inv_hbar;        // multiplies V
+  double half_R, half_gc; // R/2, gamma_c/2
+  double R, gamma_r;
+  double tx, ty, txy;     // Delta/(h dx^2), Delta/(h dy^2), Delta/(2 h dx dy)
+  double dt;
+};
+
+struct NoiseKey {
+  unsigned long long seed;
+  unsigned int instance;
+  int on;
+  float scale;            // float32(sqrt(var/2))
+};
+
+template <typename R>
+struct StepArgs {
+  Geometry geo;
+  const typename Cx<R>::T* psi_in;
+  typename Cx<R>::T* psi_out;
+  const R* n_in;
+  R* n_out;
+  const R* P;             // ncomp planes (plane 1 may alias plane 0)
+  long long P_comp_stride;
+  const R* V;             // nullptr when absent
+  Coeffs k;
+  NoiseKey noise;
+  DevClock* clock;
+  int parity;
+};
+
+struct ModelKey {
+  int precision;  // 32 | 64
+  int ncomp;      // 1 | 2
+  int reservoir;  // 0 | 1
+  int tetm;       // 0 | 1
+};
+
+// ---- launchers (return cudaGetLastError() after the launch) -------------
+cudaError_t launch_rk4_step_f32(const ModelKey& m, const StepArgs<float>& a,
+                                cudaStream_t s, int tile);
+cudaError_t launch_rk4_step_f64(const ModelKey& m, const StepArgs<double>& a,
+                                cudaStream_t s, int tile);
+
+// Fill the ghost ring of `nplanes` planes of element size `esize` bytes.
+cudaError_t launch_fill_ghosts(void* base, int esize, int nplanes,
+                               const Geometry& g, cudaStream_t s);
+
+// Reductions in FP64.  `partials` is device scratch of reduce_partials_len()
+// doubles; `out` receives the final sums on the device.
+int reduce_blocks(const Geometry& g);
+size_t reduce_partials_len(const Geometry& g);
+
+struct ReduceArgs {
+  Geometry geo;
+  const void* psi;   // padded, precision 32 or 64
+  const void* n;     // may be nullptr
+  const void* P;
+  long long P_comp_stride;
+  const void* V;
+  double idx2, idy2, ixy4;   // 1/dx^2, 1/dy^2, 1/(4 dx dy)
+  double kappa, g, g_x, g_r, delta_lt, R, gamma_c, gamma_r;  // physical units
+  int precision, ncomp, reservoir, tetm;
+};
+
+// out[0] = sum |psi|^2, out[1] = sum of the energy density (both without dV)
+cudaError_t launch_norm_energy(const ReduceArgs& a, double* partials,
+                               double* out, cudaStream_t s);
+// Two passes: out[0]=S_pp, out[1]=Re S_pK, out[2]=Im S_pK, out[3]=S_fn,
+// out[4]=S_nn, out[5]=sum|K + i omega psi|^2, out[6]=omega, out[7]=nonfinite
+cudaError_t launch_residual(const ReduceArgs& a, double* partials, double* out,
+                            cudaStream_t s);
+
+cudaError_t launch_noise_sample(unsigned long long seed, long long step,
+                                unsigned int instance, int ncomp, int nx,
+                                int ny, float scale, float* out,
+                                cudaStream_t s);
+
+// Process-wide count of kernel launches issued by this library.
+void count_launch(unsigned n = 1);
+
+}  // namespace phx

@@ -1,0 +1,21 @@
+// FP32 instantiations of the fused RK4 step.
+#include "rk4_generic.cuh"
+
+namespace phx {
+
+cudaError_t launch_rk4_step_f32(const ModelKey& m, const StepArgs<float>& a,
+                                cudaStream_t s, int tile) {
+  (void)tile;
+  if (m.ncomp == 1) {
+    if (m.reservoir) return launch_generic<float, 1, true, false, 32, 32, 256>(a, s);
+    return launch_generic<float, 1, false, false, 32, 32, 256>(a, s);
+  }
+  if (m.tetm) {
+    if (m.reservoir) return launch_generic<float, 2, true, true, 32, 16, 256>(a, s);
+    return launch_generic<float, 2, false, true, 32, 16, 256>(a, s);
+  }
+  if (m.reservoir) return launch_generic<float, 2, true, false, 32, 16, 256>(a, s);
+  return launch_generic<float, 2, false, false, 32, 16, 256>(a, s);
+}
+
+}  // namespace phx

@@ -1,0 +1,21 @@
+// FP64 instantiations of the fused RK4 step.
+#include "rk4_generic.cuh"
+
+namespace phx {
+
+cudaError_t launch_rk4_step_f64(const ModelKey& m, const StepArgs<double>& a,
+                                cudaStream_t s, int tile) {
+  (void)tile;
+  if (m.ncomp == 1) {
+    if (m.reservoir) return launch_generic<double, 1, true, false, 16, 16, 128>(a, s);
+    return launch_generic<double, 1, false, false, 16, 16, 128>(a, s);
+  }
+  if (m.tetm) {
+    if (m.reservoir) return launch_generic<double, 2, true, true, 16, 16, 128>(a, s);
+    return launch_generic<double, 2, false, true, 16, 16, 128>(a, s);
+  }
+  if (m.reservoir) return launch_generic<double, 2, true, false, 16, 16, 128>(a, s);
+  return launch_generic<double, 2, false, false, 16, 16, 128>(a, s);
+}
+
+}  // namespace phx

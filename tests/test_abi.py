@@ -1,0 +1,98 @@
+"""C-ABI library: loads, exports every symbol include/phx.h declares, and its
+host-only logic (parameter validation, stability limit) agrees with the
+oracle.  No compute call needs a GPU here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from oracle import gp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def phx():
+    __graft_entry__.build()
+    import paper_2411_18341_gb300 as m
+    return m
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        names += re.findall(r"\b(phx_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_boundary(phx):
+    names = declared_functions()
+    for must in ("phx_create", "phx_set_pump", "phx_step_n", "phx_norm_energy",
+                 "phx_destroy", "phx_residual", "phx_set_state", "phx_get_state"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(phx):
+    L = ctypes.CDLL(phx.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_params_struct_layout_matches_c(phx):
+    p = phx.phx_params_init()
+    assert p.struct_size == ctypes.sizeof(phx.phx_params)
+    assert p.nx == 64 and p.precision == 32 and p.hbar2_over_2m == 0.67
+
+
+CASES = [
+    dict(nx=64, ny=64, lx=20.0, ly=20.0),
+    dict(nx=37, ny=29, lx=11.1, ly=8.7, bc_x=1),
+    dict(nx=10, ny=12, lx=3.0, ly=3.3, bc_x=1, bc_y=1),
+    dict(nx=33, ny=16, lx=5.0, ly=4.0, spinor=True, delta_lt=0.4),
+    dict(nx=24, ny=24, lx=6.0, ly=6.0, spinor=True, delta_lt=0.025, bc_y=1),
+    dict(nx=2048, ny=2048, lx=200.0, ly=200.0, spinor=True, delta_lt=0.025),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_stability_dt_matches_oracle(phx, case):
+    p = gp.Params(**case)
+    kw = dict(case)
+    kw["spinor"] = int(kw.get("spinor", False))
+    got = phx.phx_stability_dt(phx.phx_params_init(**kw))
+    assert abs(got - gp.stability_dt_max(p)) <= 1e-12 * got
+
+
+def test_invalid_params_rejected_before_device(phx):
+    bad = [dict(nx=0), dict(ny=-3), dict(lx=0.0), dict(bc_x=2), dict(precision=16),
+           dict(g_x=0.1), dict(delta_lt=0.1), dict(noise_var=-1.0),
+           dict(dt=0.0), dict(dt=1.0), dict(g=float("nan")), dict(spinor=2)]
+    for kw in bad:
+        base = dict(nx=16, ny=16, lx=4.0, ly=4.0, dt=1e-3)
+        base.update(kw)
+        with pytest.raises(phx.PhxError) as e:
+            phx.phx_create(phx.phx_params_init(**base))
+        assert e.value.status == 1, (kw, e.value)
+
+
+def test_struct_size_checked(phx):
+    p = phx.phx_params_init(dt=1e-3)
+    p.struct_size = 8
+    with pytest.raises(phx.PhxError) as e:
+        phx.phx_create(p)
+    assert e.value.status == 1
+
+
+def test_status_strings(phx):
+    L = phx.lib()
+    assert L.phx_status_string(0) == b"PHX_OK"
+    assert L.phx_status_string(5) == b"PHX_ETIMEOUT"
+    assert L.phx_last_error(None)

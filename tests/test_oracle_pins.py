@@ -430,3 +430,20 @@ def test_derived_constants_file_matches_oracle():
     # dx = 0.3125, lambda = 0.67 * 8 / dx^2 meV
     assert abs(c["conservative_64"]["dt"] - 0.5 * 2 * np.sqrt(2) * HB / (0.67 * 8 / 0.3125 ** 2)) < 1e-15
     assert c["pump_threshold"] == pytest.approx(0.15 * 0.225 / 0.01)
+
+
+@pytest.mark.parametrize("bc", [gp.PERIODIC, gp.ZERO])
+def test_windowed_step_equals_full_grid_step(bc):
+    """oracle.gp.step_at_sites (used for sampled parity at full size) equals
+    the full-grid step at every sampled site, including edges and corners."""
+    p = gp.Params(nx=23, ny=19, lx=7.0, ly=6.0, bc_x=bc, bc_y=gp.PERIODIC,
+                  spinor=True, reservoir=True, g=0.2, g_x=0.05, g_r=0.1, R=0.05,
+                  gamma_c=0.1, gamma_r=0.2, delta_lt=0.07, noise_var=1e-3, seed=4)
+    p = p.with_(dt=0.4 * gp.stability_dt_max(p))
+    psi, n, P, V = synth.random_state(2, 19, 23, 9)
+    full_psi, full_n = gp.run(psi, n, P, V, p, 1, step0=3)
+    sites = [(0, 0), (18, 22), (0, 22), (9, 11), (5, 0), (18, 3)]
+    sp, sn = gp.step_at_sites(psi, n, P, V, p, sites, step=3)
+    for k, (j, i) in enumerate(sites):
+        assert np.allclose(sp[:, k], full_psi[:, j, i], rtol=0, atol=1e-13)
+        assert np.allclose(sn[:, k], full_n[:, j, i], rtol=0, atol=1e-13)
