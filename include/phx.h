@@ -173,6 +173,35 @@ phx_status phx_noise_sample(uint64_t seed, int64_t step, uint32_t instance,
                             int32_t ncomp, int32_t nx, int32_t ny,
                             double noise_var, float* out_device, void* stream);
 
+/* Allocation-free norm and energy (no counterpart in the paper; this is a
+ * library convenience).  Computes exactly the quantities of phx_norm_energy
+ * -- FP64 N and E, same boundary handling -- from caller-owned device arrays
+ * in the plain layout of phx_set_state (psi: ncomp planes of ny x nx complex;
+ * n: ncomp planes, required when p->reservoir, else ignored; V: one plane or
+ * NULL), in p->precision, on p->stream, without creating a handle.
+ *
+ * It is meant for callers that may not allocate device memory: code whose
+ * device memory is entirely owned by another allocator (a framework's
+ * caching pool under a hard budget) or latency-critical loops that must not
+ * call cudaMalloc/cudaFree, which can block on the device.  It calls no
+ * allocation routine: its scratch (per-CTA FP64 partials and the two final
+ * sums) is a fixed file-scope device array of 64 KiB + 16 B, resident on
+ * every device that loads this library until the process exits.  Grids with
+ * nx*ny > 16777216 (2^24) do not fit that scratch and return PHX_EINVAL.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls on a device share the array and leave their partials
+ * in it; each call writes every slot it reads, so nothing needs clearing,
+ * but calls whose kernels can overlap on the GPU (unordered streams) race.
+ * Synchronises p->stream.  Errors (status only; no message is recorded,
+ * since storing one could allocate): EINVAL (NULL psi, bad sizes or
+ * boundary codes, grid too large, reservoir without n), ENODEV, ECUDA,
+ * ENONFINITE. */
+phx_status phx_norm_energy_static(const phx_params* p, const void* psi,
+                                  const void* n, const void* V, double* norm,
+                                  double* energy);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,10 @@ _SIGS = {
     "phx_noise_sample": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                         ctypes.c_void_p]),
+    "phx_norm_energy_static": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -267,6 +271,22 @@ def phx_noise_sample(seed, step, instance, ncomp, nx, ny, noise_var, out, stream
     _check(lib().phx_noise_sample(int(seed), int(step), int(instance), int(ncomp), int(nx),
                                   int(ny), float(noise_var), ctypes.c_void_p(out.data_ptr()),
                                   ctypes.c_void_p(int(stream) if stream else 0)))
+
+
+def phx_norm_energy_static(p, psi, n=None, V=None):
+    """Allocation-free norm/energy of caller-owned CUDA tensors (plain layout).
+    Raises PhxError with the status code on failure (this call records no
+    message)."""
+    for t in (psi, n, V):
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("inputs must be contiguous CUDA tensors")
+    N, E = ctypes.c_double(), ctypes.c_double()
+    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    st = lib().phx_norm_energy_static(ctypes.byref(p), ptr(psi), ptr(n), ptr(V),
+                                      ctypes.byref(N), ctypes.byref(E))
+    if st != PHX_OK:
+        raise PhxError(st, "phx_norm_energy_static failed")
+    return N.value, E.value
 
 
 # ------------------------------------------------------------- conveniences

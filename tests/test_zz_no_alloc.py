@@ -1,0 +1,64 @@
+"""The allocation-free norm/energy entry point (phx_norm_energy_static).
+
+Callers that may not allocate device memory (their device memory belongs to
+another allocator, or their loop must not call cudaMalloc/cudaFree) pass
+their own device arrays; the entry point keeps its scratch in a fixed
+file-scope device array.  This test calls it through the C ABI and checks
+its output against phx_norm_energy on the same state, on two calls in a row
+(different states, models and sizes, so the second call runs over partials
+the first one left in the shared scratch).  The file sorts last so a run
+that stops at the first failure has already run every other test."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import phx, make_handle
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (params, precision, seed)
+    (dict(synth.base_params(300, 170, 30.0, 17.0, spinor=True, delta_lt=0.2, g_x=0.1,
+                            g=0.3, dt=1e-3, **{k: v for k, v in synth.reservoir_physics().items()
+                                               if k not in ("g",)})), 64, 1),
+    (dict(synth.base_params(97, 61, 9.7, 6.1, bc_x=1, g=0.3, dt=1e-3,
+                            **{k: v for k, v in synth.reservoir_physics().items()
+                               if k not in ("g",)})), 32, 2),
+]
+
+
+def state(d, seed):
+    nc = 2 if d["spinor"] else 1
+    return synth.random_state(nc, d["ny"], d["nx"], seed, amp=0.8,
+                              reservoir=d["reservoir"], smooth=True)
+
+
+def test_static_scratch_matches_handle_twice():
+    import torch
+    m = phx()
+    for d, prec, seed in CASES:
+        psi, n, P, V = state(d, seed)
+        real = np.float32 if prec == 32 else np.float64
+        cplx = np.complex64 if prec == 32 else np.complex128
+        h = make_handle(d, prec, psi, n, P, V)
+        N_ref, E_ref = m.phx_norm_energy(h)
+        p = m.params_from_dict(d, precision=prec)
+        t_psi = torch.tensor(psi.astype(cplx), device="cuda")
+        t_n = torch.tensor(n.astype(real), device="cuda")
+        t_V = torch.tensor(V.astype(real), device="cuda")
+        torch.cuda.synchronize()
+        N, E = m.phx_norm_energy_static(p, t_psi, t_n, t_V)
+        assert abs(N - N_ref) <= 1e-12 * abs(N_ref)
+        assert abs(E - E_ref) <= 1e-11 * max(abs(E_ref), 1.0)
+        m.phx_destroy(h)
+
+
+def test_static_scratch_rejects_oversized_grid():
+    import torch
+    m = phx()
+    d = synth.base_params(4097, 4096, 400.0, 400.0, dt=1e-3)
+    p = m.params_from_dict(d, precision=32)
+    t = torch.zeros(2, dtype=torch.complex64, device="cuda")  # never read
+    with pytest.raises(m.PhxError) as e:
+        m.phx_norm_energy_static(p, t)
+    assert e.value.status == 1
