@@ -69,7 +69,9 @@ typedef struct phx_params {
   int32_t precision;         /* 32 or 64: stencil arithmetic and storage */
   int32_t spinor;            /* 0: scalar psi; 1: two components psi_+, psi_- */
   int32_t reservoir;         /* 0/1: evolve n_c with Eq. (PULSE_res) */
-  int32_t tile;              /* 0 = automatic tile shape; otherwise a tile id */
+  int32_t tile;              /* FP32 scalar step kernel tile: 0 = automatic,
+                                1 = 64x64, 2 = 64x48, 3 = 64x32 region (TMA-fed
+                                persistent kernel), 9 = generic kernel */
   double hbar2_over_2m;      /* hbar^2/2m, meV um^2 */
   double g, g_x, g_r;        /* meV um^2 */
   double R;                  /* ps^-1 um^2 */
@@ -154,6 +156,21 @@ phx_status phx_set_stream(phx_handle* h, void* stream);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t phx_launch_count(void);
+
+/* Failure-injection hook for tests (no counterpart in the paper).  Arms, for
+ * the next matching event in this process, one of:
+ *   PHX_INJECT_ALLOC   -- the next device allocation in phx_create fails
+ *                         (phx_create returns PHX_ENOMEM, nothing leaks);
+ *   PHX_INJECT_LAUNCH  -- the next step launch reports failure (PHX_ECUDA);
+ *   PHX_INJECT_TIMEOUT -- the next launch of the TMA-fed FP32 step kernel
+ *                         leaves its first tile's mbarrier unarmed, so the
+ *                         kernel's bounded wait (~0.25 s) gives up, it sets
+ *                         the handle's device error word and returns; the
+ *                         next synchronising call returns PHX_ETIMEOUT and
+ *                         the handle stays usable (state must be reset).
+ * No hook faults, traps or hangs the GPU.  EINVAL on unknown bits. */
+enum { PHX_INJECT_ALLOC = 1, PHX_INJECT_LAUNCH = 2, PHX_INJECT_TIMEOUT = 4 };
+phx_status phx_debug_inject(uint32_t mask);
 
 /* Message of the last error on h (h = NULL: last error of a call without a
  * handle on this thread).  Never NULL. */

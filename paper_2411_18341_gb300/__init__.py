@@ -72,6 +72,7 @@ _SIGS = {
     "phx_set_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
     "phx_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "phx_launch_count": (ctypes.c_uint64, []),
+    "phx_debug_inject": (ctypes.c_int, [ctypes.c_uint32]),
     "phx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "phx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "phx_destroy": (None, [ctypes.c_void_p]),
@@ -252,6 +253,13 @@ def phx_set_stream(h, stream):
 
 def phx_launch_count():
     return int(lib().phx_launch_count())
+
+
+INJECT_ALLOC, INJECT_LAUNCH, INJECT_TIMEOUT = 1, 2, 4
+
+
+def phx_debug_inject(mask):
+    _check(lib().phx_debug_inject(int(mask)))
 
 
 def phx_last_error(h=None):

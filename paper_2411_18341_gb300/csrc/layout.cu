@@ -7,6 +7,16 @@
 namespace phx {
 
 static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<unsigned> g_inject{0};
+
+bool take_injection(unsigned what) {
+  unsigned cur = g_inject.load();
+  while (cur & what) {
+    if (g_inject.compare_exchange_weak(cur, cur & ~what)) return true;
+  }
+  return false;
+}
+void arm_injection(unsigned mask) { g_inject.fetch_or(mask); }
 void count_launch(unsigned n) { g_launches.fetch_add(n); }
 unsigned long long launch_total() { return g_launches.load(); }
 

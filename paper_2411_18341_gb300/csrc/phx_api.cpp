@@ -12,9 +12,11 @@
 
 #include "../../include/phx.h"
 #include "phx_internal.h"
+#include "rk4_tma.h"
 
 namespace phx {
 unsigned long long launch_total();
+void arm_injection(unsigned mask);
 }
 
 using namespace phx;
@@ -39,6 +41,12 @@ struct phx_handle {
   long long host_step = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
+  int num_sms = 0;
+  int* err_dev = nullptr;      // set by kernels whose bounded waits gave up
+  int tile_cfg = 0;            // chosen tile configuration of the FP32 scalar kernel
+  bool maps_ok = false;        // TMA tensor maps encoded for (tile_cfg, has_V)
+  bool maps_V = false;
+  TmaMaps maps[2];             // per current-state buffer
   std::string err;
 };
 
@@ -160,6 +168,7 @@ void free_all(phx_handle* h) {
   if (h->partials) cudaFree(h->partials);
   if (h->red_dev) cudaFree(h->red_dev);
   if (h->red_host) cudaFreeHost(h->red_host);
+  if (h->err_dev) cudaFree(h->err_dev);
   cudaSetDevice(prev);
 }
 
@@ -244,6 +253,66 @@ ReduceArgs make_reduce_args(const phx_handle* h) {
   return r;
 }
 
+// Tile configuration of the persistent FP32 scalar kernel: the one with the
+// smallest modelled time = (rounds of tiles over the SMs) x (region area).
+int choose_tile(const phx_handle* h) {
+  if (h->p.tile != 0) return h->p.tile;
+  int best = TILE_64x64;
+  double best_cost = 1e300;
+  for (int cfg : {TILE_64x64, TILE_64x48, TILE_64x32}) {
+    TmaBox b = tma_box(cfg);
+    long long tx = (h->p.nx + 1 + b.tx - 1) / b.tx, ty = (h->p.ny + b.ty - 1) / b.ty;
+    long long rounds = (tx * ty + h->num_sms - 1) / h->num_sms;
+    double cost = (double)rounds * (b.tx + 6) * (b.ty + 6);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = cfg;
+    }
+  }
+  return best;
+}
+
+bool encode_maps(phx_handle* h) {
+  const Geometry& g = h->geo;
+  TmaBox b = tma_box(h->tile_cfg);
+  const int nc = h->m.ncomp;
+  for (int k = 0; k < 2; ++k) {
+    TmaMaps& m = h->maps[k];
+    std::memset(&m, 0, sizeof m);
+    if (!encode_map_f32(&m.psi, h->psi[k], 2ull * g.pitch, g.prow, nc, (unsigned long long)g.pitch * 8,
+                        (unsigned long long)g.plane * 8, b.psi_w, b.psi_h))
+      return false;
+    if (h->m.reservoir) {
+      if (!encode_map_f32(&m.n, h->n[k], g.pitch, g.prow, nc, (unsigned long long)g.pitch * 4,
+                          (unsigned long long)g.plane * 4, b.f_w, b.f_h))
+        return false;
+      if (!encode_map_f32(&m.P, h->P, g.pitch, g.prow, nc, (unsigned long long)g.pitch * 4,
+                          (unsigned long long)g.plane * 4, b.f_w, b.f_h))
+        return false;
+    }
+    if (h->has_V) {
+      if (!encode_map_f32(&m.V, h->V, g.pitch, g.prow, 1, (unsigned long long)g.pitch * 4,
+                          (unsigned long long)g.plane * 4, b.f_w, b.f_h))
+        return false;
+    }
+  }
+  h->maps_ok = true;
+  h->maps_V = h->has_V;
+  return true;
+}
+
+// Reads and clears the device error word (synchronises the stream).
+phx_status check_device_error(phx_handle* h) {
+  int e = 0;
+  PHX_CK(h, cudaMemcpyAsync(&e, h->err_dev, sizeof e, cudaMemcpyDeviceToHost, h->stream));
+  PHX_CK(h, cudaStreamSynchronize(h->stream));
+  if (e) {
+    PHX_CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
+    return fail(h, PHX_ETIMEOUT, "a bounded wait in the step kernel gave up (TMA copy did not complete)");
+  }
+  return PHX_OK;
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -308,6 +377,7 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
   if (!h) return fail(nullptr, PHX_ENOMEM, "host allocation failed");
   h->p = *p;
   h->device = dev;
+  h->num_sms = prop.multiProcessorCount;
   h->stream = static_cast<cudaStream_t>(p->stream);
   h->m.precision = p->precision;
   h->m.ncomp = p->spinor ? 2 : 1;
@@ -324,6 +394,7 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
   g.bc_y = p->bc_y;
 
   auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+    if (take_injection(INJ_ALLOC)) return cudaErrorMemoryAllocation;
     cudaError_t r = cudaMalloc(ptr, bytes);
     if (r != cudaSuccess) return r;
     return cudaMemsetAsync(*ptr, 0, bytes, h->stream);
@@ -344,6 +415,7 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
     ce = alloc((void**)&h->partials, reduce_partials_len(g) * sizeof(double));
   if (ce == cudaSuccess) ce = alloc((void**)&h->red_dev, 8 * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&h->red_host, 8 * sizeof(double));
+  if (ce == cudaSuccess) ce = alloc((void**)&h->err_dev, sizeof(int));
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
   if (ce != cudaSuccess) {
     cudaGetLastError();
@@ -352,6 +424,7 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
     delete h;
     return fail(nullptr, ce == cudaErrorMemoryAllocation ? PHX_ENOMEM : PHX_ECUDA, msg);
   }
+  h->tile_cfg = (p->precision == 32 && !p->spinor) ? choose_tile(h) : TILE_GENERIC;
   *out = h;
   return PHX_OK;
 }
@@ -423,7 +496,7 @@ phx_status phx_get_state(phx_handle* h, void* psi, void* n, int on_device) {
     if (st != PHX_OK) return st;
   }
   PHX_CK(h, cudaStreamSynchronize(h->stream));
-  return PHX_OK;
+  return check_device_error(h);
 }
 
 phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
@@ -438,6 +511,9 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
   nz.scale = (float)std::sqrt(h->p.noise_var / 2.0);
   for (int64_t s = 0; s < nsteps; ++s) {
     cudaError_t e;
+    if (take_injection(INJ_LAUNCH))
+      return fail(h, PHX_ECUDA, "rk4 step launch: injected launch failure");
+    const int inj = take_injection(INJ_TIMEOUT) ? 1 : 0;
     if (h->m.precision == 32) {
       StepArgs<float> a;
       a.geo = h->geo;
@@ -452,7 +528,16 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.noise = nz;
       a.clock = h->clock;
       a.parity = h->parity;
-      e = launch_rk4_step_f32(h->m, a, h->stream, h->p.tile);
+      a.inject_timeout = inj;
+      if (h->tile_cfg != TILE_GENERIC && h->m.ncomp == 1) {
+        if (!h->maps_ok || h->maps_V != h->has_V) {
+          if (!encode_maps(h)) return fail(h, PHX_ECUDA, "cuTensorMapEncodeTiled failed");
+        }
+        e = launch_rk4_tma_f32(h->tile_cfg, h->m.reservoir, h->has_V, h->maps[h->cur], a,
+                               h->stream, h->err_dev, h->num_sms);
+      } else {
+        e = launch_rk4_step_f32(h->m, a, h->stream, h->p.tile);
+      }
     } else {
       StepArgs<double> a;
       a.geo = h->geo;
@@ -467,6 +552,7 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.noise = nz;
       a.clock = h->clock;
       a.parity = h->parity;
+      a.inject_timeout = 0;
       e = launch_rk4_step_f64(h->m, a, h->stream, h->p.tile);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "rk4 step launch");
@@ -485,6 +571,10 @@ phx_status phx_norm_energy(phx_handle* h, double* norm, double* energy) {
   PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 2 * sizeof(double),
                             cudaMemcpyDeviceToHost, h->stream));
   PHX_CK(h, cudaStreamSynchronize(h->stream));
+  {
+    phx_status es = check_device_error(h);
+    if (es != PHX_OK) return es;
+  }
   const double dV = (h->p.lx / h->p.nx) * (h->p.ly / h->p.ny);
   double N = dV * h->red_host[0], E = dV * h->red_host[1];
   if (norm) *norm = N;
@@ -501,6 +591,10 @@ phx_status phx_residual(phx_handle* h, double* r_psi, double* r_n, double* omega
   PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 8 * sizeof(double),
                             cudaMemcpyDeviceToHost, h->stream));
   PHX_CK(h, cudaStreamSynchronize(h->stream));
+  {
+    phx_status es = check_device_error(h);
+    if (es != PHX_OK) return es;
+  }
   const double* o = h->red_host;
   double rp = o[0] > 0.0 ? std::sqrt(o[5] / o[0]) : 0.0;
   double rn = 0.0;
@@ -545,6 +639,12 @@ phx_status phx_set_stream(phx_handle* h, void* stream) {
 }
 
 uint64_t phx_launch_count(void) { return phx::launch_total(); }
+
+phx_status phx_debug_inject(uint32_t mask) {
+  if (mask & ~7u) return fail(nullptr, PHX_EINVAL, "unknown injection bits");
+  phx::arm_injection(mask);
+  return PHX_OK;
+}
 
 const char* phx_last_error(const phx_handle* h) {
   if (h) return h->err.c_str();

@@ -67,6 +67,7 @@ struct StepArgs {
   NoiseKey noise;
   DevClock* clock;
   int parity;
+  int inject_timeout;     // test hook: leave the first tile's barrier unarmed
 };
 
 struct ModelKey {
@@ -115,6 +116,10 @@ cudaError_t launch_noise_sample(unsigned long long seed, long long step,
                                 unsigned int instance, int ncomp, int nx,
                                 int ny, float scale, float* out,
                                 cudaStream_t s);
+
+// Test hooks armed by phx_debug_inject (consumed by the next matching event).
+enum { INJ_ALLOC = 1, INJ_LAUNCH = 2, INJ_TIMEOUT = 4 };
+bool take_injection(unsigned what);
 
 // Process-wide count of kernel launches issued by this library.
 void count_launch(unsigned n = 1);

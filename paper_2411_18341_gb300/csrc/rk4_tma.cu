@@ -1,0 +1,435 @@
+// Persistent, TMA-fed fused RK4 step for the FP32 scalar field (Eq. 1 /
+// Eq. PULSE_psi with one component, optionally with the reservoir of
+// Eq. PULSE_res and a potential V).
+//
+// Per CTA (one per SM, 32*WY threads) a loop over output tiles:
+//   * the next tile's psi box (tile + depth-4 halo) and its n, P, V boxes are
+//     fetched by cp.async.bulk.tensor into the other half of a double buffer
+//     while the current tile is computed (mbarrier completion, bounded waits);
+//   * thread (lane, warp) owns a 2-column x MR-row micro-tile of the ring-3
+//     region: psi0, the running stage value, the accumulator sum_k w_k K_k and
+//     the reservoir values stay in registers across the four stages; only the
+//     micro-tile's neighbours cross shared memory (16-byte row loads above and
+//     below, 8-byte column loads left and right, one 16-byte store per row);
+//   * complex arithmetic uses the packed FP32x2 instructions of sm_100+
+//     (__ffma2_rn / __fadd2_rn / __fmul2_rn on (re, im) pairs);
+//   * psi' = psi0 + (K1 + 2K2 + 2K3 + K4) dt/6 (+ noise) is stored with
+//     16-byte stores, plus the periodic ghost images near the domain edges.
+// Tiles are offset by one column (tile kx covers domain columns
+// [kx*TX - 1, kx*TX - 1 + TX)) so that every 16-byte alignment rule holds:
+// the psi box starts at an even padded column, micro-tile columns are even.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "phx_internal.h"
+#include "phx_noise.cuh"
+#include "rk4_generic.cuh"
+#include "rk4_tma.h"
+
+namespace phx {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of `bar`, giving up after ~0.25 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && global_ns() - t0 > 250000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <bool RES, bool POT, int MR, int WY>
+struct Cfg {
+  static constexpr int RW = 64;            // region (ring-3) columns: one warp x 2 cols
+  static constexpr int RH = MR * WY;       // region rows
+  static constexpr int TX = RW - 6, TY = RH - 6;
+  static constexpr int PW = RW + 4;        // psi smem row: 2 alignment cols, ring, region, ring
+  static constexpr int PH = RH + 2;        // psi smem rows: ring, region, ring
+  static constexpr int FW = RW + 4;        // n / P / V smem row (4-float aligned box)
+  static constexpr int NT = 32 * WY;
+  static constexpr int NF = (RES ? 2 : 0) + (POT ? 1 : 0);
+  static constexpr int PSI_BYTES = ((PH * PW * 8) + 127) / 128 * 128;
+  static constexpr int F_BYTES = ((RH * FW * 4) + 127) / 128 * 128;
+  static constexpr int BUF_BYTES = PSI_BYTES + NF * F_BYTES;
+  static constexpr int TX_BYTES = PH * PW * 8 + NF * RH * FW * 4;  // bytes one tile brings
+  static constexpr int SMEM = 2 * BUF_BYTES + PSI_BYTES + 128;
+};
+
+struct TileGeo {
+  int tiles_x, tiles_y, ntiles;
+};
+
+template <bool RES, bool POT, int MR, int WY>
+__global__ void __launch_bounds__(32 * WY, 1)
+rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
+            const __grid_constant__ CUtensorMap tm_n,
+            const __grid_constant__ CUtensorMap tm_P,
+            const __grid_constant__ CUtensorMap tm_V, const StepArgs<float> a,
+            const TileGeo tg, int* err) {
+  using C = Cfg<RES, POT, MR, WY>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float2* Y = reinterpret_cast<float2*>(base + 2 * C::BUF_BYTES);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = 2 * lane;   // region column of the micro-tile's first column
+  const int r0 = MR * warp;  // region row of its first row
+  const Geometry& g = a.geo;
+
+  auto psi_buf = [&](int b) { return reinterpret_cast<float2*>(base + b * C::BUF_BYTES); };
+  auto f_buf = [&](int b, int f) {
+    return reinterpret_cast<float*>(base + b * C::BUF_BYTES + C::PSI_BYTES + f * C::F_BYTES);
+  };
+
+  // Y ring cells are never written by the stages: give them a defined value.
+  for (int i = tid; i < C::PH * C::PW; i += C::NT) {
+    int r = i / C::PW, c = i - r * C::PW;
+    if (r == 0 || r == C::PH - 1 || c < 2 || c >= C::RW + 2) Y[i] = f2(0.f, 0.f);
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int t, int b) {
+    const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
+    const int xp = kx * C::TX;  // padded column of region column 0
+    const int yp = ky * C::TY;  // padded row of region row -1
+    mbar_arrive_expect_tx(&bar[b], C::TX_BYTES);
+    tma_load_3d(psi_buf(b), &tm_psi, 2 * (xp - 2), yp, 0, &bar[b]);
+    int f = 0;
+    if (RES) {
+      tma_load_3d(f_buf(b, f++), &tm_n, xp & ~3, yp + 1, 0, &bar[b]);
+      tma_load_3d(f_buf(b, f++), &tm_P, xp & ~3, yp + 1, 0, &bar[b]);
+    }
+    if (POT) tma_load_3d(f_buf(b, f++), &tm_V, xp & ~3, yp + 1, 0, &bar[b]);
+  };
+
+  const long long step = a.clock->step[a.parity];
+  if (blockIdx.x == 0 && tid == 0) {
+    a.clock->step[a.parity ^ 1] = step + 1;
+    a.clock->t[a.parity ^ 1] = a.clock->t[a.parity] + a.k.dt;
+  }
+
+  const Coeffs& q = a.k;
+  const float2 ax2 = f2((float)q.ax, (float)q.ax), ay2 = f2((float)q.ay, (float)q.ay);
+  const float2 a02 = f2((float)q.a0, (float)q.a0);
+  const float cg = (float)q.g, cgr = (float)q.gr, cih = (float)q.inv_hbar;
+  const float hR = (float)q.half_R, hgc = (float)q.half_gc, cR = (float)q.R;
+  const float cgam = (float)q.gamma_r, dt = (float)q.dt;
+  const float dt6 = dt / 6.0f;
+
+  int t = blockIdx.x, k = 0;
+  if (t < tg.ntiles && tid == 0 && !a.inject_timeout) issue(t, 0);
+  for (; t < tg.ntiles; t += gridDim.x, ++k) {
+    const int b = k & 1;
+    const uint32_t par = (uint32_t)((k >> 1) & 1);
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < tg.ntiles) {
+      fence_proxy_async();  // generic writes to buffer b^1 (previous tile) before TMA reuse
+      issue(tn, b ^ 1);
+    }
+    int fail = 0;
+    if (tid == 0) fail = !mbar_wait_bounded(&bar[b], par);
+    if (__syncthreads_or(fail)) {
+      if (tid == 0) {
+        atomicExch(err, 1);
+        if (tn < tg.ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+      }
+      return;
+    }
+    while (!mbar_try_wait(&bar[b], par)) {
+    }
+
+    const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
+    const int xp = kx * C::TX;
+    const int foff = xp & 3;
+    float2* P0 = psi_buf(b);
+    const float* Nb = RES ? f_buf(b, 0) : nullptr;
+    const float* Pb = RES ? f_buf(b, 1) : nullptr;
+    const float* Vb = POT ? f_buf(b, RES ? 2 : 0) : nullptr;
+
+    // Registers: psi0, current stage value, accumulator (+ reservoir).
+    float2 p0[MR][2], yc[MR][2], acc[MR][2];
+    float n0[MR][2], nc[MR][2], na[MR][2], Pv[MR][2], Vv[MR][2];
+    bool ins[MR][2];
+    const int gx0 = xp - HALO + c0;        // domain column of my first column
+    const int gy0 = ky * C::TY - 3 + r0;   // domain row of my first row
+#pragma unroll
+    for (int j = 0; j < MR; ++j) {
+      const float4 v = *reinterpret_cast<const float4*>(&P0[(r0 + j + 1) * C::PW + c0 + 2]);
+      p0[j][0] = f2(v.x, v.y);
+      p0[j][1] = f2(v.z, v.w);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        yc[j][i] = p0[j][i];
+        acc[j][i] = f2(0.f, 0.f);
+        na[j][i] = 0.f;
+        const int gx = gx0 + i, gy = gy0 + j;
+        ins[j][i] = (g.bc_x == BC_PERIODIC || (gx >= 0 && gx < g.nx)) &&
+                    (g.bc_y == BC_PERIODIC || (gy >= 0 && gy < g.ny));
+        const int fi = (r0 + j) * C::FW + foff + c0 + i;
+        n0[j][i] = RES ? Nb[fi] : 0.f;
+        nc[j][i] = n0[j][i];
+        Pv[j][i] = RES ? Pb[fi] : 0.f;
+        Vv[j][i] = POT ? Vb[fi] * cih : 0.f;
+      }
+    }
+
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      const float2* src = (s & 1) ? Y : P0;
+      float2* dst = (s & 1) ? P0 : Y;
+      const float w = (s == 0 || s == 3) ? 1.f : 2.f;
+      const float cs = (s == 2) ? dt : 0.5f * dt;
+      const float2 w2 = f2(w, w), cs2 = f2(cs, cs);
+      // neighbours of the micro-tile
+      const float4 tv = *reinterpret_cast<const float4*>(&src[(r0)*C::PW + c0 + 2]);
+      const float4 bv = *reinterpret_cast<const float4*>(&src[(r0 + MR + 1) * C::PW + c0 + 2]);
+      float2 Wv[MR], Ev[MR];
+#pragma unroll
+      for (int j = 0; j < MR; ++j) {
+        Wv[j] = src[(r0 + j + 1) * C::PW + c0 + 1];
+        Ev[j] = src[(r0 + j + 1) * C::PW + c0 + 4];
+      }
+      float2 ny[MR][2];
+      float nn[MR][2];
+#pragma unroll
+      for (int j = 0; j < MR; ++j) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const float2 Cc = yc[j][i];
+          const float2 W = i ? yc[j][0] : Wv[j];
+          const float2 E = i ? Ev[j] : yc[j][1];
+          const float2 S = j ? yc[j - 1][i] : (i ? f2(tv.z, tv.w) : f2(tv.x, tv.y));
+          const float2 N = (j < MR - 1) ? yc[j + 1][i] : (i ? f2(bv.z, bv.w) : f2(bv.x, bv.y));
+          // H/hbar of the stencil part: ax (E+W) + ay (N+S) + a0 C
+          float2 lap = __fmul2_rn(ay2, __fadd2_rn(N, S));
+          lap = __ffma2_rn(ax2, __fadd2_rn(E, W), lap);
+          lap = __ffma2_rn(a02, Cc, lap);
+          const float dens = fmaf(Cc.x, Cc.x, Cc.y * Cc.y);
+          const float ncur = nc[j][i];
+          float loc = fmaf(cg, dens, Vv[j][i]);
+          if (RES) loc = fmaf(cgr, ncur, loc);
+          const float2 H = __ffma2_rn(f2(loc, loc), Cc, lap);
+          const float G = RES ? fmaf(hR, ncur, -hgc) : -hgc;
+          float2 K;
+          K.x = fmaf(G, Cc.x, H.y);
+          K.y = fmaf(G, Cc.y, -H.x);
+          acc[j][i] = __ffma2_rn(w2, K, acc[j][i]);
+          float Kn = 0.f;
+          if (RES) {
+            Kn = fmaf(-fmaf(cR, dens, cgam), ncur, Pv[j][i]);
+            na[j][i] = fmaf(w, Kn, na[j][i]);
+          }
+          ny[j][i] = __ffma2_rn(cs2, K, p0[j][i]);
+          if (!ins[j][i]) ny[j][i] = f2(0.f, 0.f);
+          nn[j][i] = RES ? fmaf(cs, Kn, n0[j][i]) : 0.f;
+        }
+      }
+      if (s < 3) {
+#pragma unroll
+        for (int j = 0; j < MR; ++j) {
+          yc[j][0] = ny[j][0];
+          yc[j][1] = ny[j][1];
+          nc[j][0] = nn[j][0];
+          nc[j][1] = nn[j][1];
+          *reinterpret_cast<float4*>(&dst[(r0 + j + 1) * C::PW + c0 + 2]) =
+              make_float4(ny[j][0].x, ny[j][0].y, ny[j][1].x, ny[j][1].y);
+        }
+      }
+      __syncthreads();
+    }
+
+    // psi' = psi0 + (K1 + 2K2 + 2K3 + K4) dt/6, written to the output tile
+    const float2 d62 = f2(dt6, dt6);
+#pragma unroll
+    for (int j = 0; j < MR; ++j) {
+      const int r = r0 + j;
+      const int gy = gy0 + j;
+      if (r < 3 || r >= 3 + C::TY || gy >= g.ny) continue;
+      float2 o[2];
+      float on[2];
+      bool ok[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int c = c0 + i, gx = gx0 + i;
+        ok[i] = c >= 3 && c < 3 + C::TX && gx >= 0 && gx < g.nx;
+        o[i] = __ffma2_rn(d62, acc[j][i], p0[j][i]);
+        on[i] = fmaf(dt6, na[j][i], n0[j][i]);
+        if (a.noise.on && ok[i]) {
+          float2 xi, unused;
+          nz_site(a.noise.seed, a.noise.instance, step, (uint32_t)(gy * g.nx + gx),
+                  a.noise.scale, xi, unused, false);
+          o[i].x = o[i].x + xi.x;
+          o[i].y = o[i].y + xi.y;
+        }
+      }
+      const bool edge_x = g.bc_x == BC_PERIODIC && (gx0 < HALO || gx0 + 1 >= g.nx - HALO);
+      const bool edge_y = g.bc_y == BC_PERIODIC && (gy < HALO || gy >= g.ny - HALO);
+      const long long roff = (long long)(gy + HALO) * g.pitch + gx0 + HALO;
+      if (ok[0] && ok[1] && !edge_x && !edge_y) {
+        *reinterpret_cast<float4*>(a.psi_out + roff) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+        if (RES) *reinterpret_cast<float2*>(a.n_out + roff) = f2(on[0], on[1]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          if (!ok[i]) continue;
+          store_with_ghosts(a.psi_out, g, gx0 + i, gy, o[i]);
+          if (RES) store_with_ghosts(a.n_out, g, gx0 + i, gy, on[i]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <bool RES, bool POT, int MR, int WY>
+cudaError_t launch_cfg(const TmaMaps& m, const StepArgs<float>& a, cudaStream_t s, int* err,
+                       int num_sms) {
+  using C = Cfg<RES, POT, MR, WY>;
+  auto kern = rk4_f32_tma<RES, POT, MR, WY>;
+  static int configured_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_dev != dev) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+  }
+  TileGeo tg;
+  tg.tiles_x = (a.geo.nx + 1 + C::TX - 1) / C::TX;
+  tg.tiles_y = (a.geo.ny + C::TY - 1) / C::TY;
+  tg.ntiles = tg.tiles_x * tg.tiles_y;
+  int grid = tg.ntiles < num_sms ? tg.ntiles : num_sms;
+  kern<<<grid, C::NT, C::SMEM, s>>>(m.psi, m.n, m.P, m.V, a, tg, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Box shapes the tensor maps must use for a given tile configuration.
+TmaBox tma_box(int tile_cfg) {
+  TmaBox b;
+  int MR = 4, WY = 16;
+  if (tile_cfg == TILE_64x48) WY = 12;
+  if (tile_cfg == TILE_64x32) WY = 8;
+  const int RW = 64, RH = MR * WY;
+  b.psi_w = 2 * (RW + 4);  // floats (interleaved complex)
+  b.psi_h = RH + 2;
+  b.f_w = RW + 4;
+  b.f_h = RH;
+  b.tx = RW - 6;
+  b.ty = RH - 6;
+  return b;
+}
+
+cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, const TmaMaps& m,
+                               const StepArgs<float>& a, cudaStream_t s, int* err,
+                               int num_sms) {
+#define PHX_TMA_CASE(CFG, MR, WY)                                                   \
+  if (tile_cfg == CFG) {                                                            \
+    if (res && pot) return launch_cfg<true, true, MR, WY>(m, a, s, err, num_sms);   \
+    if (res) return launch_cfg<true, false, MR, WY>(m, a, s, err, num_sms);         \
+    if (pot) return launch_cfg<false, true, MR, WY>(m, a, s, err, num_sms);         \
+    return launch_cfg<false, false, MR, WY>(m, a, s, err, num_sms);                 \
+  }
+  PHX_TMA_CASE(TILE_64x64, 4, 16)
+  PHX_TMA_CASE(TILE_64x48, 4, 12)
+  PHX_TMA_CASE(TILE_64x32, 4, 8)
+#undef PHX_TMA_CASE
+  return cudaErrorInvalidValue;
+}
+
+// ---- tensor-map encoding (driver entry point, no libcuda link needed) -----
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool encode_map_f32(CUtensorMap* map, void* base, unsigned long long w,
+                    unsigned long long h, unsigned long long planes,
+                    unsigned long long row_bytes, unsigned long long plane_bytes,
+                    unsigned box_w, unsigned box_h) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {w, h, planes};
+  cuuint64_t strides[2] = {row_bytes, plane_bytes};
+  cuuint32_t box[3] = {box_w, box_h, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace phx

@@ -274,3 +274,55 @@ def test_device_pointers_and_torch_stream():
                         gp.Params(**d), 5)
     assert rel_l2(outp.cpu().numpy(), o_psi) <= 1e-4
     assert rel_l2(outn.cpu().numpy(), o_n) <= 1e-4
+
+
+TILES = [0, 1, 2, 3, 9]  # auto, 64x64, 64x48, 64x32 (TMA-fed persistent), generic
+
+
+@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("kind", ["reservoir", "loss"])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1), (0, 1)])
+@pytest.mark.parametrize("size", [(131, 77), (58, 58), (59, 116), (200, 3)])
+def test_fp32_scalar_tile_configs(tile, kind, bc, size):
+    """Every tile configuration of the FP32 scalar kernel against the oracle,
+    with a potential, on grids that are exact tile multiples and ragged."""
+    m = phx()
+    d = model(kind, *size, bc=bc)
+    nc = 1
+    psi0, n0, P, V = synth.random_state(nc, size[1], size[0], 5, amp=0.7,
+                                        reservoir=d["reservoir"], smooth=True)
+    psi0, n0, P, V = (rounded(x, 32) for x in (psi0, n0, P, V))
+    h = m.phx_create(m.params_from_dict(d, precision=32, tile=tile))
+    if d["reservoir"]:
+        m.phx_set_pump(h, np.ascontiguousarray(P[0], np.float32))
+    m.phx_set_potential(h, np.ascontiguousarray(V, np.float32))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, np.complex64),
+                    None if n0 is None else np.ascontiguousarray(n0, np.float32))
+    m.phx_step_n(h, 9)
+    g_psi, g_n = get_state(h, 32)
+    o_psi, o_n = gp.run(psi0, n0, P, V, gp.Params(**d), 9)
+    assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
+    if d["reservoir"]:
+        assert rel_l2(g_n, o_n) <= 1e-4
+
+
+@pytest.mark.parametrize("size", [(1, 1), (2, 3), (4, 4), (5, 3), (3, 7), (9, 1), (1, 9)])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1), (1, 0)])
+def test_fp32_scalar_tiny_grids(size, bc):
+    d = model("reservoir", *size, bc=bc, L=(0.5 * size[0], 0.5 * size[1]))
+    h, (gp_, gn), (op, on) = run_both(d, 32, steps=7)
+    assert rel_l2(gp_, op) <= 1e-4
+    assert rel_l2(gn, on) <= 1e-4
+
+
+def test_fp32_scalar_noise_bit_path():
+    """Scalar FP32 with noise through the TMA kernel: kappa = 0 and no other
+    term, so one step from psi = 0 yields exactly xi_+."""
+    d = synth.base_params(70, 61, 7.0, 6.1, kappa=0.0, noise_var=2e-3, seed=5, dt=0.01)
+    h = make_handle(d, 32, np.zeros((1, 61, 70)))
+    phx().phx_set_time(h, 7, 0.0)
+    phx().phx_step_n(h, 1)
+    g, _ = get_state(h, 32)
+    re, im = noise.noise_field(5, 7, 0, 1, 61, 70, 2e-3)
+    assert np.array_equal(g.real.astype(np.float32), re)
+    assert np.array_equal(g.imag.astype(np.float32), im)
