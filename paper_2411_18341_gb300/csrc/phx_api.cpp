@@ -216,7 +216,7 @@ Coeffs make_coeffs(const phx_params& p) {
   k.inv_hbar = 1.0 / HBAR;
   k.half_R = 0.5 * p.R;
   k.half_gc = 0.5 * p.gamma_c;
-  k.R = p.R;
+  k.R_ = p.R;
   k.gamma_r = p.gamma_r;
   k.tx = p.delta_lt / (HBAR * dx * dx);
   k.ty = p.delta_lt / (HBAR * dy * dy);
@@ -524,7 +524,8 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.P = static_cast<const float*>(h->P);
       a.P_comp_stride = h->P_stride;
       a.V = h->has_V ? static_cast<const float*>(h->V) : nullptr;
-      a.k = k;
+      a.k = cast_coeffs<float>(k);
+      a.dt64 = k.dt;
       a.noise = nz;
       a.clock = h->clock;
       a.parity = h->parity;
@@ -549,6 +550,7 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.P_comp_stride = h->P_stride;
       a.V = h->has_V ? static_cast<const double*>(h->V) : nullptr;
       a.k = k;
+      a.dt64 = k.dt;
       a.noise = nz;
       a.clock = h->clock;
       a.parity = h->parity;

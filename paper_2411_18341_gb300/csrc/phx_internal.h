@@ -35,16 +35,33 @@ struct Geometry {
   int bc_x, bc_y;
 };
 
-// Coefficients of one RK4 step, pre-scaled by 1/hbar (units ps^-1).
-struct Coeffs {
-  double ax, ay, a0;      // -(k/h)/dx^2, -(k/h)/dy^2, 2(k/h)(1/dx^2 + 1/dy^2)
-  double g, gx, gr;       // g/h, g_x/h, g_r/h
-  double inv_hbar;        // multiplies V
-  double half_R, half_gc; // R/2, gamma_c/2
-  double R, gamma_r;
-  double tx, ty, txy;     // Delta/(h dx^2), Delta/(h dy^2), Delta/(2 h dx dy)
-  double dt;
+// Coefficients of one RK4 step, pre-scaled by 1/hbar (units ps^-1), in the
+// stencil precision R (converted once on the host: a double-to-float
+// conversion inside a kernel runs on the FP64 pipe, which is narrow on GB300).
+template <typename R>
+struct CoeffsT {
+  R ax, ay, a0;      // -(k/h)/dx^2, -(k/h)/dy^2, 2(k/h)(1/dx^2 + 1/dy^2)
+  R g, gx, gr;       // g/h, g_x/h, g_r/h
+  R inv_hbar;        // multiplies V
+  R half_R, half_gc; // R/2, gamma_c/2
+  R R_, gamma_r;
+  R tx, ty, txy;     // Delta/(h dx^2), Delta/(h dy^2), Delta/(2 h dx dy)
+  R dt;
 };
+using Coeffs = CoeffsT<double>;
+
+template <typename R>
+inline CoeffsT<R> cast_coeffs(const Coeffs& c) {
+  CoeffsT<R> o;
+  o.ax = (R)c.ax; o.ay = (R)c.ay; o.a0 = (R)c.a0;
+  o.g = (R)c.g; o.gx = (R)c.gx; o.gr = (R)c.gr;
+  o.inv_hbar = (R)c.inv_hbar;
+  o.half_R = (R)c.half_R; o.half_gc = (R)c.half_gc;
+  o.R_ = (R)c.R_; o.gamma_r = (R)c.gamma_r;
+  o.tx = (R)c.tx; o.ty = (R)c.ty; o.txy = (R)c.txy;
+  o.dt = (R)c.dt;
+  return o;
+}
 
 struct NoiseKey {
   unsigned long long seed;
@@ -63,7 +80,8 @@ struct StepArgs {
   const R* P;             // ncomp planes (plane 1 may alias plane 0)
   long long P_comp_stride;
   const R* V;             // nullptr when absent
-  Coeffs k;
+  CoeffsT<R> k;
+  double dt64;            // FP64 time step for the simulated-time accumulator
   NoiseKey noise;
   DevClock* clock;
   int parity;

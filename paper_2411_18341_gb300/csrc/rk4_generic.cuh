@@ -33,16 +33,39 @@ template <> struct CxOps<double> {
   __device__ static C mk(double a, double b) { return make_double2(a, b); }
 };
 
-// Write v at every padded position that images domain site (gx, gy).
+// Write v at every padded position that images domain site (gx, gy): the
+// site itself and, along a periodic axis within HALO of an edge, its ghost
+// images.  Interior sites take the single-store path (no division).
 template <typename T>
 __device__ __forceinline__ void store_with_ghosts(T* plane, const Geometry& g,
                                                   int gx, int gy, T v) {
+  const bool near_x = g.bc_x == BC_PERIODIC && (gx < HALO || gx >= g.nx - HALO);
+  const bool near_y = g.bc_y == BC_PERIODIC && (gy < HALO || gy >= g.ny - HALO);
+  if (!near_x && !near_y) {
+    plane[(long long)(gy + HALO) * g.pitch + gx + HALO] = v;
+    return;
+  }
+  if (g.nx >= 2 * HALO && g.ny >= 2 * HALO) {
+    // at most one image per axis: the site +-n, no division needed
+    const int ix = gx + HALO, iy = gy + HALO;
+    const int ix2 = !near_x ? -1 : (gx < HALO ? ix + g.nx : ix - g.nx);
+    const int iy2 = !near_y ? -1 : (gy < HALO ? iy + g.ny : iy - g.ny);
+    const long long r1 = (long long)iy * g.pitch;
+    plane[r1 + ix] = v;
+    if (ix2 >= 0) plane[r1 + ix2] = v;
+    if (iy2 >= 0) {
+      const long long r2 = (long long)iy2 * g.pitch;
+      plane[r2 + ix] = v;
+      if (ix2 >= 0) plane[r2 + ix2] = v;
+    }
+    return;
+  }
   int mx0 = 0, mx1 = 0, my0 = 0, my1 = 0;
-  if (g.bc_x == BC_PERIODIC) {
+  if (near_x) {
     mx0 = -((gx + HALO) / g.nx);
     mx1 = (g.nx + HALO - 1 - gx) / g.nx;
   }
-  if (g.bc_y == BC_PERIODIC) {
+  if (near_y) {
     my0 = -((gy + HALO) / g.ny);
     my1 = (g.ny + HALO - 1 - gy) / g.ny;
   }
@@ -124,12 +147,12 @@ rk4_step_generic(const StepArgs<R> a) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) psi0[k][c] = ybuf0[c * LBOX + sidx[k]];
 
-  const Coeffs& q = a.k;
-  const R ax = R(q.ax), ay = R(q.ay), a0 = R(q.a0);
-  const R cg = R(q.g), cgx = R(q.gx), cgr = R(q.gr), cih = R(q.inv_hbar);
-  const R hR = R(q.half_R), hgc = R(q.half_gc), cR = R(q.R), cgr_ = R(q.gamma_r);
-  const R tx = R(q.tx), ty = R(q.ty), txy = R(q.txy);
-  const R dt = R(q.dt);
+  const CoeffsT<R>& q = a.k;
+  const R ax = q.ax, ay = q.ay, a0 = q.a0;
+  const R cg = q.g, cgx = q.gx, cgr = q.gr, cih = q.inv_hbar;
+  const R hR = q.half_R, hgc = q.half_gc, cR = q.R_, cgr_ = q.gamma_r;
+  const R tx = q.tx, ty = q.ty, txy = q.txy;
+  const R dt = q.dt;
 
 #pragma unroll 1
   for (int s = 0; s < 4; ++s) {
@@ -212,9 +235,24 @@ rk4_step_generic(const StepArgs<R> a) {
   const long long step = a.clock->step[a.parity];
   if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
     a.clock->step[a.parity ^ 1] = step + 1;
-    a.clock->t[a.parity ^ 1] = a.clock->t[a.parity] + q.dt;
+    a.clock->t[a.parity ^ 1] = a.clock->t[a.parity] + a.dt64;
   }
   const R dt6 = dt / R(6);
+  // Noise is drawn in a grid-uniform branch of its own so that the generator
+  // is never issued (predicated off) when noise is disabled.
+  float2 xi[PPT][2];
+  if (a.noise.on) {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      int idx = tid + k * NT;
+      int ry = idx / RXN, rx = idx - ry * RXN;
+      int gx = x0 - 3 + rx, gy = y0 - 3 + ry;
+      xi[k][0] = xi[k][1] = make_float2(0.f, 0.f);
+      if (valid[k] && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny)
+        nz_site(a.noise.seed, a.noise.instance, step, (uint32_t)(gy * g.nx + gx),
+                a.noise.scale, xi[k][0], xi[k][1], NC == 2);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     if (!valid[k]) continue;
@@ -223,18 +261,14 @@ rk4_step_generic(const StepArgs<R> a) {
     if (rx < 3 || rx >= 3 + TX || ry < 3 || ry >= 3 + TY) continue;
     int gx = x0 - 3 + rx, gy = y0 - 3 + ry;
     if (gx >= g.nx || gy >= g.ny) continue;
-    float2 xi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    if (a.noise.on)
-      nz_site(a.noise.seed, a.noise.instance, step, (uint32_t)(gy * g.nx + gx),
-              a.noise.scale, xi[0], xi[1], NC == 2);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       C out;
       out.x = psi0[k][c].x + acc[k][c].x * dt6;
       out.y = psi0[k][c].y + acc[k][c].y * dt6;
       if (a.noise.on) {
-        out.x = out.x + R(xi[c].x);
-        out.y = out.y + R(xi[c].y);
+        out.x = out.x + R(xi[k][c].x);
+        out.y = out.y + R(xi[k][c].y);
       }
       store_with_ghosts(a.psi_out + c * g.plane, g, gx, gy, out);
       if (RES) {

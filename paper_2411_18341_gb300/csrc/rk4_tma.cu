@@ -29,6 +29,12 @@
 #include "rk4_generic.cuh"
 #include "rk4_tma.h"
 
+// Tile loader: TMA (cp.async.bulk.tensor + mbarrier, default) or per-thread
+// 16-byte cp.async chunks (measured slower on GB300 at 1024^2).
+#ifndef PHX_TILE_LOADER_TMA
+#define PHX_TILE_LOADER_TMA true
+#endif
+
 namespace phx {
 
 namespace {
@@ -73,12 +79,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Wait for phase `parity` of `bar`, giving up after ~0.25 s.
+// Wait for phase `parity` of `bar`, giving up after ~0.25 s; backs off with
+// __nanosleep after the first few polls so waiting warps leave issue slots.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > 250000000ull) return false;
+    if (it >= 4) __nanosleep(64);
+    if ((it & 63u) == 63u && global_ns() - t0 > 250000000ull) return false;
   }
 }
 
@@ -89,6 +98,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_1() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -114,7 +135,7 @@ struct TileGeo {
   int tiles_x, tiles_y, ntiles;
 };
 
-template <bool RES, bool POT, int MR, int WY>
+template <bool RES, bool POT, int MR, int WY, bool TMA>
 __global__ void __launch_bounds__(32 * WY, 1)
 rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
             const __grid_constant__ CUtensorMap tm_n,
@@ -149,6 +170,48 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
     fence_mbar_init();
   }
   __syncthreads();
+  // Programmatic dependent launch: this grid may have started while the
+  // previous step was still running; everything above touched only shared
+  // memory.  Let the next step's grid be scheduled as SMs free up, then wait
+  // until the previous grid has completed and its writes are visible.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  // Loader B: every thread copies 16-byte chunks with cp.async (zero fill
+  // outside the padded arrays); one commit group per tile.
+  auto issue_cp = [&](int t, int b) {
+    if (t < tg.ntiles) {
+      const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
+      const int xp = kx * C::TX, yp = ky * C::TY;
+      constexpr int CP = C::PW / 2;  // 16-byte chunks per psi row
+      float2* sp = psi_buf(b);
+      for (int q = tid; q < C::PH * CP; q += C::NT) {
+        const int r = q / CP, cc = q - r * CP;
+        const int gy = yp + r, gxp = xp - 2 + 2 * cc;
+        const bool ok = gy < g.prow && gxp >= 0 && gxp < g.pitch;
+        const float2* src = ok ? a.psi_in + (long long)gy * g.pitch + gxp : a.psi_in;
+        cp_async16(sp + r * C::PW + 2 * cc, src, ok ? 16 : 0);
+      }
+      constexpr int CF = C::FW / 4;  // 16-byte chunks per field row
+      const int fx = xp & ~3;
+      auto field = [&](float* dst, const float* base) {
+        for (int q = tid; q < C::RH * CF; q += C::NT) {
+          const int r = q / CF, cc = q - r * CF;
+          const int gy = yp + 1 + r, gx = fx + 4 * cc;
+          const bool ok = gy < g.prow && gx < g.pitch;
+          const float* src = ok ? base + (long long)gy * g.pitch + gx : base;
+          cp_async16(dst + r * C::FW + 4 * cc, src, ok ? 16 : 0);
+        }
+      };
+      int f = 0;
+      if (RES) {
+        field(f_buf(b, f++), a.n_in);
+        field(f_buf(b, f++), a.P);
+      }
+      if (POT) field(f_buf(b, f++), a.V);
+    }
+    cp_async_commit();
+  };
 
   auto issue = [&](int t, int b) {
     const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
@@ -167,37 +230,46 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
   const long long step = a.clock->step[a.parity];
   if (blockIdx.x == 0 && tid == 0) {
     a.clock->step[a.parity ^ 1] = step + 1;
-    a.clock->t[a.parity ^ 1] = a.clock->t[a.parity] + a.k.dt;
+    a.clock->t[a.parity ^ 1] = a.clock->t[a.parity] + a.dt64;
   }
 
-  const Coeffs& q = a.k;
-  const float2 ax2 = f2((float)q.ax, (float)q.ax), ay2 = f2((float)q.ay, (float)q.ay);
-  const float2 a02 = f2((float)q.a0, (float)q.a0);
-  const float cg = (float)q.g, cgr = (float)q.gr, cih = (float)q.inv_hbar;
-  const float hR = (float)q.half_R, hgc = (float)q.half_gc, cR = (float)q.R;
-  const float cgam = (float)q.gamma_r, dt = (float)q.dt;
+  const CoeffsT<float>& q = a.k;
+  const float2 ax2 = f2(q.ax, q.ax), ay2 = f2(q.ay, q.ay);
+  const float2 a02 = f2(q.a0, q.a0);
+  const float cg = q.g, cgr = q.gr, cih = q.inv_hbar;
+  const float hR = q.half_R, hgc = q.half_gc, cR = q.R_;
+  const float cgam = q.gamma_r, dt = q.dt;
   const float dt6 = dt / 6.0f;
 
   int t = blockIdx.x, k = 0;
-  if (t < tg.ntiles && tid == 0 && !a.inject_timeout) issue(t, 0);
+  if (TMA) {
+    if (t < tg.ntiles && tid == 0 && !a.inject_timeout) issue(t, 0);
+  } else {
+    issue_cp(t, 0);
+  }
   for (; t < tg.ntiles; t += gridDim.x, ++k) {
     const int b = k & 1;
     const uint32_t par = (uint32_t)((k >> 1) & 1);
     const int tn = t + gridDim.x;
-    if (tid == 0 && tn < tg.ntiles) {
-      fence_proxy_async();  // generic writes to buffer b^1 (previous tile) before TMA reuse
-      issue(tn, b ^ 1);
-    }
-    int fail = 0;
-    if (tid == 0) fail = !mbar_wait_bounded(&bar[b], par);
-    if (__syncthreads_or(fail)) {
-      if (tid == 0) {
-        atomicExch(err, 1);
-        if (tn < tg.ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+    if (TMA) {
+      if (tid == 0 && tn < tg.ntiles) {
+        fence_proxy_async();  // generic writes to buffer b^1 (previous tile) before TMA reuse
+        issue(tn, b ^ 1);
       }
-      return;
-    }
-    while (!mbar_try_wait(&bar[b], par)) {
+      // every thread waits on the barrier (bounded); the CTA leaves together
+      // if any thread gave up
+      const int fail = !mbar_wait_bounded(&bar[b], par);
+      if (__syncthreads_or(fail)) {
+        if (tid == 0) {
+          atomicExch(err, 1);
+          if (tn < tg.ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+        }
+        return;
+      }
+    } else {
+      issue_cp(tn, b ^ 1);  // prefetch (an empty group past the last tile)
+      cp_async_wait_1();    // this tile's group has landed (own copies)
+      __syncthreads();      // ... and everyone else's
     }
 
     const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
@@ -302,40 +374,55 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
 
     // psi' = psi0 + (K1 + 2K2 + 2K3 + K4) dt/6, written to the output tile
     const float2 d62 = f2(dt6, dt6);
+    float2 o[MR][2];
+    float on[MR][2];
+#pragma unroll
+    for (int j = 0; j < MR; ++j)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        o[j][i] = __ffma2_rn(d62, acc[j][i], p0[j][i]);
+        on[j][i] = fmaf(dt6, na[j][i], n0[j][i]);
+      }
+    if (a.noise.on) {  // grid-uniform branch: the generator is not issued when off
+#pragma unroll
+      for (int j = 0; j < MR; ++j) {
+        const int gy = gy0 + j;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int gx = gx0 + i;
+          const uint32_t site = (uint32_t)(((gy % g.ny + g.ny) % g.ny) * g.nx +
+                                           (gx % g.nx + g.nx) % g.nx);
+          float2 xi, unused;
+          nz_site(a.noise.seed, a.noise.instance, step, site, a.noise.scale, xi, unused, false);
+          o[j][i].x = o[j][i].x + xi.x;
+          o[j][i].y = o[j][i].y + xi.y;
+        }
+      }
+    }
 #pragma unroll
     for (int j = 0; j < MR; ++j) {
       const int r = r0 + j;
       const int gy = gy0 + j;
       if (r < 3 || r >= 3 + C::TY || gy >= g.ny) continue;
-      float2 o[2];
-      float on[2];
       bool ok[2];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const int c = c0 + i, gx = gx0 + i;
         ok[i] = c >= 3 && c < 3 + C::TX && gx >= 0 && gx < g.nx;
-        o[i] = __ffma2_rn(d62, acc[j][i], p0[j][i]);
-        on[i] = fmaf(dt6, na[j][i], n0[j][i]);
-        if (a.noise.on && ok[i]) {
-          float2 xi, unused;
-          nz_site(a.noise.seed, a.noise.instance, step, (uint32_t)(gy * g.nx + gx),
-                  a.noise.scale, xi, unused, false);
-          o[i].x = o[i].x + xi.x;
-          o[i].y = o[i].y + xi.y;
-        }
       }
       const bool edge_x = g.bc_x == BC_PERIODIC && (gx0 < HALO || gx0 + 1 >= g.nx - HALO);
       const bool edge_y = g.bc_y == BC_PERIODIC && (gy < HALO || gy >= g.ny - HALO);
       const long long roff = (long long)(gy + HALO) * g.pitch + gx0 + HALO;
       if (ok[0] && ok[1] && !edge_x && !edge_y) {
-        *reinterpret_cast<float4*>(a.psi_out + roff) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-        if (RES) *reinterpret_cast<float2*>(a.n_out + roff) = f2(on[0], on[1]);
+        *reinterpret_cast<float4*>(a.psi_out + roff) =
+            make_float4(o[j][0].x, o[j][0].y, o[j][1].x, o[j][1].y);
+        if (RES) *reinterpret_cast<float2*>(a.n_out + roff) = f2(on[j][0], on[j][1]);
       } else {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           if (!ok[i]) continue;
-          store_with_ghosts(a.psi_out, g, gx0 + i, gy, o[i]);
-          if (RES) store_with_ghosts(a.n_out, g, gx0 + i, gy, on[i]);
+          store_with_ghosts(a.psi_out, g, gx0 + i, gy, o[j][i]);
+          if (RES) store_with_ghosts(a.n_out, g, gx0 + i, gy, on[j][i]);
         }
       }
     }
@@ -347,7 +434,7 @@ template <bool RES, bool POT, int MR, int WY>
 cudaError_t launch_cfg(const TmaMaps& m, const StepArgs<float>& a, cudaStream_t s, int* err,
                        int num_sms) {
   using C = Cfg<RES, POT, MR, WY>;
-  auto kern = rk4_f32_tma<RES, POT, MR, WY>;
+  auto kern = rk4_f32_tma<RES, POT, MR, WY, PHX_TILE_LOADER_TMA>;
   static int configured_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -362,8 +449,19 @@ cudaError_t launch_cfg(const TmaMaps& m, const StepArgs<float>& a, cudaStream_t 
   tg.tiles_y = (a.geo.ny + C::TY - 1) / C::TY;
   tg.ntiles = tg.tiles_x * tg.tiles_y;
   int grid = tg.ntiles < num_sms ? tg.ntiles : num_sms;
-  kern<<<grid, C::NT, C::SMEM, s>>>(m.psi, m.n, m.P, m.V, a, tg, err);
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(C::NT);
+  lc.dynamicSmemBytes = C::SMEM;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&lc, kern, m.psi, m.n, m.P, m.V, a, tg, err);
   count_launch();
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
