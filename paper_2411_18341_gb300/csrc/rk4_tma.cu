@@ -29,12 +29,6 @@
 #include "rk4_generic.cuh"
 #include "rk4_tma.h"
 
-// Tile loader: TMA (cp.async.bulk.tensor + mbarrier, default) or per-thread
-// 16-byte cp.async chunks (measured slower on GB300 at 1024^2).
-#ifndef PHX_TILE_LOADER_TMA
-#define PHX_TILE_LOADER_TMA true
-#endif
-
 namespace phx {
 
 namespace {
@@ -100,18 +94,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-               "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_1() {
-  asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
-
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 template <bool RES, bool POT, int MR, int WY>
@@ -128,14 +110,17 @@ struct Cfg {
   static constexpr int F_BYTES = ((RH * FW * 4) + 127) / 128 * 128;
   static constexpr int BUF_BYTES = PSI_BYTES + NF * F_BYTES;
   static constexpr int TX_BYTES = PH * PW * 8 + NF * RH * FW * 4;  // bytes one tile brings
-  static constexpr int SMEM = 2 * BUF_BYTES + PSI_BYTES + 128;
+  // Input buffers: one per tile in flight (three when shared memory allows,
+  // so that a CTA with three tiles has all its loads in flight at once).
+  static constexpr int NBUF = (3 * BUF_BYTES + PSI_BYTES + 128 <= 227 * 1024) ? 3 : 2;
+  static constexpr int SMEM = NBUF * BUF_BYTES + PSI_BYTES + 128;
 };
 
 struct TileGeo {
   int tiles_x, tiles_y, ntiles;
 };
 
-template <bool RES, bool POT, int MR, int WY, bool TMA>
+template <bool RES, bool POT, int MR, int WY>
 __global__ void __launch_bounds__(32 * WY, 1)
 rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
             const __grid_constant__ CUtensorMap tm_n,
@@ -144,10 +129,10 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
             const TileGeo tg, int* err) {
   using C = Cfg<RES, POT, MR, WY>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[3];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  float2* Y = reinterpret_cast<float2*>(base + 2 * C::BUF_BYTES);
+  float2* Y = reinterpret_cast<float2*>(base + C::NBUF * C::BUF_BYTES);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c0 = 2 * lane;   // region column of the micro-tile's first column
@@ -165,8 +150,7 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
     if (r == 0 || r == C::PH - 1 || c < 2 || c >= C::RW + 2) Y[i] = f2(0.f, 0.f);
   }
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < C::NBUF; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -176,42 +160,6 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
   // until the previous grid has completed and its writes are visible.
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
-
-  // Loader B: every thread copies 16-byte chunks with cp.async (zero fill
-  // outside the padded arrays); one commit group per tile.
-  auto issue_cp = [&](int t, int b) {
-    if (t < tg.ntiles) {
-      const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
-      const int xp = kx * C::TX, yp = ky * C::TY;
-      constexpr int CP = C::PW / 2;  // 16-byte chunks per psi row
-      float2* sp = psi_buf(b);
-      for (int q = tid; q < C::PH * CP; q += C::NT) {
-        const int r = q / CP, cc = q - r * CP;
-        const int gy = yp + r, gxp = xp - 2 + 2 * cc;
-        const bool ok = gy < g.prow && gxp >= 0 && gxp < g.pitch;
-        const float2* src = ok ? a.psi_in + (long long)gy * g.pitch + gxp : a.psi_in;
-        cp_async16(sp + r * C::PW + 2 * cc, src, ok ? 16 : 0);
-      }
-      constexpr int CF = C::FW / 4;  // 16-byte chunks per field row
-      const int fx = xp & ~3;
-      auto field = [&](float* dst, const float* base) {
-        for (int q = tid; q < C::RH * CF; q += C::NT) {
-          const int r = q / CF, cc = q - r * CF;
-          const int gy = yp + 1 + r, gx = fx + 4 * cc;
-          const bool ok = gy < g.prow && gx < g.pitch;
-          const float* src = ok ? base + (long long)gy * g.pitch + gx : base;
-          cp_async16(dst + r * C::FW + 4 * cc, src, ok ? 16 : 0);
-        }
-      };
-      int f = 0;
-      if (RES) {
-        field(f_buf(b, f++), a.n_in);
-        field(f_buf(b, f++), a.P);
-      }
-      if (POT) field(f_buf(b, f++), a.V);
-    }
-    cp_async_commit();
-  };
 
   auto issue = [&](int t, int b) {
     const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
@@ -242,34 +190,31 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
   const float dt6 = dt / 6.0f;
 
   int t = blockIdx.x, k = 0;
-  if (TMA) {
-    if (t < tg.ntiles && tid == 0 && !a.inject_timeout) issue(t, 0);
-  } else {
-    issue_cp(t, 0);
+  if (tid == 0) {  // prologue: the first NBUF-1 tiles
+    for (int i = 0; i < C::NBUF - 1; ++i) {
+      const int ti = t + i * (int)gridDim.x;
+      if (ti < tg.ntiles && !(i == 0 && a.inject_timeout)) issue(ti, i);
+    }
   }
   for (; t < tg.ntiles; t += gridDim.x, ++k) {
-    const int b = k & 1;
-    const uint32_t par = (uint32_t)((k >> 1) & 1);
-    const int tn = t + gridDim.x;
-    if (TMA) {
-      if (tid == 0 && tn < tg.ntiles) {
-        fence_proxy_async();  // generic writes to buffer b^1 (previous tile) before TMA reuse
-        issue(tn, b ^ 1);
+    const int b = k % C::NBUF;
+    const uint32_t par = (uint32_t)((k / C::NBUF) & 1);
+    const int tn = t + (C::NBUF - 1) * (int)gridDim.x;
+    if (tid == 0 && tn < tg.ntiles) {
+      fence_proxy_async();  // generic accesses of that buffer (previous tile) before TMA reuse
+      issue(tn, (k + C::NBUF - 1) % C::NBUF);
+    }
+    // every thread waits on the barrier (bounded); the CTA leaves together
+    // if any thread gave up, after waiting (bounded) for its other loads
+    const int fail = !mbar_wait_bounded(&bar[b], par);
+    if (__syncthreads_or(fail)) {
+      if (tid == 0) {
+        atomicExch(err, 1);
+        for (int j = k + 1; j < k + C::NBUF; ++j)
+          if (t + (j - k) * (int)gridDim.x < tg.ntiles)
+            mbar_wait_bounded(&bar[j % C::NBUF], (uint32_t)((j / C::NBUF) & 1));
       }
-      // every thread waits on the barrier (bounded); the CTA leaves together
-      // if any thread gave up
-      const int fail = !mbar_wait_bounded(&bar[b], par);
-      if (__syncthreads_or(fail)) {
-        if (tid == 0) {
-          atomicExch(err, 1);
-          if (tn < tg.ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
-        }
-        return;
-      }
-    } else {
-      issue_cp(tn, b ^ 1);  // prefetch (an empty group past the last tile)
-      cp_async_wait_1();    // this tile's group has landed (own copies)
-      __syncthreads();      // ... and everyone else's
+      return;
     }
 
     const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
@@ -434,7 +379,7 @@ template <bool RES, bool POT, int MR, int WY>
 cudaError_t launch_cfg(const TmaMaps& m, const StepArgs<float>& a, cudaStream_t s, int* err,
                        int num_sms) {
   using C = Cfg<RES, POT, MR, WY>;
-  auto kern = rk4_f32_tma<RES, POT, MR, WY, PHX_TILE_LOADER_TMA>;
+  auto kern = rk4_f32_tma<RES, POT, MR, WY>;
   static int configured_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
