@@ -69,9 +69,13 @@ typedef struct phx_params {
   int32_t precision;         /* 32 or 64: stencil arithmetic and storage */
   int32_t spinor;            /* 0: scalar psi; 1: two components psi_+, psi_- */
   int32_t reservoir;         /* 0/1: evolve n_c with Eq. (PULSE_res) */
-  int32_t tile;              /* FP32 scalar step kernel tile: 0 = automatic,
-                                1 = 64x64, 2 = 64x48, 3 = 64x32 region (TMA-fed
-                                persistent kernel), 9 = generic kernel */
+  int32_t tile;              /* FP32 scalar step kernel configuration:
+                                0 = autotune (the first phx_step_n times each
+                                configuration on the handle's own state, without
+                                changing it, synchronising the stream once; the
+                                choice is cached per grid shape), 1..5 = a fixed
+                                shared-memory region and thread shape of the
+                                TMA-fed persistent kernel, 9 = generic kernel */
   double hbar2_over_2m;      /* hbar^2/2m, meV um^2 */
   double g, g_x, g_r;        /* meV um^2 */
   double R;                  /* ps^-1 um^2 */
@@ -125,8 +129,9 @@ phx_status phx_set_state(phx_handle* h, const void* psi, const void* n,
 phx_status phx_get_state(phx_handle* h, void* psi, void* n, int on_device);
 
 /* Queue nsteps >= 0 RK4 steps (Eqs. rk4_K1-final, plus noise when
- * noise_var > 0).  Asynchronous on the stream; advances the step counter
- * and the FP64 simulated time t += dt on the device. */
+ * noise_var > 0).  Asynchronous on the stream (except the one-time autotune
+ * of tile = 0, see phx_params); advances the step counter and the FP64
+ * simulated time t += dt on the device. */
 phx_status phx_step_n(phx_handle* h, int64_t nsteps);
 
 /* FP64 norm N = dx dy sum_c |psi_c|^2 and energy

@@ -4,6 +4,9 @@
 
 #include <cmath>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -44,6 +47,7 @@ struct phx_handle {
   int num_sms = 0;
   int* err_dev = nullptr;      // set by kernels whose bounded waits gave up
   int tile_cfg = 0;            // chosen tile configuration of the FP32 scalar kernel
+  bool tuned = false;          // tile_cfg settled (explicit or autotuned)
   bool maps_ok = false;        // TMA tensor maps encoded for (tile_cfg, has_V)
   bool maps_V = false;
   TmaMaps maps[2];             // per current-state buffer
@@ -270,6 +274,68 @@ int choose_tile(const phx_handle* h) {
     }
   }
   return best;
+}
+
+// Process-wide autotune results: (device, nx, ny, bc_x, bc_y, reservoir,
+// potential) -> fastest tile configuration.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int, int>, int> g_tune;
+
+bool encode_maps(phx_handle* h);
+
+// Time every tile configuration of the FP32 scalar kernel on this handle's
+// own state and keep the fastest.  A step reads the current buffer and writes
+// the other one, so repeating it without swapping leaves the state intact.
+phx_status autotune(phx_handle* h, StepArgs<float> a) {
+  a.inject_timeout = 0;  // a test hook armed for the real step must not fire here
+  const auto key = std::make_tuple(h->device, h->p.nx, h->p.ny, h->p.bc_x, h->p.bc_y,
+                                   (int)h->m.reservoir, (int)h->has_V);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      h->tile_cfg = it->second;
+      h->maps_ok = false;
+      return PHX_OK;
+    }
+  }
+  const int cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64, TILE_64x32};
+  cudaEvent_t e0, e1;
+  PHX_CK(h, cudaEventCreate(&e0));
+  PHX_CK(h, cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int best = h->tile_cfg;
+  for (int cfg : cands) {
+    h->tile_cfg = cfg;
+    if (!encode_maps(h)) continue;
+    auto launch = [&]() {
+      return launch_rk4_tma_f32(cfg, h->m.reservoir, h->has_V, h->maps[h->cur], a, h->stream,
+                                h->err_dev, h->num_sms);
+    };
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cfg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tile_cfg = best;
+  h->maps_ok = false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return PHX_OK;
 }
 
 bool encode_maps(phx_handle* h) {
@@ -531,6 +597,13 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.parity = h->parity;
       a.inject_timeout = inj;
       if (h->tile_cfg != TILE_GENERIC && h->m.ncomp == 1) {
+        if (!h->tuned) {
+          if (h->p.tile == 0) {
+            phx_status ts = autotune(h, a);
+            if (ts != PHX_OK) return ts;
+          }
+          h->tuned = true;
+        }
         if (!h->maps_ok || h->maps_V != h->has_V) {
           if (!encode_maps(h)) return fail(h, PHX_ECUDA, "cuTensorMapEncodeTiled failed");
         }

@@ -418,6 +418,8 @@ TmaBox tma_box(int tile_cfg) {
   int MR = 4, WY = 16;
   if (tile_cfg == TILE_64x48) WY = 12;
   if (tile_cfg == TILE_64x32) WY = 8;
+  if (tile_cfg == TILE_64x48_M2) { MR = 2; WY = 24; }
+  if (tile_cfg == TILE_64x64_M2) { MR = 2; WY = 32; }
   const int RW = 64, RH = MR * WY;
   b.psi_w = 2 * (RW + 4);  // floats (interleaved complex)
   b.psi_h = RH + 2;
@@ -441,6 +443,8 @@ cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, const TmaMaps& 
   PHX_TMA_CASE(TILE_64x64, 4, 16)
   PHX_TMA_CASE(TILE_64x48, 4, 12)
   PHX_TMA_CASE(TILE_64x32, 4, 8)
+  PHX_TMA_CASE(TILE_64x48_M2, 2, 24)
+  PHX_TMA_CASE(TILE_64x64_M2, 2, 32)
 #undef PHX_TMA_CASE
   return cudaErrorInvalidValue;
 }

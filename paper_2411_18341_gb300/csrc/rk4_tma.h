@@ -9,7 +9,15 @@
 namespace phx {
 
 // Tile configurations (region columns x region rows; output = region - 6).
-enum { TILE_AUTO = 0, TILE_64x64 = 1, TILE_64x48 = 2, TILE_64x32 = 3, TILE_GENERIC = 9 };
+enum {
+  TILE_AUTO = 0,
+  TILE_64x64 = 1,     // 4 rows x 2 columns per thread, 16 warps
+  TILE_64x48 = 2,     // 4 x 2, 12 warps
+  TILE_64x32 = 3,     // 4 x 2, 8 warps
+  TILE_64x48_M2 = 4,  // 2 x 2, 24 warps
+  TILE_64x64_M2 = 5,  // 2 x 2, 32 warps
+  TILE_GENERIC = 9
+};
 
 struct TmaMaps {
   CUtensorMap psi, n, P, V;
