@@ -187,6 +187,44 @@ const char* phx_status_string(phx_status s);
 /* Free the handle and its device memory.  NULL-safe. */
 void phx_destroy(phx_handle* h);
 
+/* ---- batches: many independent instances, one launch per RK4 step -------
+ *
+ * A batch holds `count` independent FP32 scalar problems (Eq. 1 /
+ * Eq. PULSE_psi with one component; all with or all without reservoir),
+ * each with its own grid size, domain, coefficients, dt, seed and instance
+ * id.  phx_batch_step_n advances every member by the same number of RK4
+ * steps: each step is ONE persistent kernel launch over the tiles of all
+ * members (a per-tile instance table), replayed from a CUDA graph, with the
+ * tile configuration picked by an autotuner on the first call (which
+ * synchronises the stream once).  Members are addressed by index 0..count-1;
+ * their arrays follow the single-handle conventions above.  params[0].stream
+ * is used for all work.  Member i's FP64 simulated time is t0_i + steps*dt_i
+ * accumulated on the device. */
+typedef struct phx_batch phx_batch;
+
+/* EINVAL: count < 1, any invalid member (see phx_create), precision != 32,
+ * spinor != 0, mixed reservoir flags, or a grid smaller than 8 x 8. */
+phx_status phx_batch_create(const phx_params* params, int32_t count, phx_batch** out);
+phx_status phx_batch_set_pump(phx_batch* b, int32_t i, const void* P, int on_device);
+/* V = NULL removes the member's potential; stepping requires that either all
+ * members or none have a potential (ESTATE otherwise). */
+phx_status phx_batch_set_potential(phx_batch* b, int32_t i, const void* V, int on_device);
+phx_status phx_batch_set_state(phx_batch* b, int32_t i, const void* psi, const void* n,
+                               int on_device);
+phx_status phx_batch_get_state(phx_batch* b, int32_t i, void* psi, void* n, int on_device);
+phx_status phx_batch_step_n(phx_batch* b, int64_t nsteps);
+/* Per-member FP64 norm and energy (arrays of count doubles; either may be
+ * NULL), same definitions as phx_norm_energy.  Synchronises. */
+phx_status phx_batch_norm_energy(phx_batch* b, double* norms, double* energies);
+/* Per-member steady-state residuals (arrays of count; any may be NULL). */
+phx_status phx_batch_residual(phx_batch* b, double* r_psi, double* r_n, double* omega);
+/* Common step counter and per-member FP64 times (t: count doubles or NULL). */
+phx_status phx_batch_time(phx_batch* b, int64_t* step, double* t);
+/* Tile configuration in use (0 until the first step), see phx_params.tile. */
+int32_t phx_batch_tile(const phx_batch* b);
+const char* phx_batch_last_error(const phx_batch* b);
+void phx_batch_destroy(phx_batch* b);
+
 /* Generate the noise field xi_c(seed, step, instance, site) that a step
  * with these keys adds, as float32 (re, im) pairs in out_device
  * [ncomp][ny][nx][2] (device memory, caller-owned).  Asynchronous on stream.

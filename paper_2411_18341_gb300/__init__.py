@@ -79,6 +79,23 @@ _SIGS = {
     "phx_noise_sample": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                         ctypes.c_void_p]),
+    "phx_batch_create": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "phx_batch_set_pump": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
+    "phx_batch_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_int]),
+    "phx_batch_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int]),
+    "phx_batch_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int]),
+    "phx_batch_step_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "phx_batch_norm_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "phx_batch_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "phx_batch_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
+    "phx_batch_tile": (ctypes.c_int32, [ctypes.c_void_p]),
+    "phx_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "phx_batch_destroy": (None, [ctypes.c_void_p]),
     "phx_norm_energy_static": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.POINTER(ctypes.c_double),
@@ -295,6 +312,105 @@ def phx_norm_energy_static(p, psi, n=None, V=None):
     if st != PHX_OK:
         raise PhxError(st, "phx_norm_energy_static failed")
     return N.value, E.value
+
+
+# ------------------------------------------------------------------ batches
+
+class Batch:
+    """Owns a phx_batch*; remembers member sizes for argument checks."""
+
+    def __init__(self, ptr, plist):
+        self.ptr = ptr
+        self.sizes = [(p.nx, p.ny) for p in plist]
+        self.count = len(plist)
+        self.reservoir = bool(plist[0].reservoir)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().phx_batch_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def _bcheck(st, b):
+    if st != PHX_OK:
+        raise PhxError(st, lib().phx_batch_last_error(b.ptr if b is not None else None)
+                       .decode(errors="replace"))
+
+
+def phx_batch_create(params):
+    arr = (phx_params * len(params))(*params)
+    out = ctypes.c_void_p()
+    st = lib().phx_batch_create(arr, len(params), ctypes.byref(out))
+    if st != PHX_OK:
+        raise PhxError(st, lib().phx_batch_last_error(None).decode(errors="replace"))
+    return Batch(out, list(params))
+
+
+def phx_batch_set_pump(b, i, P):
+    nx, ny = b.sizes[i]
+    a, dev, k = _ptr(P, np.float32, False, nx * ny)
+    _bcheck(lib().phx_batch_set_pump(b.ptr, i, a, dev), b)
+
+
+def phx_batch_set_potential(b, i, V):
+    nx, ny = b.sizes[i]
+    a, dev, k = _ptr(V, np.float32, False, nx * ny)
+    _bcheck(lib().phx_batch_set_potential(b.ptr, i, a, dev), b)
+
+
+def phx_batch_set_state(b, i, psi, n=None):
+    nx, ny = b.sizes[i]
+    a, da, ka = _ptr(psi, np.float32, True, nx * ny)
+    c, dc, kc = _ptr(n, np.float32, False, nx * ny)
+    dev = da if a is not None else dc
+    _bcheck(lib().phx_batch_set_state(b.ptr, i, a, c, dev), b)
+
+
+def phx_batch_get_state(b, i, psi_out=None, n_out=None):
+    nx, ny = b.sizes[i]
+    a, da, ka = _ptr(psi_out, np.float32, True, nx * ny)
+    c, dc, kc = _ptr(n_out, np.float32, False, nx * ny)
+    dev = da if a is not None else dc
+    _bcheck(lib().phx_batch_get_state(b.ptr, i, a, c, dev), b)
+
+
+def phx_batch_step_n(b, nsteps):
+    _bcheck(lib().phx_batch_step_n(b.ptr, int(nsteps)), b)
+
+
+def phx_batch_norm_energy(b):
+    N = np.zeros(b.count)
+    E = np.zeros(b.count)
+    _bcheck(lib().phx_batch_norm_energy(b.ptr, N.ctypes.data, E.ctypes.data), b)
+    return N, E
+
+
+def phx_batch_residual(b):
+    r = np.zeros(b.count)
+    rn = np.zeros(b.count)
+    om = np.zeros(b.count)
+    _bcheck(lib().phx_batch_residual(b.ptr, r.ctypes.data, rn.ctypes.data, om.ctypes.data), b)
+    return r, rn, om
+
+
+def phx_batch_time(b):
+    s = ctypes.c_int64()
+    t = np.zeros(b.count)
+    _bcheck(lib().phx_batch_time(b.ptr, ctypes.byref(s), t.ctypes.data), b)
+    return s.value, t
+
+
+def phx_batch_tile(b):
+    return int(lib().phx_batch_tile(b.ptr))
+
+
+def phx_batch_destroy(b):
+    if b.ptr:
+        lib().phx_batch_destroy(b.ptr)
+        b.ptr = None
 
 
 # ------------------------------------------------------------- conveniences

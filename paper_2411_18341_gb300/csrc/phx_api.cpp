@@ -50,7 +50,8 @@ struct phx_handle {
   bool tuned = false;          // tile_cfg settled (explicit or autotuned)
   bool maps_ok = false;        // TMA tensor maps encoded for (tile_cfg, has_V)
   bool maps_V = false;
-  TmaMaps maps[2];             // per current-state buffer
+  TileInst h_inst;             // descriptor of this handle for the persistent kernel
+  TileInst* d_inst = nullptr;  // its device copy
   std::string err;
 };
 
@@ -80,79 +81,9 @@ phx_status cuda_fail(phx_handle* h, cudaError_t e, const char* what) {
 
 bool is_finite(double x) { return std::isfinite(x); }
 
-// Largest |eigenvalue| of the linear Hermitian operator -kappa Lap (+ TE-TM)
-// over the grid's modes: periodic axis phases 2 pi m/N, zero axis Dirichlet
-// phases pi m/(N+1).  K^2 = (2 - 2cos a)/d^2, s^2 = sin^2(a)/d^2; the TE-TM
-// 2x2 block at a mode has eigenvalues kappa(Kx^2+Ky^2) +- Delta
-// sqrt((Kx^2-Ky^2)^2 + 4 sx^2 sy^2).
-double spectral_radius(const phx_params& p) {
-  auto axis = [](int N, int bc, double d, std::vector<double>& K2,
-                 std::vector<double>& s2) {
-    const double pi = 3.14159265358979323846;
-    if (bc == PHX_BC_PERIODIC) {
-      for (int m = 0; m <= N / 2; ++m) {  // phases m and N-m coincide in K2, s2
-        double a = 2.0 * pi * m / N;
-        K2.push_back((2.0 - 2.0 * std::cos(a)) / (d * d));
-        s2.push_back(std::sin(a) * std::sin(a) / (d * d));
-      }
-    } else {
-      for (int m = 1; m <= N; ++m) {
-        double a = pi * m / (N + 1);
-        K2.push_back((2.0 - 2.0 * std::cos(a)) / (d * d));
-        s2.push_back(std::sin(a) * std::sin(a) / (d * d));
-      }
-    }
-  };
-  std::vector<double> kx, sx, ky, sy;
-  double dx = p.lx / p.nx, dy = p.ly / p.ny;
-  axis(p.nx, p.bc_x, dx, kx, sx);
-  axis(p.ny, p.bc_y, dy, ky, sy);
-  const double kap = p.hbar2_over_2m;
-  if (!(p.spinor && p.delta_lt != 0.0)) {
-    double mx = 0, my = 0;
-    for (double v : kx) mx = std::fmax(mx, v);
-    for (double v : ky) my = std::fmax(my, v);
-    return std::fabs(kap) * (mx + my);
-  }
-  const double D = std::fabs(p.delta_lt);
-  double best = 0.0;
-  for (size_t j = 0; j < ky.size(); ++j)
-    for (size_t i = 0; i < kx.size(); ++i) {
-      double lam = kap * (kx[i] + ky[j]);
-      double dd = kx[i] - ky[j];
-      double off = D * std::sqrt(dd * dd + 4.0 * sx[i] * sy[j]);
-      best = std::fmax(best, std::fmax(std::fabs(lam + off), std::fabs(lam - off)));
-    }
-  return best;
-}
-
 phx_status validate(const phx_params* p, double* dtmax_out) {
-  if (!p) return fail(nullptr, PHX_EINVAL, "params is NULL");
-  if (p->struct_size != sizeof(phx_params))
-    return fail(nullptr, PHX_EINVAL, "params.struct_size mismatch (call phx_params_init)");
-  if (p->nx < 1 || p->ny < 1) return fail(nullptr, PHX_EINVAL, "nx, ny must be >= 1");
-  if ((long long)p->nx * p->ny > (1ll << 31) - 1)
-    return fail(nullptr, PHX_EINVAL, "nx*ny must be < 2^31");
-  if (!(p->lx > 0) || !(p->ly > 0) || !is_finite(p->lx) || !is_finite(p->ly))
-    return fail(nullptr, PHX_EINVAL, "lx, ly must be positive and finite");
-  if ((p->bc_x != PHX_BC_PERIODIC && p->bc_x != PHX_BC_ZERO) ||
-      (p->bc_y != PHX_BC_PERIODIC && p->bc_y != PHX_BC_ZERO))
-    return fail(nullptr, PHX_EINVAL, "bc_x, bc_y must be PHX_BC_PERIODIC or PHX_BC_ZERO");
-  if (p->precision != 32 && p->precision != 64)
-    return fail(nullptr, PHX_EINVAL, "precision must be 32 or 64");
-  if ((p->spinor != 0 && p->spinor != 1) || (p->reservoir != 0 && p->reservoir != 1))
-    return fail(nullptr, PHX_EINVAL, "spinor and reservoir must be 0 or 1");
-  const double c[] = {p->hbar2_over_2m, p->g, p->g_x, p->g_r, p->R, p->gamma_c,
-                      p->gamma_r, p->delta_lt, p->dt, p->noise_var};
-  for (double v : c)
-    if (!is_finite(v)) return fail(nullptr, PHX_EINVAL, "coefficients must be finite");
-  if (p->hbar2_over_2m < 0) return fail(nullptr, PHX_EINVAL, "hbar2_over_2m must be >= 0");
-  if (!p->spinor && (p->g_x != 0.0 || p->delta_lt != 0.0))
-    return fail(nullptr, PHX_EINVAL, "g_x and delta_lt need spinor = 1");
-  if (p->noise_var < 0) return fail(nullptr, PHX_EINVAL, "noise_var must be >= 0");
-  double lam = spectral_radius(*p);
-  double dtmax = lam > 0 ? 2.0 * std::sqrt(2.0) * HBAR / lam : INFINITY;
-  if (dtmax_out) *dtmax_out = dtmax;
+  const char* msg = check_params(p, dtmax_out);
+  if (msg) return fail(nullptr, PHX_EINVAL, msg);
   return PHX_OK;
 }
 
@@ -173,88 +104,25 @@ void free_all(phx_handle* h) {
   if (h->red_dev) cudaFree(h->red_dev);
   if (h->red_host) cudaFreeHost(h->red_host);
   if (h->err_dev) cudaFree(h->err_dev);
+  if (h->d_inst) cudaFree(h->d_inst);
   cudaSetDevice(prev);
 }
 
-// Copy a user array (ncomp planes of ny x nx elements of `elem` bytes) into
-// the padded interior of `dst`, then refresh the ghost ring.
 phx_status upload(phx_handle* h, void* dst, const void* src, int nplanes,
                   size_t elem, int on_device) {
-  const Geometry& g = h->geo;
-  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  for (int c = 0; c < nplanes; ++c) {
-    char* d = static_cast<char*>(dst) +
-              ((size_t)c * g.plane + (size_t)HALO * g.pitch + HALO) * elem;
-    const char* s = static_cast<const char*>(src) + (size_t)c * g.nx * g.ny * elem;
-    PHX_CK(h, cudaMemcpy2DAsync(d, (size_t)g.pitch * elem, s, (size_t)g.nx * elem,
-                                (size_t)g.nx * elem, g.ny, kind, h->stream));
-  }
-  PHX_CK(h, launch_fill_ghosts(dst, (int)elem, nplanes, g, h->stream));
+  PHX_CK(h, upload_field(dst, src, nplanes, elem, h->geo, on_device, h->stream));
   return PHX_OK;
 }
 
 phx_status download(phx_handle* h, void* dst, const void* src, int nplanes,
                     size_t elem, int on_device) {
-  const Geometry& g = h->geo;
-  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  for (int c = 0; c < nplanes; ++c) {
-    const char* s = static_cast<const char*>(src) +
-                    ((size_t)c * g.plane + (size_t)HALO * g.pitch + HALO) * elem;
-    char* d = static_cast<char*>(dst) + (size_t)c * g.nx * g.ny * elem;
-    PHX_CK(h, cudaMemcpy2DAsync(d, (size_t)g.nx * elem, s, (size_t)g.pitch * elem,
-                                (size_t)g.nx * elem, g.ny, kind, h->stream));
-  }
+  PHX_CK(h, download_field(dst, src, nplanes, elem, h->geo, on_device, h->stream));
   return PHX_OK;
 }
 
-Coeffs make_coeffs(const phx_params& p) {
-  Coeffs k;
-  const double dx = p.lx / p.nx, dy = p.ly / p.ny;
-  const double kh = p.hbar2_over_2m / HBAR;
-  k.ax = -kh / (dx * dx);
-  k.ay = -kh / (dy * dy);
-  k.a0 = 2.0 * kh * (1.0 / (dx * dx) + 1.0 / (dy * dy));
-  k.g = p.g / HBAR;
-  k.gx = p.g_x / HBAR;
-  k.gr = p.g_r / HBAR;
-  k.inv_hbar = 1.0 / HBAR;
-  k.half_R = 0.5 * p.R;
-  k.half_gc = 0.5 * p.gamma_c;
-  k.R_ = p.R;
-  k.gamma_r = p.gamma_r;
-  k.tx = p.delta_lt / (HBAR * dx * dx);
-  k.ty = p.delta_lt / (HBAR * dy * dy);
-  k.txy = p.delta_lt / (2.0 * HBAR * dx * dy);
-  k.dt = p.dt;
-  return k;
-}
-
 ReduceArgs make_reduce_args(const phx_handle* h) {
-  ReduceArgs r;
-  const phx_params& p = h->p;
-  const double dx = p.lx / p.nx, dy = p.ly / p.ny;
-  r.geo = h->geo;
-  r.psi = h->psi[h->cur];
-  r.n = h->m.reservoir ? h->n[h->cur] : nullptr;
-  r.P = h->P;
-  r.P_comp_stride = h->P_stride;
-  r.V = h->has_V ? h->V : nullptr;
-  r.idx2 = 1.0 / (dx * dx);
-  r.idy2 = 1.0 / (dy * dy);
-  r.ixy4 = 1.0 / (4.0 * dx * dy);
-  r.kappa = p.hbar2_over_2m;
-  r.g = p.g;
-  r.g_x = p.g_x;
-  r.g_r = p.g_r;
-  r.delta_lt = p.delta_lt;
-  r.R = p.R;
-  r.gamma_c = p.gamma_c;
-  r.gamma_r = p.gamma_r;
-  r.precision = p.precision;
-  r.ncomp = h->m.ncomp;
-  r.reservoir = h->m.reservoir;
-  r.tetm = h->m.tetm;
-  return r;
+  return reduce_args(h->p, h->geo, h->psi[h->cur], h->m.reservoir ? h->n[h->cur] : nullptr,
+                     h->P, h->P_stride, h->has_V ? h->V : nullptr);
 }
 
 // Tile configuration of the persistent FP32 scalar kernel: the one with the
@@ -282,12 +150,12 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int>, int> g_tune;
 
 bool encode_maps(phx_handle* h);
+TileArgs tile_args(phx_handle* h, int inj);
 
 // Time every tile configuration of the FP32 scalar kernel on this handle's
 // own state and keep the fastest.  A step reads the current buffer and writes
 // the other one, so repeating it without swapping leaves the state intact.
-phx_status autotune(phx_handle* h, StepArgs<float> a) {
-  a.inject_timeout = 0;  // a test hook armed for the real step must not fire here
+phx_status autotune(phx_handle* h) {
   const auto key = std::make_tuple(h->device, h->p.nx, h->p.ny, h->p.bc_x, h->p.bc_y,
                                    (int)h->m.reservoir, (int)h->has_V);
   {
@@ -308,9 +176,11 @@ phx_status autotune(phx_handle* h, StepArgs<float> a) {
   for (int cfg : cands) {
     h->tile_cfg = cfg;
     if (!encode_maps(h)) continue;
+    // a test hook armed for the real step must not fire here
+    const TileArgs ta = tile_args(h, 0);
+    const int grid = ta.ntiles < h->num_sms ? ta.ntiles : h->num_sms;
     auto launch = [&]() {
-      return launch_rk4_tma_f32(cfg, h->m.reservoir, h->has_V, h->maps[h->cur], a, h->stream,
-                                h->err_dev, h->num_sms);
+      return launch_rk4_tma_f32(cfg, h->m.reservoir, h->has_V, ta, h->stream, grid);
     };
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch();
@@ -338,33 +208,33 @@ phx_status autotune(phx_handle* h, StepArgs<float> a) {
   return PHX_OK;
 }
 
+// Fill the handle's instance descriptor for the current tile configuration
+// and queue its upload on the handle's stream.
 bool encode_maps(phx_handle* h) {
-  const Geometry& g = h->geo;
-  TmaBox b = tma_box(h->tile_cfg);
-  const int nc = h->m.ncomp;
-  for (int k = 0; k < 2; ++k) {
-    TmaMaps& m = h->maps[k];
-    std::memset(&m, 0, sizeof m);
-    if (!encode_map_f32(&m.psi, h->psi[k], 2ull * g.pitch, g.prow, nc, (unsigned long long)g.pitch * 8,
-                        (unsigned long long)g.plane * 8, b.psi_w, b.psi_h))
-      return false;
-    if (h->m.reservoir) {
-      if (!encode_map_f32(&m.n, h->n[k], g.pitch, g.prow, nc, (unsigned long long)g.pitch * 4,
-                          (unsigned long long)g.plane * 4, b.f_w, b.f_h))
-        return false;
-      if (!encode_map_f32(&m.P, h->P, g.pitch, g.prow, nc, (unsigned long long)g.pitch * 4,
-                          (unsigned long long)g.plane * 4, b.f_w, b.f_h))
-        return false;
-    }
-    if (h->has_V) {
-      if (!encode_map_f32(&m.V, h->V, g.pitch, g.prow, 1, (unsigned long long)g.pitch * 4,
-                          (unsigned long long)g.plane * 4, b.f_w, b.f_h))
-        return false;
-    }
-  }
+  if (!fill_tile_inst(h->h_inst, h->p, h->geo, h->psi, h->n, h->P, h->has_V ? h->V : nullptr,
+                      h->tile_cfg))
+    return false;
+  if (cudaMemcpyAsync(h->d_inst, &h->h_inst, sizeof(TileInst), cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess)
+    return false;
   h->maps_ok = true;
   h->maps_V = h->has_V;
   return true;
+}
+
+TileArgs tile_args(phx_handle* h, int inj) {
+  TileArgs ta;
+  ta.inst = h->d_inst;
+  ta.tile_inst = nullptr;
+  ta.ntiles = h->h_inst.tiles_x * h->h_inst.tiles_y;
+  ta.ninst = 1;
+  ta.cur = h->cur;
+  ta.clock = h->clock;
+  ta.parity = h->parity;
+  ta.t_inst = nullptr;
+  ta.err = h->err_dev;
+  ta.inject_timeout = inj;
+  return ta;
 }
 
 // Reads and clears the device error word (synchronises the stream).
@@ -450,14 +320,8 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
   h->m.reservoir = p->reservoir;
   h->m.tetm = (p->spinor && p->delta_lt != 0.0) ? 1 : 0;
   h->esize = p->precision == 32 ? 4 : 8;
-  Geometry& g = h->geo;
-  g.nx = p->nx;
-  g.ny = p->ny;
-  g.pitch = ((p->nx + 2 * HALO + PITCH_ALIGN - 1) / PITCH_ALIGN) * PITCH_ALIGN;
-  g.prow = p->ny + 2 * HALO;
-  g.plane = (long long)g.pitch * g.prow;
-  g.bc_x = p->bc_x;
-  g.bc_y = p->bc_y;
+  h->geo = padded_geometry(*p);
+  const Geometry& g = h->geo;
 
   auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
     if (take_injection(INJ_ALLOC)) return cudaErrorMemoryAllocation;
@@ -482,6 +346,7 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
   if (ce == cudaSuccess) ce = alloc((void**)&h->red_dev, 8 * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&h->red_host, 8 * sizeof(double));
   if (ce == cudaSuccess) ce = alloc((void**)&h->err_dev, sizeof(int));
+  if (ce == cudaSuccess) ce = alloc((void**)&h->d_inst, sizeof(TileInst));
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
   if (ce != cudaSuccess) {
     cudaGetLastError();
@@ -599,7 +464,7 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       if (h->tile_cfg != TILE_GENERIC && h->m.ncomp == 1) {
         if (!h->tuned) {
           if (h->p.tile == 0) {
-            phx_status ts = autotune(h, a);
+            phx_status ts = autotune(h);
             if (ts != PHX_OK) return ts;
           }
           h->tuned = true;
@@ -607,8 +472,9 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
         if (!h->maps_ok || h->maps_V != h->has_V) {
           if (!encode_maps(h)) return fail(h, PHX_ECUDA, "cuTensorMapEncodeTiled failed");
         }
-        e = launch_rk4_tma_f32(h->tile_cfg, h->m.reservoir, h->has_V, h->maps[h->cur], a,
-                               h->stream, h->err_dev, h->num_sms);
+        const TileArgs ta = tile_args(h, inj);
+        const int grid = ta.ntiles < h->num_sms ? ta.ntiles : h->num_sms;
+        e = launch_rk4_tma_f32(h->tile_cfg, h->m.reservoir, h->has_V, ta, h->stream, grid);
       } else {
         e = launch_rk4_step_f32(h->m, a, h->stream, h->p.tile);
       }

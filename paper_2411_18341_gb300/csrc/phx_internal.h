@@ -6,7 +6,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
+
+#include "../../include/phx.h"
 
 namespace phx {
 
@@ -138,6 +141,19 @@ cudaError_t launch_noise_sample(unsigned long long seed, long long step,
 // Test hooks armed by phx_debug_inject (consumed by the next matching event).
 enum { INJ_ALLOC = 1, INJ_LAUNCH = 2, INJ_TIMEOUT = 4 };
 bool take_injection(unsigned what);
+
+// ---- host helpers shared by handles and batches (common.cpp) -------------
+// nullptr if *p is valid (and *dtmax = RK4 stability limit), else a message
+const char* check_params(const phx_params* p, double* dtmax);
+double spectral_radius(const phx_params& p);
+Coeffs make_coeffs(const phx_params& p);
+Geometry padded_geometry(const phx_params& p);
+cudaError_t upload_field(void* dst, const void* src, int nplanes, size_t elem,
+                         const Geometry& g, int on_device, cudaStream_t s);
+cudaError_t download_field(void* dst, const void* src, int nplanes, size_t elem,
+                           const Geometry& g, int on_device, cudaStream_t s);
+ReduceArgs reduce_args(const phx_params& p, const Geometry& g, const void* psi, const void* n,
+                       const void* P, long long P_stride, const void* V);
 
 // Process-wide count of kernel launches issued by this library.
 void count_launch(unsigned n = 1);

@@ -116,17 +116,9 @@ struct Cfg {
   static constexpr int SMEM = NBUF * BUF_BYTES + PSI_BYTES + 128;
 };
 
-struct TileGeo {
-  int tiles_x, tiles_y, ntiles;
-};
-
 template <bool RES, bool POT, int MR, int WY>
 __global__ void __launch_bounds__(32 * WY, 1)
-rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
-            const __grid_constant__ CUtensorMap tm_n,
-            const __grid_constant__ CUtensorMap tm_P,
-            const __grid_constant__ CUtensorMap tm_V, const StepArgs<float> a,
-            const TileGeo tg, int* err) {
+rk4_f32_tma(const TileArgs ta) {
   using C = Cfg<RES, POT, MR, WY>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[3];
@@ -137,8 +129,6 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c0 = 2 * lane;   // region column of the micro-tile's first column
   const int r0 = MR * warp;  // region row of its first row
-  const Geometry& g = a.geo;
-
   auto psi_buf = [&](int b) { return reinterpret_cast<float2*>(base + b * C::BUF_BYTES); };
   auto f_buf = [&](int b, int f) {
     return reinterpret_cast<float*>(base + b * C::BUF_BYTES + C::PSI_BYTES + f * C::F_BYTES);
@@ -161,46 +151,54 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
+  // Instance of global tile t and the tile's index within that instance.
+  auto locate = [&](int t, const TileInst*& I, int& kx, int& ky) {
+    I = ta.inst + (ta.tile_inst ? ta.tile_inst[t] : 0);
+    const int lt = t - I->tile0;
+    kx = lt % I->tiles_x;
+    ky = lt / I->tiles_x;
+  };
   auto issue = [&](int t, int b) {
-    const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
+    const TileInst* I;
+    int kx, ky;
+    locate(t, I, kx, ky);
     const int xp = kx * C::TX;  // padded column of region column 0
     const int yp = ky * C::TY;  // padded row of region row -1
     mbar_arrive_expect_tx(&bar[b], C::TX_BYTES);
-    tma_load_3d(psi_buf(b), &tm_psi, 2 * (xp - 2), yp, 0, &bar[b]);
+    tma_load_3d(psi_buf(b), &I->psi[ta.cur], 2 * (xp - 2), yp, 0, &bar[b]);
     int f = 0;
     if (RES) {
-      tma_load_3d(f_buf(b, f++), &tm_n, xp & ~3, yp + 1, 0, &bar[b]);
-      tma_load_3d(f_buf(b, f++), &tm_P, xp & ~3, yp + 1, 0, &bar[b]);
+      tma_load_3d(f_buf(b, f++), &I->n[ta.cur], xp & ~3, yp + 1, 0, &bar[b]);
+      tma_load_3d(f_buf(b, f++), &I->P, xp & ~3, yp + 1, 0, &bar[b]);
     }
-    if (POT) tma_load_3d(f_buf(b, f++), &tm_V, xp & ~3, yp + 1, 0, &bar[b]);
+    if (POT) tma_load_3d(f_buf(b, f++), &I->V, xp & ~3, yp + 1, 0, &bar[b]);
   };
 
-  const long long step = a.clock->step[a.parity];
-  if (blockIdx.x == 0 && tid == 0) {
-    a.clock->step[a.parity ^ 1] = step + 1;
-    a.clock->t[a.parity ^ 1] = a.clock->t[a.parity] + a.dt64;
+  // FP64 simulated time: instance 0 in the clock, all instances in t_inst
+  const long long step = ta.clock->step[ta.parity];
+  if (blockIdx.x == 0) {
+    if (tid == 0) {
+      ta.clock->step[ta.parity ^ 1] = step + 1;
+      ta.clock->t[ta.parity ^ 1] = ta.clock->t[ta.parity] + ta.inst[0].dt64;
+    }
+    if (ta.t_inst)
+      for (int i = tid; i < ta.ninst; i += C::NT)
+        ta.t_inst[(ta.parity ^ 1) * ta.ninst + i] =
+            ta.t_inst[ta.parity * ta.ninst + i] + ta.inst[i].dt64;
   }
-
-  const CoeffsT<float>& q = a.k;
-  const float2 ax2 = f2(q.ax, q.ax), ay2 = f2(q.ay, q.ay);
-  const float2 a02 = f2(q.a0, q.a0);
-  const float cg = q.g, cgr = q.gr, cih = q.inv_hbar;
-  const float hR = q.half_R, hgc = q.half_gc, cR = q.R_;
-  const float cgam = q.gamma_r, dt = q.dt;
-  const float dt6 = dt / 6.0f;
 
   int t = blockIdx.x, k = 0;
   if (tid == 0) {  // prologue: the first NBUF-1 tiles
     for (int i = 0; i < C::NBUF - 1; ++i) {
       const int ti = t + i * (int)gridDim.x;
-      if (ti < tg.ntiles && !(i == 0 && a.inject_timeout)) issue(ti, i);
+      if (ti < ta.ntiles && !(i == 0 && ta.inject_timeout)) issue(ti, i);
     }
   }
-  for (; t < tg.ntiles; t += gridDim.x, ++k) {
+  for (; t < ta.ntiles; t += gridDim.x, ++k) {
     const int b = k % C::NBUF;
     const uint32_t par = (uint32_t)((k / C::NBUF) & 1);
     const int tn = t + (C::NBUF - 1) * (int)gridDim.x;
-    if (tid == 0 && tn < tg.ntiles) {
+    if (tid == 0 && tn < ta.ntiles) {
       fence_proxy_async();  // generic accesses of that buffer (previous tile) before TMA reuse
       issue(tn, (k + C::NBUF - 1) % C::NBUF);
     }
@@ -209,15 +207,27 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
     const int fail = !mbar_wait_bounded(&bar[b], par);
     if (__syncthreads_or(fail)) {
       if (tid == 0) {
-        atomicExch(err, 1);
+        atomicExch(ta.err, 1);
         for (int j = k + 1; j < k + C::NBUF; ++j)
-          if (t + (j - k) * (int)gridDim.x < tg.ntiles)
+          if (t + (j - k) * (int)gridDim.x < ta.ntiles)
             mbar_wait_bounded(&bar[j % C::NBUF], (uint32_t)((j / C::NBUF) & 1));
       }
       return;
     }
 
-    const int kx = t % tg.tiles_x, ky = t / tg.tiles_x;
+    const TileInst* I;
+    int kx, ky;
+    locate(t, I, kx, ky);
+    const Geometry g = I->geo;
+    float2* const psi_out = I->psi_buf[ta.cur ^ 1];
+    float* const n_out = I->n_buf[ta.cur ^ 1];
+    const CoeffsT<float> q = I->k;
+    const float2 ax2 = f2(q.ax, q.ax), ay2 = f2(q.ay, q.ay);
+    const float2 a02 = f2(q.a0, q.a0);
+    const float cg = q.g, cgr = q.gr, cih = q.inv_hbar;
+    const float hR = q.half_R, hgc = q.half_gc, cR = q.R_;
+    const float cgam = q.gamma_r, dt = q.dt;
+    const float dt6 = dt / 6.0f;
     const int xp = kx * C::TX;
     const int foff = xp & 3;
     float2* P0 = psi_buf(b);
@@ -328,7 +338,7 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
         o[j][i] = __ffma2_rn(d62, acc[j][i], p0[j][i]);
         on[j][i] = fmaf(dt6, na[j][i], n0[j][i]);
       }
-    if (a.noise.on) {  // grid-uniform branch: the generator is not issued when off
+    if (I->noise.on) {  // grid-uniform branch: the generator is not issued when off
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
         const int gy = gy0 + j;
@@ -338,7 +348,7 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
           const uint32_t site = (uint32_t)(((gy % g.ny + g.ny) % g.ny) * g.nx +
                                            (gx % g.nx + g.nx) % g.nx);
           float2 xi, unused;
-          nz_site(a.noise.seed, a.noise.instance, step, site, a.noise.scale, xi, unused, false);
+          nz_site(I->noise.seed, I->noise.instance, step, site, I->noise.scale, xi, unused, false);
           o[j][i].x = o[j][i].x + xi.x;
           o[j][i].y = o[j][i].y + xi.y;
         }
@@ -359,15 +369,15 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
       const bool edge_y = g.bc_y == BC_PERIODIC && (gy < HALO || gy >= g.ny - HALO);
       const long long roff = (long long)(gy + HALO) * g.pitch + gx0 + HALO;
       if (ok[0] && ok[1] && !edge_x && !edge_y) {
-        *reinterpret_cast<float4*>(a.psi_out + roff) =
+        *reinterpret_cast<float4*>(psi_out + roff) =
             make_float4(o[j][0].x, o[j][0].y, o[j][1].x, o[j][1].y);
-        if (RES) *reinterpret_cast<float2*>(a.n_out + roff) = f2(on[j][0], on[j][1]);
+        if (RES) *reinterpret_cast<float2*>(n_out + roff) = f2(on[j][0], on[j][1]);
       } else {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           if (!ok[i]) continue;
-          store_with_ghosts(a.psi_out, g, gx0 + i, gy, o[j][i]);
-          if (RES) store_with_ghosts(a.n_out, g, gx0 + i, gy, on[j][i]);
+          store_with_ghosts(psi_out, g, gx0 + i, gy, o[j][i]);
+          if (RES) store_with_ghosts(n_out, g, gx0 + i, gy, on[j][i]);
         }
       }
     }
@@ -376,8 +386,7 @@ rk4_f32_tma(const __grid_constant__ CUtensorMap tm_psi,
 }
 
 template <bool RES, bool POT, int MR, int WY>
-cudaError_t launch_cfg(const TmaMaps& m, const StepArgs<float>& a, cudaStream_t s, int* err,
-                       int num_sms) {
+cudaError_t launch_cfg(const TileArgs& ta, cudaStream_t s, int grid) {
   using C = Cfg<RES, POT, MR, WY>;
   auto kern = rk4_f32_tma<RES, POT, MR, WY>;
   static int configured_dev = -1;
@@ -389,11 +398,6 @@ cudaError_t launch_cfg(const TmaMaps& m, const StepArgs<float>& a, cudaStream_t 
     if (e != cudaSuccess) return e;
     configured_dev = dev;
   }
-  TileGeo tg;
-  tg.tiles_x = (a.geo.nx + 1 + C::TX - 1) / C::TX;
-  tg.tiles_y = (a.geo.ny + C::TY - 1) / C::TY;
-  tg.ntiles = tg.tiles_x * tg.tiles_y;
-  int grid = tg.ntiles < num_sms ? tg.ntiles : num_sms;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(grid);
   lc.blockDim = dim3(C::NT);
@@ -404,7 +408,7 @@ cudaError_t launch_cfg(const TmaMaps& m, const StepArgs<float>& a, cudaStream_t 
   at[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&lc, kern, m.psi, m.n, m.P, m.V, a, tg, err);
+  cudaError_t e = cudaLaunchKernelEx(&lc, kern, ta);
   count_launch();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -430,15 +434,14 @@ TmaBox tma_box(int tile_cfg) {
   return b;
 }
 
-cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, const TmaMaps& m,
-                               const StepArgs<float>& a, cudaStream_t s, int* err,
-                               int num_sms) {
-#define PHX_TMA_CASE(CFG, MR, WY)                                                   \
-  if (tile_cfg == CFG) {                                                            \
-    if (res && pot) return launch_cfg<true, true, MR, WY>(m, a, s, err, num_sms);   \
-    if (res) return launch_cfg<true, false, MR, WY>(m, a, s, err, num_sms);         \
-    if (pot) return launch_cfg<false, true, MR, WY>(m, a, s, err, num_sms);         \
-    return launch_cfg<false, false, MR, WY>(m, a, s, err, num_sms);                 \
+cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, const TileArgs& ta,
+                               cudaStream_t s, int grid) {
+#define PHX_TMA_CASE(CFG, MR, WY)                                            \
+  if (tile_cfg == CFG) {                                                     \
+    if (res && pot) return launch_cfg<true, true, MR, WY>(ta, s, grid);      \
+    if (res) return launch_cfg<true, false, MR, WY>(ta, s, grid);            \
+    if (pot) return launch_cfg<false, true, MR, WY>(ta, s, grid);            \
+    return launch_cfg<false, false, MR, WY>(ta, s, grid);                    \
   }
   PHX_TMA_CASE(TILE_64x64, 4, 16)
   PHX_TMA_CASE(TILE_64x48, 4, 12)

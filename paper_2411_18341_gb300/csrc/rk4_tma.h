@@ -19,8 +19,33 @@ enum {
   TILE_GENERIC = 9
 };
 
-struct TmaMaps {
-  CUtensorMap psi, n, P, V;
+// One problem instance as the persistent step kernel sees it (device memory,
+// read-only during a launch).  A single handle is a one-instance table; a
+// batch has one entry per member.  Tensor maps must be 64-byte aligned.
+struct alignas(128) TileInst {
+  CUtensorMap psi[2];   // load maps of the psi buffers 0 and 1
+  CUtensorMap n[2];     // load maps of the n buffers 0 and 1
+  CUtensorMap P, V;
+  float2* psi_buf[2];   // the psi buffers (outputs go to buffer cur ^ 1)
+  float* n_buf[2];
+  Geometry geo;
+  CoeffsT<float> k;
+  NoiseKey noise;
+  double dt64;          // FP64 step for the simulated-time accumulator
+  int tiles_x, tiles_y; // tiles of this instance for the chosen configuration
+  int tile0;            // index of its first tile in the global tile list
+};
+
+struct TileArgs {
+  const TileInst* inst;  // device array of ninst instances
+  const int* tile_inst;  // instance of each global tile (nullptr: instance 0)
+  int ntiles, ninst;
+  int cur;               // input buffer of this step
+  DevClock* clock;       // step counter and FP64 time of instance 0
+  int parity;
+  double* t_inst;        // [2][ninst] FP64 times of all instances, or nullptr
+  int* err;              // set when a bounded wait gives up
+  int inject_timeout;    // test hook: leave the first tile's barrier unarmed
 };
 
 struct TmaBox {
@@ -36,8 +61,12 @@ bool encode_map_f32(CUtensorMap* map, void* base, unsigned long long w,
                     unsigned long long row_bytes, unsigned long long plane_bytes,
                     unsigned box_w, unsigned box_h);
 
-cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, const TmaMaps& m,
-                               const StepArgs<float>& a, cudaStream_t s, int* err,
-                               int num_sms);
+// Build the descriptor of one instance (host memory) for a tile
+// configuration; false if a tensor map cannot be encoded.
+bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* const psi[2],
+                    void* const n[2], void* P, void* V, int tile_cfg);
+
+cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, const TileArgs& ta,
+                               cudaStream_t s, int grid);
 
 }  // namespace phx
