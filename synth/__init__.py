@@ -201,3 +201,65 @@ def random_state(ncomp, ny, nx, seed, amp=1.0, reservoir=True, smooth=False):
     P = rng.uniform(0.0, 5.0, size=(ncomp, ny, nx)) if reservoir else None
     V = rng.uniform(-1.0, 1.0, size=(ny, nx))
     return psi, n, P, V
+
+
+# ------------------------------------------------------------ FNO inputs
+
+FNO_SCALE_PSI = 5.0    # output normalisation of Re/Im psi (|psi| ~ 5 at 1-3 P_thr)
+FNO_SCALE_N = 15.0     # output normalisation of n (n ~ gamma_c / R = 15)
+
+
+def fno_init_weights(shapes, seed=0, channels=32):
+    """Seeded initial parameters for the flat layout given by `shapes`
+    [(name, shape), ...]: spectral weights ~ U[0, 1/(C*C)) (Li et al.),
+    dense weights ~ U[-1/sqrt(fan_in), 1/sqrt(fan_in)), biases 0."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in shapes:
+        n = int(np.prod(shape))
+        if name.startswith("R"):
+            parts.append(rng.uniform(0.0, 1.0 / (channels * channels), n))
+        elif len(shape) == 2:
+            bound = 1.0 / np.sqrt(shape[0])
+            parts.append(rng.uniform(-bound, bound, n))
+        else:
+            parts.append(np.zeros(n))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def fno_features(P, length, pump_threshold):
+    """Network input [B, H, W, 3]: (P / P_thr, x / (L/2), y / (L/2))."""
+    P = np.asarray(P, np.float64)
+    if P.ndim == 2:
+        P = P[None]
+    B, H, W = P.shape
+    X, Y = mesh(W, H, length, length)
+    a = np.empty((B, H, W, 3), np.float32)
+    a[..., 0] = P / pump_threshold
+    a[..., 1] = X / (0.5 * length)
+    a[..., 2] = Y / (0.5 * length)
+    return a
+
+
+def fno_targets(psi, n):
+    """Target [B, H, W, 3] = (Re psi, Im psi, n) scaled, with the global phase
+    removed (psi multiplied by exp(-i arg sum psi))."""
+    psi = np.asarray(psi)
+    if psi.ndim == 2:
+        psi = psi[None]
+        n = np.asarray(n)[None]
+    out = np.empty(psi.shape + (3,), np.float32)
+    for b in range(psi.shape[0]):
+        s = psi[b].sum()
+        ph = np.exp(-1j * np.angle(s)) if abs(s) > 0 else 1.0
+        q = psi[b] * ph
+        out[b, ..., 0] = q.real / FNO_SCALE_PSI
+        out[b, ..., 1] = q.imag / FNO_SCALE_PSI
+        out[b, ..., 2] = np.asarray(n[b]) / FNO_SCALE_N
+    return out
+
+
+def fno_state_from_output(u):
+    """Inverse of fno_targets for one sample [H, W, 3] -> (psi, n)."""
+    u = np.asarray(u, np.float64)
+    return (u[..., 0] + 1j * u[..., 1]) * FNO_SCALE_PSI, u[..., 2] * FNO_SCALE_N
