@@ -262,6 +262,88 @@ phx_status phx_norm_energy_static(const phx_params* p, const void* psi,
                                   const void* n, const void* V, double* norm,
                                   double* energy);
 
+/* ---------------------------------------------------------------------
+ * Learned warm start: Fourier neural operator (Li et al., "Fourier Neural
+ * Operator for Parametric Partial Differential Equations", 2020) mapping a
+ * pump image to an approximate steady state (psi, n), used as the initial
+ * condition of the RK4 relaxation.  The paper has no such component; it is
+ * an extension of its steady-state workflow (time evolution until the
+ * state stops changing, Sec. V).
+ *
+ *   v0 = a W_lift + b_lift;  v_{l+1} = sigma(K_l v_l + v_l W_l + b_l)
+ *   (no sigma after the last layer);  u = sigma(v_L Q1 + q1) Q2 + q2;
+ *   K v = irfft2(R . rfft2(v)) on kx in [0, modes_x), ky in
+ *   [0, modes_y/2) U [height - modes_y/2, height); sigma = exact GELU;
+ *   loss = mean of (u - target)^2 over all output elements.
+ *
+ * Tensors are channels-last FP32 [batch][height][width][channels] in
+ * device memory (caller-owned).  The flat FP32 parameter vector is, in
+ * order: W_lift [in, C], b_lift [C]; per layer Rr [modes_y][modes_x][C][C],
+ * Ri (same), W [C][C], b [C]; Q1 [C][P], q1 [P], Q2 [P][out], q2 [out]
+ * (mode row my < modes_y/2 is ky = my, else ky = height - modes_y + my).
+ * Every contraction runs on the tensor cores with BF16 operands and FP32
+ * accumulation; activations and parameters are stored in FP32.  Work is
+ * queued on config.stream; calls returning host values synchronise it.
+ * Errors: EINVAL (NULL pointer, bad configuration, batch outside
+ * [1, max_batch]), ENOMEM, ECUDA; message in phx_fno_last_error.
+ * --------------------------------------------------------------------- */
+typedef struct phx_fno_config {
+  uint32_t struct_size;      /* = sizeof(phx_fno_config); set by phx_fno_config_init */
+  int32_t height, width;     /* grid (H rows = y, W columns = x) */
+  int32_t channels;          /* C, hidden width (<= 256) */
+  int32_t layers;            /* spectral layers, 1..8 */
+  int32_t modes_x;           /* kept kx modes, <= width/2 */
+  int32_t modes_y;           /* kept ky modes (even, <= height), half low and half high */
+  int32_t in_channels, out_channels, proj_hidden;  /* out, P <= 256 */
+  int32_t max_batch;         /* activations are allocated for this many samples */
+  void* stream;              /* cudaStream_t */
+} phx_fno_config;
+
+typedef struct phx_fno phx_fno;
+
+/* Defaults: 256 x 256, C = 32, 4 layers, 16 x 32 modes, 3 -> 3 channels,
+ * P = 64, max_batch 8, stream NULL. */
+phx_status phx_fno_config_init(phx_fno_config* c);
+/* Allocates parameters (uninitialised until phx_fno_set_params), Adam
+ * moments, DFT tables and activations for max_batch samples. */
+phx_status phx_fno_create(const phx_fno_config* c, phx_fno** out);
+int64_t phx_fno_num_params(const phx_fno* f);
+/* Copies the flat parameters in and resets the Adam moments and step. */
+phx_status phx_fno_set_params(phx_fno* f, const float* w, int on_device);
+phx_status phx_fno_get_params(phx_fno* f, float* w, int on_device);
+/* out [batch][H][W][out] = u(in [batch][H][W][in]); asynchronous. */
+phx_status phx_fno_forward(phx_fno* f, const float* in, float* out, int32_t batch);
+/* loss (host, may be NULL) and, when grad != NULL, the gradient with
+ * respect to the flat parameters into grad (device, num_params floats).
+ * Deterministic: fixed-order reductions, no atomics. */
+phx_status phx_fno_loss_grad(phx_fno* f, const float* in, const float* target,
+                             int32_t batch, double* loss, float* grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * mini-batch; loss (before the update) returned when non-NULL. */
+phx_status phx_fno_train_step(phx_fno* f, const float* in, const float* target,
+                              int32_t batch, float lr, double* loss);
+const char* phx_fno_last_error(const phx_fno* f);
+void phx_fno_destroy(phx_fno* f);
+
+/* Network input and output maps (device arrays, caller-owned, asynchronous
+ * on `stream`; messages in phx_fno_last_error(NULL)).
+ * phx_fno_features: P [batch][height][width] -> out [batch][height][width][3]
+ *   = (P / p_thr, x / (lx/2), y / (ly/2)), cell positions -l/2 + i l/n.
+ * phx_fno_targets: psi [batch][height][width] complex (re, im) and n (same
+ *   shape) -> out [..][3] = (Re, Im of psi e^{-i arg sum psi}) / scale_psi,
+ *   n / scale_n: the global phase of a stationary state is arbitrary, so the
+ *   target fixes it (sum in FP64, fixed order; batch <= 65535).
+ * phx_fno_to_state: u [..][3] -> psi = (u0 + i u1) scale_psi,
+ *   n = max(u2, 0) scale_n (n may be NULL). */
+phx_status phx_fno_features(const float* P, int32_t batch, int32_t height, int32_t width,
+                            double lx, double ly, double p_thr, float* out, void* stream);
+phx_status phx_fno_targets(const float* psi, const float* n, int32_t batch, int32_t height,
+                           int32_t width, double scale_psi, double scale_n, float* out,
+                           void* stream);
+phx_status phx_fno_to_state(const float* u, int32_t batch, int32_t height, int32_t width,
+                            double scale_psi, double scale_n, float* psi, float* n,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,18 @@ class phx_params(ctypes.Structure):
     ]
 
 
+class phx_fno_config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+        ("channels", ctypes.c_int32), ("layers", ctypes.c_int32),
+        ("modes_x", ctypes.c_int32), ("modes_y", ctypes.c_int32),
+        ("in_channels", ctypes.c_int32), ("out_channels", ctypes.c_int32),
+        ("proj_hidden", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 _lib = None
 
 _SIGS = {
@@ -100,6 +112,27 @@ _SIGS = {
                                               ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double)]),
+    "phx_fno_config_init": (ctypes.c_int, [ctypes.POINTER(phx_fno_config)]),
+    "phx_fno_create": (ctypes.c_int, [ctypes.POINTER(phx_fno_config), ctypes.POINTER(ctypes.c_void_p)]),
+    "phx_fno_num_params": (ctypes.c_int64, [ctypes.c_void_p]),
+    "phx_fno_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "phx_fno_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "phx_fno_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "phx_fno_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "phx_fno_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
+    "phx_fno_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "phx_fno_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "phx_fno_targets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "phx_fno_to_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "phx_fno_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -425,3 +458,158 @@ def params_from_dict(d, precision=32, stream=None, tile=0):
     kw["spinor"] = int(bool(kw.get("spinor", 0)))
     kw["reservoir"] = int(bool(kw.get("reservoir", 0)))
     return phx_params_init(precision=precision, stream=stream or 0, tile=tile, **kw)
+
+
+# -------------------------------------------------------- FNO warm start
+
+FNO_CONFIG_KEYS = ("height", "width", "channels", "layers", "modes_x", "modes_y",
+                   "in_channels", "out_channels", "proj_hidden", "max_batch")
+
+
+class Fno:
+    """Owns a phx_fno*; remembers the configuration for argument checks."""
+
+    def __init__(self, ptr, cfg):
+        self.ptr = ptr
+        self.cfg = {k: int(getattr(cfg, k)) for k in FNO_CONFIG_KEYS}
+        self.num_params = int(lib().phx_fno_num_params(ptr))
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().phx_fno_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def _fcheck(st, f):
+    if st != PHX_OK:
+        raise PhxError(st, lib().phx_fno_last_error(f.ptr if f is not None else None)
+                       .decode(errors="replace"))
+
+
+def _dev_f32(t, numel, what):
+    """Pointer of a contiguous float32 CUDA tensor of `numel` elements."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % what)
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (what, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def phx_fno_create(stream=None, **kw):
+    c = phx_fno_config()
+    _fcheck(lib().phx_fno_config_init(ctypes.byref(c)), None)
+    for k, v in kw.items():
+        if k not in FNO_CONFIG_KEYS:
+            raise KeyError(k)
+        setattr(c, k, int(v))
+    c.stream = stream or 0
+    out = ctypes.c_void_p()
+    _fcheck(lib().phx_fno_create(ctypes.byref(c), ctypes.byref(out)), None)
+    return Fno(out, c)
+
+
+def _fno_io(f, x, batch, channels, what):
+    c = f.cfg
+    return _dev_f32(x, batch * c["height"] * c["width"] * channels, what)
+
+
+def phx_fno_set_params(f, w):
+    a, dev, keep = _ptr(w, np.float32, False, f.num_params)
+    _fcheck(lib().phx_fno_set_params(f.ptr, a, dev), f)
+
+
+def phx_fno_get_params(f, out=None):
+    if out is None:
+        out = np.empty(f.num_params, np.float32)
+    a, dev, keep = _ptr(out, np.float32, False, f.num_params)
+    _fcheck(lib().phx_fno_get_params(f.ptr, a, dev), f)
+    return out
+
+
+def phx_fno_forward(f, x, out):
+    """out[B,H,W,Cout] = FNO(x[B,H,W,Cin]); both float32 CUDA tensors."""
+    B = x.shape[0]
+    _fcheck(lib().phx_fno_forward(f.ptr, _fno_io(f, x, B, f.cfg["in_channels"], "input"),
+                                  _fno_io(f, out, B, f.cfg["out_channels"], "output"), B), f)
+    return out
+
+
+def phx_fno_loss_grad(f, x, target, grad=None):
+    """Loss (float) and, into `grad` (float32 CUDA tensor), the gradient."""
+    B = x.shape[0]
+    loss = ctypes.c_double()
+    g = _dev_f32(grad, f.num_params, "grad") if grad is not None else None
+    _fcheck(lib().phx_fno_loss_grad(f.ptr, _fno_io(f, x, B, f.cfg["in_channels"], "input"),
+                                    _fno_io(f, target, B, f.cfg["out_channels"], "target"), B,
+                                    ctypes.byref(loss), g), f)
+    return loss.value
+
+
+def phx_fno_train_step(f, x, target, lr):
+    B = x.shape[0]
+    loss = ctypes.c_double()
+    _fcheck(lib().phx_fno_train_step(f.ptr, _fno_io(f, x, B, f.cfg["in_channels"], "input"),
+                                     _fno_io(f, target, B, f.cfg["out_channels"], "target"), B,
+                                     float(lr), ctypes.byref(loss)), f)
+    return loss.value
+
+
+def phx_fno_destroy(f):
+    if f.ptr:
+        lib().phx_fno_destroy(f.ptr)
+        f.ptr = None
+
+
+def _cdev(t, dtype, numel, what):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous %s CUDA tensor" % (what, dtype))
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (what, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def phx_fno_features(P, lx, ly, p_thr, out, stream=None):
+    """P [B,H,W] float32 CUDA -> out [B,H,W,3] float32 CUDA."""
+    import torch
+    B, H, W = P.shape
+    _fcheck(lib().phx_fno_features(_cdev(P, torch.float32, B * H * W, "P"), B, H, W, float(lx),
+                                   float(ly), float(p_thr), _cdev(out, torch.float32, 3 * B * H * W, "out"),
+                                   _stream_ptr(stream)), None)
+    return out
+
+
+def phx_fno_targets(psi, n, scale_psi, scale_n, out, stream=None):
+    """psi [B,H,W] complex64, n [B,H,W] float32 -> out [B,H,W,3] float32."""
+    import torch
+    B, H, W = psi.shape
+    _fcheck(lib().phx_fno_targets(_cdev(psi, torch.complex64, B * H * W, "psi"),
+                                  _cdev(n, torch.float32, B * H * W, "n"), B, H, W,
+                                  float(scale_psi), float(scale_n),
+                                  _cdev(out, torch.float32, 3 * B * H * W, "out"), _stream_ptr(stream)),
+            None)
+    return out
+
+
+def phx_fno_to_state(u, scale_psi, scale_n, psi, n=None, stream=None):
+    """u [B,H,W,3] float32 -> psi [B,H,W] complex64, n [B,H,W] float32."""
+    import torch
+    B, H, W, _ = u.shape
+    _fcheck(lib().phx_fno_to_state(_cdev(u, torch.float32, 3 * B * H * W, "u"), B, H, W,
+                                   float(scale_psi), float(scale_n),
+                                   _cdev(psi, torch.complex64, B * H * W, "psi"),
+                                   None if n is None else _cdev(n, torch.float32, B * H * W, "n"),
+                                   _stream_ptr(stream)), None)
+    return psi, n
