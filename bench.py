@@ -83,6 +83,13 @@ def max_over_ranks(pg, x):
     return float(t.item())
 
 
+def aggregate(pg, world, units_per_rank, ms_local):
+    """Whole-job throughput of `world` weak-scaled replicas: every rank did
+    `units_per_rank` units; the job took the slowest rank's time."""
+    ms = max_over_ranks(pg, ms_local)
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 def workload(name, seed_offset=0):
     import synth
     if name == "reservoir_1024":
@@ -102,12 +109,16 @@ def workload(name, seed_offset=0):
     return cfg, kind, desc
 
 
+STEP_KERNEL_SOURCES = ("phx_internal.h", "phx_noise.cuh", "rk4_generic.cuh", "rk4_tma.h",
+                       "rk4_tma.cu", "rk4_f32.cu", "rk4_f64.cu")
+
+
 def kernel_hash():
+    """Hash of the sources the fused step kernels are compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_18341_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -308,9 +319,7 @@ def main():
     clk = clocks.stop() if clocks else None
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     kern_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    ms = float(np.mean(step_ms))
-    ms = max_over_ranks(pg, ms)
-    value = world * sites * rk4_steps / (ms * 1e-3)
+    ms, value = aggregate(pg, world, sites * rk4_steps, float(np.mean(step_ms)))
 
     # end to end through the C ABI with pinned host buffers
     psi_h = torch.tensor(np.ascontiguousarray(cfg["psi0"]), dtype=cplx).pin_memory()
