@@ -21,7 +21,7 @@ def half_limit(**kw):
 
 def main():
     out = {"note": "written by synth/derive_constants.py from oracle.gp; "
-                   "dt = 0.5 * 2 sqrt(2) hbar / lambda_max"}
+                   "dt = 0.5 * 2 sqrt(2) hbar / lambda_max (0.85 for steady_256)"}
     res = dict(reservoir=True, g=6e-3, g_r=1.2e-2, R=0.01, gamma_c=0.15,
                gamma_r=0.225, kappa=KAPPA)
     out["pump_threshold"] = gp.pump_threshold(gp.Params(nx=1, ny=1, lx=1, ly=1, **res))
@@ -33,8 +33,13 @@ def main():
     for n, L in ((2048, 200.0), (512, 50.0), (64, 6.25), (96, 9.375)):
         out["spinor_%d_L%g" % (n, L)] = {"dt": half_limit(
             nx=n, ny=n, lx=L, ly=L, spinor=True, delta_lt=0.025, **res)}
-    out["steady_256_L128"] = {"dt": half_limit(nx=256, ny=256, lx=128.0,
-                                               ly=128.0, **res)}
+    # Steady-state workload: dt at 0.85 of the limit.  RK4 damps the band
+    # |lambda| dt ~ 1 (|R(i y)|^2 = 1 - y^6/72 + y^8/576); at 0.85 that damping
+    # exceeds the reservoir gain for the zero-group-velocity lattice modes at
+    # the (pi/dx, 0) saddles of the 5-point dispersion, which at 0.5 out-grow
+    # the k ~ 0 condensate.  The stationary state does not depend on dt.
+    dmax = 2 * half_limit(nx=256, ny=256, lx=128.0, ly=128.0, **res)
+    out["steady_256_L128"] = {"dt": 0.85 * dmax, "dt_max": dmax}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
                         "constants.json")
     with open(path, "w") as f:
