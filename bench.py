@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phx", choices=["phx", "reference"])
     ap.add_argument("--workload", default="reservoir_1024",
-                    choices=["reservoir_1024", "spinor_2048", "conservative_64"])
+                    choices=["reservoir_1024", "reservoir", "spinor_2048", "conservative_64",
+                             "ensemble"])
+    ap.add_argument("--grid", type=int, default=1024,
+                    help="grid size of the 'reservoir' workload (100 um box, config-2 physics)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--rk4-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,13 +93,24 @@ def aggregate(pg, world, units_per_rank, ms_local):
     return ms, world * units_per_rank / (ms * 1e-3)
 
 
-def workload(name, seed_offset=0):
+def workload_name(args):
+    if args.workload == "reservoir":
+        return "reservoir_%d" % args.grid
+    return args.workload
+
+
+def workload(name, seed_offset=0, grid=1024):
     import synth
-    if name == "reservoir_1024":
+    if name == "reservoir_1024" or (name == "reservoir" and grid == 1024):
         cfg = synth.reservoir_1024(seed=2 + seed_offset)
         kind = "reservoir"
         desc = ("driven-dissipative GP + reservoir, 1024x1024, 100 um periodic, ring "
                 "pump r=20 um w=3 um at 1.5 P_thr, psi0 noise 1e-2, dt = half RK4 limit")
+    elif name == "reservoir":
+        cfg = synth.reservoir_grid(grid, seed=2 + seed_offset)
+        kind = "reservoir"
+        desc = ("driven-dissipative GP + reservoir, %dx%d, 100 um periodic, ring pump r=20 um "
+                "w=3 um at 1.5 P_thr, psi0 noise 1e-2, dt = half RK4 limit" % (grid, grid))
     elif name == "spinor_2048":
         cfg = synth.spinor_grid(2048, seed=3 + seed_offset, const_key="spinor_2048_L200")
         kind = "spinor"
@@ -217,7 +231,11 @@ def peaks():
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    cfg, kind, desc = workload(args.workload)
+    if args.workload == "ensemble":
+        cfg, kind, desc = workload("reservoir", grid=128)
+        desc = "one 128x128 member of the ensemble workload"
+    else:
+        cfg, kind, desc = workload(args.workload, grid=args.grid)
     from oracle import gp
     p = gp.Params(**cfg["params"])
     psi, n = np.array(cfg["psi0"], complex), cfg["n0"]
@@ -246,6 +264,118 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args, world, rank, local, pg):
+    """Ensemble workload: 256 independent reservoir instances on uneven grids
+    (64 each at 128^2, 256^2, 512^2, 1024^2; pumps U[0.8, 3] P_thr, distinct
+    seeds) advanced together, one persistent launch per RK4 step, replayed
+    from a CUDA graph; per-member FP64 norm/energy and residual."""
+    import torch
+    import synth
+    import paper_2411_18341_gb300 as phx
+    from paper_2411_18341_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    members = synth.ensemble(seed0=1000 + 10000 * rank)
+    rk4_steps = args.rk4_steps or 500
+    stream = torch.cuda.Stream(device=dev)
+    b = phx.phx_batch_create([phx.params_from_dict(m["params"], precision=32,
+                                                   stream=stream.cuda_stream) for m in members])
+    psi_d, n_d = [], []
+    for i, m in enumerate(members):
+        phx.phx_batch_set_pump(b, i, torch.tensor(m["P"][0], dtype=torch.float32, device=dev))
+        psi_d.append(torch.tensor(m["psi0"][0], dtype=torch.complex64, device=dev))
+        n_d.append(torch.tensor(m["n0"][0], dtype=torch.float32, device=dev))
+    sites = sum(m["params"]["nx"] * m["params"]["ny"] for m in members)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step(k0=None, k1=None):
+        for i in range(len(members)):
+            phx.phx_batch_set_state(b, i, psi_d[i], n_d[i])
+        if k0 is not None:
+            k0.record(stream)
+        phx.phx_batch_step_n(b, rk4_steps)
+        if k1 is not None:
+            k1.record(stream)
+        phx.phx_batch_norm_energy(b)
+        phx.phx_batch_residual(b)
+
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    launches0 = phx.phx_launch_count()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a, e, k0, k1 = ev[k]
+        a.record(stream)
+        one_step(k0, k1)
+        e.record(stream)
+    torch.cuda.synchronize()
+    launches = phx.phx_launch_count() - launches0
+    barrier(pg)
+    clk = clocks.stop() if clocks else None
+    ms, value = aggregate(pg, world, sites * rk4_steps,
+                          float(np.mean([x[0].elapsed_time(x[1]) for x in ev])))
+    kern_s = float(np.mean([x[2].elapsed_time(x[3]) for x in ev])) * 1e-3 / rk4_steps
+
+    # end to end: pinned host inputs in, every member's state out
+    psi_h = [t.cpu().pin_memory() for t in psi_d]
+    n_h = [t.cpu().pin_memory() for t in n_d]
+    P_h = [torch.tensor(m["P"][0], dtype=torch.float32).pin_memory() for m in members]
+    out_psi = [torch.empty_like(t).pin_memory() for t in psi_h]
+    out_n = [torch.empty_like(t).pin_memory() for t in n_h]
+    torch.cuda.synchronize()
+    barrier(pg)
+    t0 = time.perf_counter()
+    for i in range(len(members)):
+        phx.phx_batch_set_pump(b, i, P_h[i])
+        phx.phx_batch_set_state(b, i, psi_h[i], n_h[i])
+    phx.phx_batch_step_n(b, rk4_steps)
+    phx.phx_batch_norm_energy(b)
+    phx.phx_batch_residual(b)
+    for i in range(len(members)):
+        phx.phx_batch_get_state(b, i, out_psi[i], out_n[i])
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    pk, pk_kind = peaks()
+    achieved = 28 * sites / kern_s / 1e9
+    line = {
+        "metric": "RK4 site-updates/s", "value": value, "unit": "site-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "ensemble",
+                   "description": "256 reservoir instances, 64 each at 128^2/256^2/512^2/1024^2, "
+                                  "100 um, ring pumps U[0.8,3] P_thr, distinct seeds",
+                   "sites": sites, "rk4_steps_per_step": rk4_steps, "tile": phx.phx_batch_tile(b),
+                   "per_step": "set_state x256 + %d batched RK4 steps + per-member FP64 "
+                               "norm/energy + residual" % rk4_steps,
+                   "l2": "inputs (%.1f GB) larger than L2" % (28 * sites / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": world * sites * rk4_steps / e2e_s, "unit": "site-updates/s",
+                "h2d_bytes_per_step": sites * 16, "d2h_bytes_per_step": sites * 12},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": recorded_traffic("ensemble", 32),
+                     "kernel": "rk4_f32_tma (persistent, all members per launch)",
+                     "algorithmic_bytes_per_site": 28, "avg_launch_us": kern_s * 1e6,
+                     "peak_source": pk_kind},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cfg, _, _ = workload("reservoir", grid=128)
+        line["cpu_baseline"] = cpu_baseline("ensemble (one 128x128 member)", cfg)
+    phx.phx_batch_destroy(b)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_setup(args)
@@ -262,7 +392,13 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    cfg, kind, desc = workload(args.workload, seed_offset=rank)
+    if args.workload == "ensemble":
+        run_ensemble(args, world, rank, local, pg)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    wname = workload_name(args)
+    cfg, kind, desc = workload(args.workload, seed_offset=rank, grid=args.grid)
     rk4_steps = args.rk4_steps or (RK4_STEPS if args.workload != "conservative_64" else 1000)
     if args.workload == "spinor_2048" and args.rk4_steps is None:
         rk4_steps = 2000
@@ -350,14 +486,14 @@ def main():
     bps = BYTES_PER_SITE[(prec, kind)]
     kern_s = float(np.mean(kern_ms)) * 1e-3 / rk4_steps
     achieved = bps * sites / kern_s / 1e9
-    traffic = recorded_traffic(args.workload, prec)
+    traffic = recorded_traffic(wname, prec)
     line = {
         "metric": "RK4 site-updates/s",
         "value": value, "unit": "site-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc,
+        "config": {"workload": wname, "description": desc,
                    "grid": "%dx%d" % (nx, ny), "rk4_steps_per_step": rk4_steps,
                    "per_step": "set_state + %d fused RK4 steps + FP64 norm/energy + "
                                "FP64 residual" % rk4_steps,
@@ -379,7 +515,7 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, cfg)
+        line["cpu_baseline"] = cpu_baseline(wname, cfg)
     phx.phx_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
