@@ -151,8 +151,11 @@ TileArgs batch_args(const phx_batch* b, int cur, int parity) {
 
 cudaError_t launch_step(const phx_batch* b, int cur, int parity, cudaStream_t s) {
   const int grid = b->ntiles < b->num_sms ? b->ntiles : b->num_sms;
-  return launch_rk4_tma_f32(b->tile_cfg, b->reservoir, b->tables_V, batch_args(b, cur, parity),
-                            s, grid);
+  bool per = true;
+  for (const phx_params& q : b->p)
+    per = per && q.bc_x == PHX_BC_PERIODIC && q.bc_y == PHX_BC_PERIODIC;
+  return launch_rk4_tma_f32(b->tile_cfg, b->reservoir, b->tables_V, per,
+                            batch_args(b, cur, parity), s, grid);
 }
 
 // Time each tile configuration on the batch's own state (a step reads buffer

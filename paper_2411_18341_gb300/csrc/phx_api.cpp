@@ -59,6 +59,10 @@ namespace {
 
 thread_local std::string g_err = "no error";
 
+bool periodic(const phx_params& p) {
+  return p.bc_x == PHX_BC_PERIODIC && p.bc_y == PHX_BC_PERIODIC;
+}
+
 phx_status fail(phx_handle* h, phx_status s, const std::string& msg) {
   if (h)
     h->err = msg;
@@ -180,7 +184,8 @@ phx_status autotune(phx_handle* h) {
     const TileArgs ta = tile_args(h, 0);
     const int grid = ta.ntiles < h->num_sms ? ta.ntiles : h->num_sms;
     auto launch = [&]() {
-      return launch_rk4_tma_f32(cfg, h->m.reservoir, h->has_V, ta, h->stream, grid);
+      return launch_rk4_tma_f32(cfg, h->m.reservoir, h->has_V, periodic(h->p), ta, h->stream,
+                                grid);
     };
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch();
@@ -474,7 +479,8 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
         }
         const TileArgs ta = tile_args(h, inj);
         const int grid = ta.ntiles < h->num_sms ? ta.ntiles : h->num_sms;
-        e = launch_rk4_tma_f32(h->tile_cfg, h->m.reservoir, h->has_V, ta, h->stream, grid);
+        e = launch_rk4_tma_f32(h->tile_cfg, h->m.reservoir, h->has_V, periodic(h->p), ta,
+                               h->stream, grid);
       } else {
         e = launch_rk4_step_f32(h->m, a, h->stream, h->p.tile);
       }

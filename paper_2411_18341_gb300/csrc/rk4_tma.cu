@@ -116,7 +116,9 @@ struct Cfg {
   static constexpr int SMEM = NBUF * BUF_BYTES + PSI_BYTES + 128;
 };
 
-template <bool RES, bool POT, int MR, int WY>
+// PER: both axes periodic (every ring cell holds a periodic image, so no
+// stage value needs forcing to zero).
+template <bool RES, bool POT, bool PER, int MR, int WY>
 __global__ void __launch_bounds__(32 * WY, 1)
 rk4_f32_tma(const TileArgs ta) {
   using C = Cfg<RES, POT, MR, WY>;
@@ -252,8 +254,8 @@ rk4_f32_tma(const TileArgs ta) {
         acc[j][i] = f2(0.f, 0.f);
         na[j][i] = 0.f;
         const int gx = gx0 + i, gy = gy0 + j;
-        ins[j][i] = (g.bc_x == BC_PERIODIC || (gx >= 0 && gx < g.nx)) &&
-                    (g.bc_y == BC_PERIODIC || (gy >= 0 && gy < g.ny));
+        ins[j][i] = PER || ((g.bc_x == BC_PERIODIC || (gx >= 0 && gx < g.nx)) &&
+                            (g.bc_y == BC_PERIODIC || (gy >= 0 && gy < g.ny)));
         const int fi = (r0 + j) * C::FW + foff + c0 + i;
         n0[j][i] = RES ? Nb[fi] : 0.f;
         nc[j][i] = n0[j][i];
@@ -262,7 +264,7 @@ rk4_f32_tma(const TileArgs ta) {
       }
     }
 
-#pragma unroll 1
+#pragma unroll
     for (int s = 0; s < 4; ++s) {
       const float2* src = (s & 1) ? Y : P0;
       float2* dst = (s & 1) ? P0 : Y;
@@ -309,7 +311,7 @@ rk4_f32_tma(const TileArgs ta) {
             na[j][i] = fmaf(w, Kn, na[j][i]);
           }
           ny[j][i] = __ffma2_rn(cs2, K, p0[j][i]);
-          if (!ins[j][i]) ny[j][i] = f2(0.f, 0.f);
+          if (!PER && !ins[j][i]) ny[j][i] = f2(0.f, 0.f);
           nn[j][i] = RES ? fmaf(cs, Kn, n0[j][i]) : 0.f;
         }
       }
@@ -385,10 +387,10 @@ rk4_f32_tma(const TileArgs ta) {
   }
 }
 
-template <bool RES, bool POT, int MR, int WY>
+template <bool RES, bool POT, bool PER, int MR, int WY>
 cudaError_t launch_cfg(const TileArgs& ta, cudaStream_t s, int grid) {
   using C = Cfg<RES, POT, MR, WY>;
-  auto kern = rk4_f32_tma<RES, POT, MR, WY>;
+  auto kern = rk4_f32_tma<RES, POT, PER, MR, WY>;
   static int configured_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -434,14 +436,20 @@ TmaBox tma_box(int tile_cfg) {
   return b;
 }
 
-cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, const TileArgs& ta,
-                               cudaStream_t s, int grid) {
-#define PHX_TMA_CASE(CFG, MR, WY)                                            \
-  if (tile_cfg == CFG) {                                                     \
-    if (res && pot) return launch_cfg<true, true, MR, WY>(ta, s, grid);      \
-    if (res) return launch_cfg<true, false, MR, WY>(ta, s, grid);            \
-    if (pot) return launch_cfg<false, true, MR, WY>(ta, s, grid);            \
-    return launch_cfg<false, false, MR, WY>(ta, s, grid);                    \
+cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per,
+                               const TileArgs& ta, cudaStream_t s, int grid) {
+#define PHX_TMA_CASE(CFG, MR, WY)                                                      \
+  if (tile_cfg == CFG) {                                                               \
+    if (per) {                                                                         \
+      if (res && pot) return launch_cfg<true, true, true, MR, WY>(ta, s, grid);        \
+      if (res) return launch_cfg<true, false, true, MR, WY>(ta, s, grid);              \
+      if (pot) return launch_cfg<false, true, true, MR, WY>(ta, s, grid);              \
+      return launch_cfg<false, false, true, MR, WY>(ta, s, grid);                      \
+    }                                                                                  \
+    if (res && pot) return launch_cfg<true, true, false, MR, WY>(ta, s, grid);         \
+    if (res) return launch_cfg<true, false, false, MR, WY>(ta, s, grid);               \
+    if (pot) return launch_cfg<false, true, false, MR, WY>(ta, s, grid);               \
+    return launch_cfg<false, false, false, MR, WY>(ta, s, grid);                       \
   }
   PHX_TMA_CASE(TILE_64x64, 4, 16)
   PHX_TMA_CASE(TILE_64x48, 4, 12)

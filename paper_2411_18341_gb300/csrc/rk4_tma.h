@@ -66,7 +66,9 @@ bool encode_map_f32(CUtensorMap* map, void* base, unsigned long long w,
 bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* const psi[2],
                     void* const n[2], void* P, void* V, int tile_cfg);
 
-cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, const TileArgs& ta,
+// per: every instance is periodic in both axes (selects the variant that
+// never forces stage values to zero).
+cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per, const TileArgs& ta,
                                cudaStream_t s, int grid);
 
 }  // namespace phx

@@ -192,10 +192,10 @@ def test_feature_target_state_maps():
     oracle's inputs (synth.fno_features / fno_targets / fno_state_from_output)."""
     m = phx()
     pthr = synth.load_constants()["pump_threshold"]
-    P = synth.random_gaussian_pumps(64, 50.0, 3, seed=900).astype(np.float32)
+    P = synth.random_gaussian_pumps(64, 128.0, 3, seed=900).astype(np.float32)
     feat = torch.empty(3, 64, 64, 3, device="cuda")
-    m.phx_fno_features(torch.from_numpy(P).cuda(), 50.0, 50.0, pthr, feat)
-    ref = synth.fno_features(P.astype(np.float64), 50.0, pthr)
+    m.phx_fno_features(torch.from_numpy(P).cuda(), 128.0, 128.0, pthr, feat)
+    ref = synth.fno_features(P.astype(np.float64), 128.0, pthr)
     torch.cuda.synchronize()
     assert np.max(np.abs(feat.cpu().numpy() - ref)) < 1e-6 * max(1.0, np.abs(ref).max())
     rng = np.random.default_rng(901)
