@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--rk4-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="step-kernel configuration (0 = autotune, 1..6 TMA-fed, 9 generic)")
     return ap.parse_args()
 
 
@@ -410,7 +412,8 @@ def main():
     nc = 2 if d["spinor"] else 1
     sites = nx * ny
     stream = torch.cuda.Stream(device=dev)
-    h = phx.phx_create(phx.params_from_dict(d, precision=prec, stream=stream.cuda_stream))
+    h = phx.phx_create(phx.params_from_dict(d, precision=prec, stream=stream.cuda_stream,
+                                            tile=args.tile))
 
     # resident inputs on the device
     psi0_d = torch.tensor(np.ascontiguousarray(cfg["psi0"]), dtype=cplx, device=dev)
@@ -501,6 +504,7 @@ def main():
                          "stays L2-resident within a step" % (
                              (2 * sites * nc * 2 * esz + (2 * sites * nc * esz if n_h is not None else 0)
                               + (sites * esz if P_h is not None else 0)) / 2 ** 20),
+                   "tile": phx.phx_tile(h),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": world * sites * rk4_steps / e2e_s, "unit": "site-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -73,7 +73,7 @@ typedef struct phx_params {
                                 0 = autotune (the first phx_step_n times each
                                 configuration on the handle's own state, without
                                 changing it, synchronising the stream once; the
-                                choice is cached per grid shape), 1..5 = a fixed
+                                choice is cached per grid shape), 1..6 = a fixed
                                 shared-memory region and thread shape of the
                                 TMA-fed persistent kernel, 9 = generic kernel */
   double hbar2_over_2m;      /* hbar^2/2m, meV um^2 */
@@ -158,6 +158,10 @@ phx_status phx_set_time(phx_handle* h, int64_t step, double t);
 
 /* Replace the stream used by later calls. */
 phx_status phx_set_stream(phx_handle* h, void* stream);
+
+/* Step-kernel configuration in use (see phx_params.tile; after autotuning,
+ * the configuration it chose; 9 = generic kernel), or 0 for NULL. */
+int32_t phx_tile(const phx_handle* h);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t phx_launch_count(void);

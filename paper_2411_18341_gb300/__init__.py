@@ -83,6 +83,7 @@ _SIGS = {
     "phx_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "phx_set_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
     "phx_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "phx_tile": (ctypes.c_int32, [ctypes.c_void_p]),
     "phx_launch_count": (ctypes.c_uint64, []),
     "phx_debug_inject": (ctypes.c_int, [ctypes.c_uint32]),
     "phx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -299,6 +300,10 @@ def phx_set_time(h, step, t):
 
 def phx_set_stream(h, stream):
     _check(lib().phx_set_stream(h.ptr, ctypes.c_void_p(int(stream) if stream else 0)), h.ptr)
+
+
+def phx_tile(h):
+    return int(lib().phx_tile(h.ptr))
 
 
 def phx_launch_count():

@@ -150,7 +150,8 @@ TileArgs batch_args(const phx_batch* b, int cur, int parity) {
 }
 
 cudaError_t launch_step(const phx_batch* b, int cur, int parity, cudaStream_t s) {
-  const int grid = b->ntiles < b->num_sms ? b->ntiles : b->num_sms;
+  const int slots = b->num_sms * tma_ctas_per_sm(b->tile_cfg);
+  const int grid = b->ntiles < slots ? b->ntiles : slots;
   bool per = true;
   for (const phx_params& q : b->p)
     per = per && q.bc_x == PHX_BC_PERIODIC && q.bc_y == PHX_BC_PERIODIC;
@@ -161,7 +162,8 @@ cudaError_t launch_step(const phx_batch* b, int cur, int parity, cudaStream_t s)
 // Time each tile configuration on the batch's own state (a step reads buffer
 // cur and writes cur ^ 1, so repeating it leaves the state intact).
 phx_status autotune(phx_batch* b) {
-  const int cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64, TILE_64x32};
+  const int cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64, TILE_64x32,
+                       TILE_64x32_M2_2};
   cudaEvent_t e0, e1;
   PHX_BCK(b, cudaEventCreate(&e0));
   PHX_BCK(b, cudaEventCreate(&e1));

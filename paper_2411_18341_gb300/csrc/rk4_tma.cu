@@ -96,7 +96,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-template <bool RES, bool POT, int MR, int WY>
+template <bool RES, bool POT, int MR, int WY, int MINB = 1>
 struct Cfg {
   static constexpr int RW = 64;            // region (ring-3) columns: one warp x 2 cols
   static constexpr int RH = MR * WY;       // region rows
@@ -112,16 +112,18 @@ struct Cfg {
   static constexpr int TX_BYTES = PH * PW * 8 + NF * RH * FW * 4;  // bytes one tile brings
   // Input buffers: one per tile in flight (three when shared memory allows,
   // so that a CTA with three tiles has all its loads in flight at once).
-  static constexpr int NBUF = (3 * BUF_BYTES + PSI_BYTES + 128 <= 227 * 1024) ? 3 : 2;
+  // (Two buffers when two CTAs share an SM.)
+  static constexpr int NBUF =
+      (MINB == 1 && 3 * BUF_BYTES + PSI_BYTES + 128 <= 227 * 1024) ? 3 : 2;
   static constexpr int SMEM = NBUF * BUF_BYTES + PSI_BYTES + 128;
 };
 
 // PER: both axes periodic (every ring cell holds a periodic image, so no
 // stage value needs forcing to zero).
-template <bool RES, bool POT, bool PER, int MR, int WY>
-__global__ void __launch_bounds__(32 * WY, 1)
+template <bool RES, bool POT, bool PER, int MR, int WY, int MINB>
+__global__ void __launch_bounds__(32 * WY, MINB)
 rk4_f32_tma(const TileArgs ta) {
-  using C = Cfg<RES, POT, MR, WY>;
+  using C = Cfg<RES, POT, MR, WY, MINB>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[3];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -387,10 +389,10 @@ rk4_f32_tma(const TileArgs ta) {
   }
 }
 
-template <bool RES, bool POT, bool PER, int MR, int WY>
+template <bool RES, bool POT, bool PER, int MR, int WY, int MINB>
 cudaError_t launch_cfg(const TileArgs& ta, cudaStream_t s, int grid) {
-  using C = Cfg<RES, POT, MR, WY>;
-  auto kern = rk4_f32_tma<RES, POT, PER, MR, WY>;
+  using C = Cfg<RES, POT, MR, WY, MINB>;
+  auto kern = rk4_f32_tma<RES, POT, PER, MR, WY, MINB>;
   static int configured_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -426,6 +428,7 @@ TmaBox tma_box(int tile_cfg) {
   if (tile_cfg == TILE_64x32) WY = 8;
   if (tile_cfg == TILE_64x48_M2) { MR = 2; WY = 24; }
   if (tile_cfg == TILE_64x64_M2) { MR = 2; WY = 32; }
+  if (tile_cfg == TILE_64x32_M2_2) { MR = 2; WY = 16; }
   const int RW = 64, RH = MR * WY;
   b.psi_w = 2 * (RW + 4);  // floats (interleaved complex)
   b.psi_h = RH + 2;
@@ -436,26 +439,29 @@ TmaBox tma_box(int tile_cfg) {
   return b;
 }
 
+int tma_ctas_per_sm(int tile_cfg) { return tile_cfg == TILE_64x32_M2_2 ? 2 : 1; }
+
 cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per,
                                const TileArgs& ta, cudaStream_t s, int grid) {
-#define PHX_TMA_CASE(CFG, MR, WY)                                                      \
+#define PHX_TMA_CASE(CFG, MR, WY, MB)                                                  \
   if (tile_cfg == CFG) {                                                               \
     if (per) {                                                                         \
-      if (res && pot) return launch_cfg<true, true, true, MR, WY>(ta, s, grid);        \
-      if (res) return launch_cfg<true, false, true, MR, WY>(ta, s, grid);              \
-      if (pot) return launch_cfg<false, true, true, MR, WY>(ta, s, grid);              \
-      return launch_cfg<false, false, true, MR, WY>(ta, s, grid);                      \
+      if (res && pot) return launch_cfg<true, true, true, MR, WY, MB>(ta, s, grid);    \
+      if (res) return launch_cfg<true, false, true, MR, WY, MB>(ta, s, grid);          \
+      if (pot) return launch_cfg<false, true, true, MR, WY, MB>(ta, s, grid);          \
+      return launch_cfg<false, false, true, MR, WY, MB>(ta, s, grid);                  \
     }                                                                                  \
-    if (res && pot) return launch_cfg<true, true, false, MR, WY>(ta, s, grid);         \
-    if (res) return launch_cfg<true, false, false, MR, WY>(ta, s, grid);               \
-    if (pot) return launch_cfg<false, true, false, MR, WY>(ta, s, grid);               \
-    return launch_cfg<false, false, false, MR, WY>(ta, s, grid);                       \
+    if (res && pot) return launch_cfg<true, true, false, MR, WY, MB>(ta, s, grid);     \
+    if (res) return launch_cfg<true, false, false, MR, WY, MB>(ta, s, grid);           \
+    if (pot) return launch_cfg<false, true, false, MR, WY, MB>(ta, s, grid);           \
+    return launch_cfg<false, false, false, MR, WY, MB>(ta, s, grid);                   \
   }
-  PHX_TMA_CASE(TILE_64x64, 4, 16)
-  PHX_TMA_CASE(TILE_64x48, 4, 12)
-  PHX_TMA_CASE(TILE_64x32, 4, 8)
-  PHX_TMA_CASE(TILE_64x48_M2, 2, 24)
-  PHX_TMA_CASE(TILE_64x64_M2, 2, 32)
+  PHX_TMA_CASE(TILE_64x64, 4, 16, 1)
+  PHX_TMA_CASE(TILE_64x48, 4, 12, 1)
+  PHX_TMA_CASE(TILE_64x32, 4, 8, 1)
+  PHX_TMA_CASE(TILE_64x48_M2, 2, 24, 1)
+  PHX_TMA_CASE(TILE_64x64_M2, 2, 32, 1)
+  PHX_TMA_CASE(TILE_64x32_M2_2, 2, 16, 2)
 #undef PHX_TMA_CASE
   return cudaErrorInvalidValue;
 }

@@ -16,6 +16,7 @@ enum {
   TILE_64x32 = 3,     // 4 x 2, 8 warps
   TILE_64x48_M2 = 4,  // 2 x 2, 24 warps
   TILE_64x64_M2 = 5,  // 2 x 2, 32 warps
+  TILE_64x32_M2_2 = 6,  // 2 x 2, 16 warps, two CTAs per SM
   TILE_GENERIC = 9
 };
 
@@ -55,6 +56,10 @@ struct TmaBox {
 };
 
 TmaBox tma_box(int tile_cfg);
+
+// Resident CTAs per SM the configuration is built for (the persistent grid
+// is this many CTAs per SM).
+int tma_ctas_per_sm(int tile_cfg);
 
 bool encode_map_f32(CUtensorMap* map, void* base, unsigned long long w,
                     unsigned long long h, unsigned long long planes,

@@ -276,7 +276,7 @@ def test_device_pointers_and_torch_stream():
     assert rel_l2(outn.cpu().numpy(), o_n) <= 1e-4
 
 
-TILES = [0, 1, 2, 3, 9]  # auto, 64x64, 64x48, 64x32 (TMA-fed persistent), generic
+TILES = [0, 1, 2, 3, 4, 5, 6, 9]  # auto, TMA-fed persistent configurations 1..6, generic
 
 
 @pytest.mark.parametrize("tile", TILES)
