@@ -31,7 +31,7 @@ struct phx_batch {
   std::vector<void*> V_owned;    // potentials are allocated on demand
   TileInst* d_inst = nullptr;
   std::vector<TileInst> h_inst;
-  int* d_tile_inst = nullptr;
+  int2* d_tile_info = nullptr;   // per tile: (member, kx | ky << 16)
   int ntiles = 0;
   DevClock* clock = nullptr;
   double* t_inst = nullptr;      // [2][count]
@@ -81,7 +81,7 @@ void bfree(phx_batch* b) {
     if (v) cudaFree(v);
   if (b->pool) cudaFree(b->pool);
   if (b->d_inst) cudaFree(b->d_inst);
-  if (b->d_tile_inst) cudaFree(b->d_tile_inst);
+  if (b->d_tile_info) cudaFree(b->d_tile_info);
   if (b->clock) cudaFree(b->clock);
   if (b->t_inst) cudaFree(b->t_inst);
   if (b->partials) cudaFree(b->partials);
@@ -99,7 +99,7 @@ bool all_V(const phx_batch* b) {
 
 // Instance descriptors and the global tile list for configuration cfg.
 phx_status build_tables(phx_batch* b, int cfg) {
-  std::vector<int> tile_inst;
+  std::vector<int2> tile_info;
   int tile0 = 0;
   for (int i = 0; i < b->count; ++i) {
     void* psi[2] = {b->psi[0][i], b->psi[1][i]};
@@ -108,19 +108,21 @@ phx_status build_tables(phx_batch* b, int cfg) {
                         b->has_V[i] ? b->V[i] : nullptr, cfg))
       return bfail(b, PHX_ECUDA, "cuTensorMapEncodeTiled failed");
     b->h_inst[i].tile0 = tile0;
-    const int nt = b->h_inst[i].tiles_x * b->h_inst[i].tiles_y;
-    tile_inst.insert(tile_inst.end(), nt, i);
-    tile0 += nt;
+    const int tx = b->h_inst[i].tiles_x, ty = b->h_inst[i].tiles_y;
+    if (tx > 0xffff || ty > 0x7fff) return bfail(b, PHX_EINVAL, "member grid too large");
+    for (int ky = 0; ky < ty; ++ky)
+      for (int kx = 0; kx < tx; ++kx) tile_info.push_back(make_int2(i, kx | (ky << 16)));
+    tile0 += tx * ty;
   }
-  if (b->d_tile_inst && b->ntiles < tile0) {
-    cudaFree(b->d_tile_inst);
-    b->d_tile_inst = nullptr;
+  if (b->d_tile_info && b->ntiles < tile0) {
+    cudaFree(b->d_tile_info);
+    b->d_tile_info = nullptr;
   }
-  if (!b->d_tile_inst) PHX_BCK(b, cudaMalloc(&b->d_tile_inst, sizeof(int) * tile0));
+  if (!b->d_tile_info) PHX_BCK(b, cudaMalloc(&b->d_tile_info, sizeof(int2) * tile0));
   b->ntiles = tile0;
   // synchronous copies: the host vectors are temporaries
   PHX_BCK(b, cudaStreamSynchronize(b->stream));
-  PHX_BCK(b, cudaMemcpy(b->d_tile_inst, tile_inst.data(), sizeof(int) * tile0,
+  PHX_BCK(b, cudaMemcpy(b->d_tile_info, tile_info.data(), sizeof(int2) * tile0,
                         cudaMemcpyHostToDevice));
   PHX_BCK(b, cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(TileInst) * b->count,
                         cudaMemcpyHostToDevice));
@@ -137,7 +139,8 @@ phx_status build_tables(phx_batch* b, int cfg) {
 TileArgs batch_args(const phx_batch* b, int cur, int parity) {
   TileArgs ta;
   ta.inst = b->d_inst;
-  ta.tile_inst = b->d_tile_inst;
+  ta.tile_info = b->d_tile_info;
+  ta.one = scalars_of(b->h_inst[0]);
   ta.ntiles = b->ntiles;
   ta.ninst = b->count;
   ta.cur = cur;

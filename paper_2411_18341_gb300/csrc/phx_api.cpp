@@ -232,7 +232,8 @@ bool encode_maps(phx_handle* h) {
 TileArgs tile_args(phx_handle* h, int inj) {
   TileArgs ta;
   ta.inst = h->d_inst;
-  ta.tile_inst = nullptr;
+  ta.tile_info = nullptr;
+  ta.one = scalars_of(h->h_inst);
   ta.ntiles = h->h_inst.tiles_x * h->h_inst.tiles_y;
   ta.ninst = 1;
   ta.cur = h->cur;

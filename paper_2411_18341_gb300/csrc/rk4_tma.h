@@ -37,9 +37,34 @@ struct alignas(128) TileInst {
   int tile0;            // index of its first tile in the global tile list
 };
 
+// The scalar part of one instance, passed by value in the kernel parameters
+// when a launch covers a single instance.
+struct InstScalars {
+  Geometry geo;
+  CoeffsT<float> k;
+  NoiseKey noise;
+  float2* psi_buf[2];
+  float* n_buf[2];
+  int tiles_x;
+};
+
+inline InstScalars scalars_of(const TileInst& I) {
+  InstScalars s;
+  s.geo = I.geo;
+  s.k = I.k;
+  s.noise = I.noise;
+  s.psi_buf[0] = I.psi_buf[0];
+  s.psi_buf[1] = I.psi_buf[1];
+  s.n_buf[0] = I.n_buf[0];
+  s.n_buf[1] = I.n_buf[1];
+  s.tiles_x = I.tiles_x;
+  return s;
+}
+
 struct TileArgs {
-  const TileInst* inst;  // device array of ninst instances
-  const int* tile_inst;  // instance of each global tile (nullptr: instance 0)
+  const TileInst* inst;   // device array of ninst instances
+  const int2* tile_info;  // per global tile: (instance, kx | ky << 16); unused if ninst == 1
+  InstScalars one;        // scalars of instance 0 (read when ninst == 1)
   int ntiles, ninst;
   int cur;               // input buffer of this step
   DevClock* clock;       // step counter and FP64 time of instance 0
@@ -75,5 +100,19 @@ bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* c
 // never forces stage values to zero).
 cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per, const TileArgs& ta,
                                cudaStream_t s, int grid);
+
+// One per tile configuration (rk4_tma_cfgN.cu): every model variant of it.
+cudaError_t launch_tma_cfg1(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid);
+cudaError_t launch_tma_cfg2(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid);
+cudaError_t launch_tma_cfg3(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid);
+cudaError_t launch_tma_cfg4(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid);
+cudaError_t launch_tma_cfg5(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid);
+cudaError_t launch_tma_cfg6(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid);
 
 }  // namespace phx

@@ -1,0 +1,12 @@
+// Instantiations of the persistent TMA-fed step kernel for tile
+// configuration 2 (4-row x 2-column micro-tiles, 12 warps, 1 CTA per SM).
+#include "rk4_tma_kernel.cuh"
+
+namespace phx {
+
+cudaError_t launch_tma_cfg2(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid) {
+  return tma::launch_variants<4, 12, 1>(res, pot, per, one, ta, s, grid);
+}
+
+}  // namespace phx

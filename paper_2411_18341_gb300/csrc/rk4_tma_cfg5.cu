@@ -1,0 +1,12 @@
+// Instantiations of the persistent TMA-fed step kernel for tile
+// configuration 5 (2-row x 2-column micro-tiles, 32 warps, 1 CTA per SM).
+#include "rk4_tma_kernel.cuh"
+
+namespace phx {
+
+cudaError_t launch_tma_cfg5(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid) {
+  return tma::launch_variants<2, 32, 1>(res, pot, per, one, ta, s, grid);
+}
+
+}  // namespace phx
