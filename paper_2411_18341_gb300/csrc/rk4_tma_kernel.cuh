@@ -127,8 +127,9 @@ rk4_f32_tma(const TileArgs ta) {
   using C = Cfg<RES, POT, MR, WY, MINB>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[3];
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  // 128-byte aligned start, by pointer arithmetic on the shared array so that
+  // the compiler keeps every derived access in the shared state space
+  unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   float2* Y = reinterpret_cast<float2*>(base + C::NBUF * C::BUF_BYTES);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -259,7 +260,6 @@ rk4_f32_tma(const TileArgs ta) {
     const NoiseKey nz = ONE ? ta.one.noise : I->noise;
     advance(cc, t + (int)gridDim.x);
     const float2 ax2 = f2(q.ax, q.ax), ay2 = f2(q.ay, q.ay);
-    const float2 a02 = f2(q.a0, q.a0);
     const float cg = q.g, cgr = q.gr, cih = q.inv_hbar;
     const float hR = q.half_R, hgc = q.half_gc, cR = q.R_;
     const float cgam = q.gamma_r, dt = q.dt;
@@ -294,7 +294,8 @@ rk4_f32_tma(const TileArgs ta) {
         n0[j][i] = RES ? Nb[fi] : 0.f;
         nc[j][i] = n0[j][i];
         Pv[j][i] = RES ? Pb[fi] : 0.f;
-        Vv[j][i] = POT ? Vb[fi] * cih : 0.f;
+        // the stencil's diagonal a0 rides with the local potential
+        Vv[j][i] = POT ? fmaf(Vb[fi], cih, q.a0) : q.a0;
       }
     }
 
@@ -308,11 +309,22 @@ rk4_f32_tma(const TileArgs ta) {
       // neighbours of the micro-tile
       const float4 tv = *reinterpret_cast<const float4*>(&src[(r0)*C::PW + c0 + 2]);
       const float4 bv = *reinterpret_cast<const float4*>(&src[(r0 + MR + 1) * C::PW + c0 + 2]);
+      // West / east neighbours: from the loaded box in the first stage (the
+      // ring columns -1 and 64 must be right there), from the neighbouring
+      // lanes' registers afterwards (lanes 0 and 31 then see their own
+      // values: finite, and only in the ring region that no output needs).
       float2 Wv[MR], Ev[MR];
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
-        Wv[j] = src[(r0 + j + 1) * C::PW + c0 + 1];
-        Ev[j] = src[(r0 + j + 1) * C::PW + c0 + 4];
+        if (s == 0) {
+          Wv[j] = src[(r0 + j + 1) * C::PW + c0 + 1];
+          Ev[j] = src[(r0 + j + 1) * C::PW + c0 + 4];
+        } else {
+          Wv[j].x = __shfl_up_sync(0xffffffffu, yc[j][1].x, 1);
+          Wv[j].y = __shfl_up_sync(0xffffffffu, yc[j][1].y, 1);
+          Ev[j].x = __shfl_down_sync(0xffffffffu, yc[j][0].x, 1);
+          Ev[j].y = __shfl_down_sync(0xffffffffu, yc[j][0].y, 1);
+        }
       }
       float2 ny[MR][2];
       float nn[MR][2];
@@ -325,10 +337,10 @@ rk4_f32_tma(const TileArgs ta) {
           const float2 E = i ? Ev[j] : yc[j][1];
           const float2 S = j ? yc[j - 1][i] : (i ? f2(tv.z, tv.w) : f2(tv.x, tv.y));
           const float2 N = (j < MR - 1) ? yc[j + 1][i] : (i ? f2(bv.z, bv.w) : f2(bv.x, bv.y));
-          // H/hbar of the stencil part: ax (E+W) + ay (N+S) + a0 C
+          // H/hbar: off-diagonal stencil ax (E+W) + ay (N+S), plus the local
+          // term (a0 + V/hbar + g|psi|^2 + g_r n) psi
           float2 lap = __fmul2_rn(ay2, __fadd2_rn(N, S));
           lap = __ffma2_rn(ax2, __fadd2_rn(E, W), lap);
-          lap = __ffma2_rn(a02, Cc, lap);
           const float dens = fmaf(Cc.x, Cc.x, Cc.y * Cc.y);
           const float ncur = nc[j][i];
           float loc = fmaf(cg, dens, Vv[j][i]);
@@ -338,11 +350,11 @@ rk4_f32_tma(const TileArgs ta) {
           float2 K;
           K.x = fmaf(G, Cc.x, H.y);
           K.y = fmaf(G, Cc.y, -H.x);
-          acc[j][i] = __ffma2_rn(w2, K, acc[j][i]);
+          acc[j][i] = s == 0 ? K : __ffma2_rn(w2, K, acc[j][i]);
           float Kn = 0.f;
           if (RES) {
             Kn = fmaf(-fmaf(cR, dens, cgam), ncur, Pv[j][i]);
-            na[j][i] = fmaf(w, Kn, na[j][i]);
+            na[j][i] = s == 0 ? Kn : fmaf(w, Kn, na[j][i]);
           }
           ny[j][i] = __ffma2_rn(cs2, K, p0[j][i]);
           if (!PER && !ins[j][i]) ny[j][i] = f2(0.f, 0.f);
@@ -356,8 +368,10 @@ rk4_f32_tma(const TileArgs ta) {
           yc[j][1] = ny[j][1];
           nc[j][0] = nn[j][0];
           nc[j][1] = nn[j][1];
-          *reinterpret_cast<float4*>(&dst[(r0 + j + 1) * C::PW + c0 + 2]) =
-              make_float4(ny[j][0].x, ny[j][0].y, ny[j][1].x, ny[j][1].y);
+          // only the micro-tile's first and last rows are read by other warps
+          if (j == 0 || j == MR - 1)
+            *reinterpret_cast<float4*>(&dst[(r0 + j + 1) * C::PW + c0 + 2]) =
+                make_float4(ny[j][0].x, ny[j][0].y, ny[j][1].x, ny[j][1].y);
         }
       }
       __syncthreads();
