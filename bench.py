@@ -31,6 +31,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 RK4_STEPS = 10000
+# Algorithmic FP64 flops per site per RK4 step (FMA = 2): per stage the
+# complex 5-point stencil 14, |psi|^2 3, local potential 4 (2 without the
+# reservoir), H 4, gain G 2, K 4, Kn 4, accumulators 6, stage values 6; four
+# stages plus the final combination.
+FLOPS_PER_SITE = {"reservoir": 194, "conservative": 144}
+# FP64 pipe of GB300: 2 DFMA per SM per cycle (152 SMs, 2.07 GHz max clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 BYTES_PER_SITE = {  # algorithmic bytes per site per RK4 step (read + write once)
     (32, "reservoir"): 28, (64, "reservoir"): 56,
     (32, "conservative"): 16, (64, "conservative"): 32,
@@ -126,7 +133,9 @@ def workload(name, seed_offset=0, grid=1024):
 
 
 STEP_KERNEL_SOURCES = ("phx_internal.h", "phx_noise.cuh", "rk4_generic.cuh", "rk4_tma.h",
-                       "rk4_tma.cu", "rk4_f32.cu", "rk4_f64.cu")
+                       "rk4_tma_kernel.cuh", "rk4_tma.cu", "rk4_tma_cfg1.cu", "rk4_tma_cfg2.cu",
+                       "rk4_tma_cfg3.cu", "rk4_tma_cfg4.cu", "rk4_tma_cfg5.cu", "rk4_tma_cfg6.cu",
+                       "rk4_f32.cu", "rk4_f64.cu")
 
 
 def kernel_hash():
@@ -138,9 +147,10 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name, precision):
+def recorded_traffic(workload_name, precision, tile=None):
     """DRAM bytes per launch of the fused step kernel from the committed ncu
-    summary, if it was captured from the current kernel sources."""
+    summary, if it was captured from the current kernel sources (and, when
+    given, with the tile configuration in use)."""
     path = os.path.join(ROOT, "profiles", "rk4_step_traffic.json")
     try:
         rec = json.load(open(path))
@@ -149,6 +159,8 @@ def recorded_traffic(workload_name, precision):
     key = "%s_fp%d" % (workload_name, precision)
     e = rec.get(key)
     if not e or e.get("kernel_sources") != kernel_hash():
+        return None
+    if tile is not None and e.get("tile") not in (None, tile):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -489,7 +501,24 @@ def main():
     bps = BYTES_PER_SITE[(prec, kind)]
     kern_s = float(np.mean(kern_ms)) * 1e-3 / rk4_steps
     achieved = bps * sites / kern_s / 1e9
-    traffic = recorded_traffic(wname, prec)
+    traffic = recorded_traffic(wname, prec, phx.phx_tile(h))
+    if prec == 64 and kind in FLOPS_PER_SITE:
+        # the FP64 stencil is bound by the FP64 pipe, not by HBM
+        tf = FLOPS_PER_SITE[kind] * sites / kern_s / 1e12
+        roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "rk4_step_generic (FP64)", "algorithmic_flops_per_site": FLOPS_PER_SITE[kind],
+                "hbm_gbs_algorithmic": achieved, "avg_launch_us": kern_s * 1e6,
+                "peak_source": "derived: 152 SMs x 2 DFMA/cycle x 2 flop x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                "traffic": traffic,
+                "kernel": "rk4_f32_tma (fused, one launch per RK4 step)" if prec == 32 and kind != "spinor"
+                          else "rk4_step_generic (fused, one launch per RK4 step)",
+                "algorithmic_bytes_per_site": bps,
+                "avg_launch_us": kern_s * 1e6,
+                "peak_source": pk_kind}
     line = {
         "metric": "RK4 site-updates/s",
         "value": value, "unit": "site-updates/s", "n_gpus": world,
@@ -509,13 +538,7 @@ def main():
         "e2e": {"value": world * sites * rk4_steps / e2e_s, "unit": "site-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     "traffic": traffic,
-                     "kernel": "rk4_step (fused, one launch per RK4 step)",
-                     "algorithmic_bytes_per_site": bps,
-                     "avg_launch_us": kern_s * 1e6,
-                     "peak_source": pk_kind},
+        "roofline": roof,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

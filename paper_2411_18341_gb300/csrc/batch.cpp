@@ -170,26 +170,35 @@ phx_status autotune(phx_batch* b) {
   cudaEvent_t e0, e1;
   PHX_BCK(b, cudaEventCreate(&e0));
   PHX_BCK(b, cudaEventCreate(&e1));
-  float best_ms = 1e30f;
-  int best = TILE_64x48_M2;
-  for (int cfg : cands) {
-    if (build_tables(b, cfg) != PHX_OK) continue;
-    cudaError_t e = launch_step(b, b->cur, b->parity, b->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = launch_step(b, b->cur, b->parity, b->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = cfg;
+  // three interleaved rounds; each configuration keeps its fastest round
+  const int nc = (int)(sizeof cands / sizeof cands[0]);
+  float cfg_ms[sizeof cands / sizeof cands[0]];
+  for (int c = 0; c < nc; ++c) cfg_ms[c] = 1e30f;
+  for (int round = 0; round < 3; ++round) {
+    for (int c = 0; c < nc; ++c) {
+      if (build_tables(b, cands[c]) != PHX_OK) continue;
+      cudaError_t e = launch_step(b, b->cur, b->parity, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        e = launch_step(b, b->cur, b->parity, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (ms < cfg_ms[c]) cfg_ms[c] = ms;
     }
   }
+  float best_ms = 1e30f;
+  int best = TILE_64x48_M2;
+  for (int c = 0; c < nc; ++c)
+    if (cfg_ms[c] < best_ms) {
+      best_ms = cfg_ms[c];
+      best = cands[c];
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return build_tables(b, best);

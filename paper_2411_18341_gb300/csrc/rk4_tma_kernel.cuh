@@ -233,22 +233,25 @@ rk4_f32_tma(const TileArgs ta) {
     const int b = k % C::NBUF;
     const uint32_t par = (uint32_t)((k / C::NBUF) & 1);
     const int tn = t + (C::NBUF - 1) * (int)gridDim.x;
-    if (tid == 0 && tn < ta.ntiles) {
-      fence_proxy_async();  // generic accesses of that buffer (previous tile) before TMA reuse
-      issue(cn, (k + C::NBUF - 1) % C::NBUF);
-      advance(cn, tn + (int)gridDim.x);
-    }
     // every thread waits on the barrier (bounded); the CTA leaves together
-    // if any thread gave up, after waiting (bounded) for its other loads
+    // if any thread gave up, after waiting (bounded) for its other loads.
+    // This barrier also closes the previous tile: every thread has finished
+    // reading its buffers and the shared stage buffer Y.
     const int fail = !mbar_wait_bounded(&bar[b], par);
     if (__syncthreads_or(fail)) {
       if (tid == 0) {
         atomicExch(ta.err, 1);
-        for (int j = k + 1; j < k + C::NBUF; ++j)
+        for (int j = k + 1; j < k + C::NBUF - 1; ++j)
           if (t + (j - k) * (int)gridDim.x < ta.ntiles)
             mbar_wait_bounded(&bar[j % C::NBUF], (uint32_t)((j / C::NBUF) & 1));
       }
       return;
+    }
+    // refill the buffer the previous tile used
+    if (tid == 0 && tn < ta.ntiles) {
+      fence_proxy_async();  // its generic reads before the async-proxy write
+      issue(cn, (k + C::NBUF - 1) % C::NBUF);
+      advance(cn, tn + (int)gridDim.x);
     }
 
     const int kx = cc.kx, ky = cc.ky;
@@ -373,8 +376,8 @@ rk4_f32_tma(const TileArgs ta) {
             *reinterpret_cast<float4*>(&dst[(r0 + j + 1) * C::PW + c0 + 2]) =
                 make_float4(ny[j][0].x, ny[j][0].y, ny[j][1].x, ny[j][1].y);
         }
+        __syncthreads();  // the last stage reads but writes no shared memory
       }
-      __syncthreads();
     }
 
     // psi' = psi0 + (K1 + 2K2 + 2K3 + K4) dt/6, written to the output tile
@@ -459,7 +462,6 @@ rk4_f32_tma(const TileArgs ta) {
         }
       }
     }
-    __syncthreads();
   }
 }
 
