@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--rk4-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=0,
-                    help="step-kernel configuration (0 = autotune, 1..6 TMA-fed, 9 generic)")
+                    help="step-kernel configuration (0 = autotune, 1..7 TMA-fed, 9 generic)")
     return ap.parse_args()
 
 
@@ -135,6 +135,7 @@ def workload(name, seed_offset=0, grid=1024):
 STEP_KERNEL_SOURCES = ("phx_internal.h", "phx_noise.cuh", "rk4_generic.cuh", "rk4_tma.h",
                        "rk4_tma_kernel.cuh", "rk4_tma.cu", "rk4_tma_cfg1.cu", "rk4_tma_cfg2.cu",
                        "rk4_tma_cfg3.cu", "rk4_tma_cfg4.cu", "rk4_tma_cfg5.cu", "rk4_tma_cfg6.cu",
+                       "rk4_tma_cfg7.cu",
                        "rk4_f32.cu", "rk4_f64.cu")
 
 
@@ -192,7 +193,7 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
@@ -203,14 +204,30 @@ class Clocks:
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
         os.unlink(self.path)
         if not sm:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if pw:
+            out["power_w_median"] = float(np.median(pw))
+        return out
+
+
+def energy(clk, seconds, updates):
+    """Board energy per site-update (the paper's energy per grid point and
+    step) from the median power sampled during the timed region."""
+    if not clk or "power_w_median" not in clk or updates <= 0:
+        return None
+    return {"nJ_per_site_update": clk["power_w_median"] * seconds / updates * 1e9,
+            "power_w_median": clk["power_w_median"], "source": "nvidia-smi power.draw"}
 
 
 def cpu_baseline(name, cfg, budget_s=15.0):
@@ -381,6 +398,7 @@ def run_ensemble(args, world, rank, local, pg):
                      "algorithmic_bytes_per_site": 28, "avg_launch_us": kern_s * 1e6,
                      "peak_source": pk_kind},
         "clocks": clk,
+        "energy": energy(clk, ms * 1e-3, sites * rk4_steps),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cfg, _, _ = workload("reservoir", grid=128)
@@ -540,6 +558,7 @@ def main():
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk,
+        "energy": energy(clk, ms * 1e-3, sites * rk4_steps),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wname, cfg)

@@ -73,7 +73,7 @@ typedef struct phx_params {
                                 0 = autotune (the first phx_step_n times each
                                 configuration on the handle's own state, without
                                 changing it, synchronising the stream once; the
-                                choice is cached per grid shape), 1..6 = a fixed
+                                choice is cached per grid shape), 1..7 = a fixed
                                 shared-memory region and thread shape of the
                                 TMA-fed persistent kernel, 9 = generic kernel */
   double hbar2_over_2m;      /* hbar^2/2m, meV um^2 */

@@ -166,7 +166,7 @@ cudaError_t launch_step(const phx_batch* b, int cur, int parity, cudaStream_t s)
 // cur and writes cur ^ 1, so repeating it leaves the state intact).
 phx_status autotune(phx_batch* b) {
   const int cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64, TILE_64x32,
-                       TILE_64x32_M2_2};
+                       TILE_64x32_M2_2, TILE_64x32_M4_2};
   cudaEvent_t e0, e1;
   PHX_BCK(b, cudaEventCreate(&e0));
   PHX_BCK(b, cudaEventCreate(&e1));

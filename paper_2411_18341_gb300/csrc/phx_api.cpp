@@ -172,7 +172,7 @@ phx_status autotune(phx_handle* h) {
     }
   }
   const int cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64, TILE_64x32,
-                       TILE_64x32_M2_2};
+                       TILE_64x32_M2_2, TILE_64x32_M4_2};
   cudaEvent_t e0, e1;
   PHX_CK(h, cudaEventCreate(&e0));
   PHX_CK(h, cudaEventCreate(&e1));

@@ -20,6 +20,7 @@ TmaBox tma_box(int tile_cfg) {
   if (tile_cfg == TILE_64x48_M2) { MR = 2; WY = 24; }
   if (tile_cfg == TILE_64x64_M2) { MR = 2; WY = 32; }
   if (tile_cfg == TILE_64x32_M2_2) { MR = 2; WY = 16; }
+  if (tile_cfg == TILE_64x32_M4_2) { MR = 4; WY = 8; }
   const int RW = 64, RH = MR * WY;
   b.psi_w = 2 * (RW + 4);  // floats (interleaved complex)
   b.psi_h = RH + 2;
@@ -30,7 +31,9 @@ TmaBox tma_box(int tile_cfg) {
   return b;
 }
 
-int tma_ctas_per_sm(int tile_cfg) { return tile_cfg == TILE_64x32_M2_2 ? 2 : 1; }
+int tma_ctas_per_sm(int tile_cfg) {
+  return tile_cfg == TILE_64x32_M2_2 || tile_cfg == TILE_64x32_M4_2 ? 2 : 1;
+}
 
 cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per,
                                const TileArgs& ta, cudaStream_t s, int grid) {
@@ -42,6 +45,7 @@ cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per,
     case TILE_64x48_M2: return launch_tma_cfg4(res, pot, per, one, ta, s, grid);
     case TILE_64x64_M2: return launch_tma_cfg5(res, pot, per, one, ta, s, grid);
     case TILE_64x32_M2_2: return launch_tma_cfg6(res, pot, per, one, ta, s, grid);
+    case TILE_64x32_M4_2: return launch_tma_cfg7(res, pot, per, one, ta, s, grid);
     default: break;
   }
   return cudaErrorInvalidValue;

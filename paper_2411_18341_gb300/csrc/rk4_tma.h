@@ -17,6 +17,7 @@ enum {
   TILE_64x48_M2 = 4,  // 2 x 2, 24 warps
   TILE_64x64_M2 = 5,  // 2 x 2, 32 warps
   TILE_64x32_M2_2 = 6,  // 2 x 2, 16 warps, two CTAs per SM
+  TILE_64x32_M4_2 = 7,  // 4 x 2, 8 warps, two CTAs per SM
   TILE_GENERIC = 9
 };
 
@@ -113,6 +114,8 @@ cudaError_t launch_tma_cfg4(bool res, bool pot, bool per, bool one, const TileAr
 cudaError_t launch_tma_cfg5(bool res, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
 cudaError_t launch_tma_cfg6(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid);
+cudaError_t launch_tma_cfg7(bool res, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
 
 }  // namespace phx

@@ -1,0 +1,12 @@
+// Instantiations of the persistent TMA-fed step kernel for tile
+// configuration 7 (4-row x 2-column micro-tiles, 8 warps, 2 CTAs per SM).
+#include "rk4_tma_kernel.cuh"
+
+namespace phx {
+
+cudaError_t launch_tma_cfg7(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+                            cudaStream_t s, int grid) {
+  return tma::launch_variants<4, 8, 2>(res, pot, per, one, ta, s, grid);
+}
+
+}  // namespace phx

@@ -276,7 +276,7 @@ def test_device_pointers_and_torch_stream():
     assert rel_l2(outn.cpu().numpy(), o_n) <= 1e-4
 
 
-TILES = [0, 1, 2, 3, 4, 5, 6, 9]  # auto, TMA-fed persistent configurations 1..6, generic
+TILES = [0, 1, 2, 3, 4, 5, 6, 7, 9]  # auto, TMA-fed persistent configurations 1..7, generic
 
 
 @pytest.mark.parametrize("tile", TILES)
