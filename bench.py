@@ -161,9 +161,10 @@ def recorded_traffic(workload_name, precision, tile=None):
     e = rec.get(key)
     if not e or e.get("kernel_sources") != kernel_hash():
         return None
-    if tile is not None and e.get("tile") not in (None, tile):
-        return None
-    return e.get("dram_bytes_per_launch")
+    tiles = e.get("tiles", {})
+    if tile is not None:
+        e = tiles.get(str(tile))
+    return e.get("dram_bytes_per_launch") if e else None
 
 
 class Clocks:
