@@ -147,6 +147,198 @@ __global__ void __launch_bounds__(GT) gemm_bf16_kernel(const GemmDesc d) {
       }
 }
 
+
+// ------------------------------------------- tcgen05 GEMM (M-tile 128)
+// C[b] = alpha * A[b] B[b] + beta * C[b] on the 5th-generation tensor cores:
+// the CTA's 128 threads stage 128 x 64 tiles of A and BN x 64 tiles of B
+// (FP32 from global, rounded to BF16) into shared memory in the canonical
+// K-major layout without swizzle -- 8-row x 16-byte core matrices, core
+// matrix (row group g, k group j) at (g * 8 + j) * 128 bytes, so the
+// stride between k groups (LBO) is 128 B and between row groups (SBO)
+// 1024 B -- and one elected thread issues four tcgen05.mma (K = 16 each)
+// per stage into a 128 x BN FP32 accumulator in tensor memory; a
+// tcgen05.commit on an mbarrier releases the stage's buffers.  Two stages
+// alternate.  The epilogue reads the accumulator with tcgen05.ld (warp w
+// owns TMEM lanes 32w..32w+31 = rows).  Waits are bounded; a CTA that gives
+// up raises *err and skips its epilogue.
+constexpr int TC_BM = 128, TC_BK = 64, TC_T = 128;
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  const uint64_t lbo = 128 >> 4, sbo = 1024 >> 4;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+#pragma unroll 1
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it >= 16) __nanosleep(64);
+  }
+  return false;
+}
+
+// byte offset of element (row, k) of a tile in the canonical layout
+__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+  return (uint32_t)((((row >> 3) << 3) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_T) gemm_tc_kernel(const GemmDesc d, int* err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  constexpr int A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
+  auto sA = [&](int st) { return tc_smem + st * A_BYTES; };
+  auto sB = [&](int st) { return tc_smem + 2 * A_BYTES + st * B_BYTES; };
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+  const int bz = blockIdx.z, b1 = bz / d.nb2, b2 = bz - b1 * d.nb2;
+  const float* A = d.A + b1 * d.a_b1 + b2 * d.a_b2;
+  const float* B = d.B + b1 * d.b_b1 + b2 * d.b_b2;
+  float* C = d.C + b1 * d.c_b1 + b2 * d.c_b2;
+  const int K = bz == (int)gridDim.z - 1 ? d.K_last : d.K;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // accumulator: BN columns x 128 lanes of tensor memory
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  // instruction descriptor: F32 accumulator, BF16 A and B, both K-major,
+  // N >> 3 at bit 17, M >> 4 at bit 24
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)(TC_BM >> 4) << 24);
+
+  const int nk = (K + TC_BK - 1) / TC_BK;
+  bool ok = true;
+  for (int kc = 0; kc < nk; ++kc) {
+    const int st = kc & 1;
+    if (kc >= 2 && ok) ok = tc_wait(&mbar[st], (uint32_t)(((kc - 2) >> 1) & 1));
+    const int k0 = kc * TC_BK;
+    // stage A (pairs of k per thread -> one 4-byte shared store)
+    for (int e = tid; e < TC_BM * TC_BK / 2; e += TC_T) {
+      int row, kp;
+      if (d.a_k == 1) {
+        row = e / (TC_BK / 2);
+        kp = e - row * (TC_BK / 2);
+      } else {
+        kp = e / TC_BM;
+        row = e - kp * TC_BM;
+      }
+      const int m = m0 + row, k = k0 + 2 * kp;
+      float v0 = 0.f, v1 = 0.f;
+      if (m < d.M) {
+        const float* ap = A + m * d.a_m;
+        if (k < K) v0 = ap[k * d.a_k];
+        if (k + 1 < K) v1 = ap[(k + 1) * d.a_k];
+      }
+      __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+      *reinterpret_cast<__nv_bfloat162*>(sA(st) + tc_off(row, 2 * kp)) = h;
+    }
+    for (int e = tid; e < BN * TC_BK / 2; e += TC_T) {
+      int col, kp;
+      if (d.b_k == 1) {
+        col = e / (TC_BK / 2);
+        kp = e - col * (TC_BK / 2);
+      } else {
+        kp = e / BN;
+        col = e - kp * BN;
+      }
+      const int n = n0 + col, k = k0 + 2 * kp;
+      float v0 = 0.f, v1 = 0.f;
+      if (n < d.N) {
+        const float* bp = B + n * d.b_n;
+        if (k < K) v0 = bp[k * d.b_k];
+        if (k + 1 < K) v1 = bp[(k + 1) * d.b_k];
+      }
+      __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+      *reinterpret_cast<__nv_bfloat162*>(sB(st) + tc_off(col, 2 * kp)) = h;
+    }
+    // generic-proxy shared stores -> visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t da = tc_desc(su32(sA(st))), db = tc_desc(su32(sB(st)));
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+        // K = 16 spans two k groups: advance the start address by 2 * LBO
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da + (uint64_t)(kk * 16)), "l"(db + (uint64_t)(kk * 16)), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              su32(&mbar[st]))
+          : "memory");
+    }
+  }
+  // all MMAs done: the last stage's commit covers every earlier one
+  if (nk > 0 && ok) ok = tc_wait(&mbar[(nk - 1) & 1], (uint32_t)(((nk - 1) >> 1) & 1));
+  if (nk > 1 && ok) ok = tc_wait(&mbar[nk & 1], (uint32_t)(((nk - 2) >> 1) & 1));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int m = m0 + 32 * warp + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < d.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < d.N) {
+            float* p = C + m * d.c_m + n * d.c_n;
+            const float v = d.alpha * __uint_as_float(r[j]);
+            *p = d.beta == 0.f ? v : v + d.beta * *p;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                 : "memory");
+  }
+}
+
 // Deterministic split-K reduction: out = alpha * sum_s part[s] + beta * out.
 __global__ void splitk_reduce_kernel(const float* part, int S, int M, int N, float* C,
                                      long long c_m, long long c_n, float alpha, float beta) {
@@ -343,6 +535,7 @@ struct phx_fno {
   float* splitk = nullptr;
   long long splitk_len = 0;
   float* colpart = nullptr;
+  int* tc_err = nullptr;  // set by a tensor-core GEMM whose bounded wait gave up
   double* lpart = nullptr;
   double* lpart_host = nullptr;
   int device = 0;
@@ -382,7 +575,34 @@ GemmDesc gd(int M, int N, int K, int nb1, int nb2, const float* A, long long a_m
   return d;
 }
 
+template <int BN>
+cudaError_t run_gemm_tc(phx_fno* f, const GemmDesc& d) {
+  const int smem = 2 * TC_BM * TC_BK * 2 + 2 * BN * TC_BK * 2;
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  dim3 grid((d.M + TC_BM - 1) / TC_BM, (d.N + BN - 1) / BN, d.nb1 * d.nb2);
+  gemm_tc_kernel<BN><<<grid, TC_T, smem, f->stream>>>(d, f->tc_err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Tall products (M >= 128: the pointwise layers over batch x H x W rows and
+// the inverse DFTs over H or W rows) run on tcgen05 with a 128-row tile;
+// short ones (the forward truncated DFTs, the per-mode mixing, the split-K
+// weight gradients) on the mma.sync kernel, whose 64-row tile wastes less.
 cudaError_t run_gemm(phx_fno* f, const GemmDesc& d) {
+  if (d.M >= TC_BM && d.N <= 256) {
+    if (d.N <= 32) return run_gemm_tc<32>(f, d);
+    if (d.N <= 64) return run_gemm_tc<64>(f, d);
+    if (d.N <= 128) return run_gemm_tc<128>(f, d);
+  }
   dim3 grid((d.M + GM - 1) / GM, (d.N + GN - 1) / GN, d.nb1 * d.nb2);
   gemm_bf16_kernel<<<grid, GT, 0, f->stream>>>(d);
   count_launch();
@@ -684,6 +904,7 @@ void free_fno(phx_fno* f) {
   for (float* p : f->Vxy_l)
     if (p) cudaFree(p);
   if (f->lpart) cudaFree(f->lpart);
+  if (f->tc_err) cudaFree(f->tc_err);
   if (f->lpart_host) cudaFreeHost(f->lpart_host);
 }
 
@@ -788,6 +1009,8 @@ phx_status phx_fno_create(const phx_fno_config* cfg, phx_fno** out) {
   if (e == cudaSuccess) e = alloc(&f->splitk, f->splitk_len);
   if (e == cudaSuccess) e = alloc(&f->colpart, 512LL * 256);
   if (e == cudaSuccess) e = cudaMalloc(&f->lpart, sizeof(double) * 512);
+  if (e == cudaSuccess) e = cudaMalloc(&f->tc_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->tc_err, 0, sizeof(int), f->stream);
   if (e == cudaSuccess) e = cudaMallocHost(&f->lpart_host, sizeof(double) * 512);
   if (e != cudaSuccess) return fail_alloc(e);
   // DFT tables (FP64 angles, FP32 values)
@@ -856,6 +1079,9 @@ phx_status phx_fno_loss_grad(phx_fno* f, const float* in, const float* target, i
   if (batch < 1 || batch > f->cfg.max_batch) return ffail(f, PHX_EINVAL, "batch out of range");
   PHX_FCK(f, forward(f, in, batch));
   PHX_FCK(f, backward(f, in, target, batch, loss));
+  int tc_err = 0;
+  PHX_FCK(f, cudaMemcpy(&tc_err, f->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (tc_err) return ffail(f, PHX_ETIMEOUT, "a tensor-core GEMM wait timed out");
   if (grad) {
     PHX_FCK(f, cudaMemcpyAsync(grad, f->g, sizeof(float) * f->nparams, cudaMemcpyDeviceToDevice,
                                f->stream));

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 def test_warm_start_beats_cold_start():
     phx()
     from paper_2411_18341_gb300 import warmstart
-    rep, net = warmstart.run_experiment(n_train=192, n_test=48, gen_steps=30000, epochs=12,
+    rep, net = warmstart.run_experiment(n_train=192, n_test=96, gen_steps=30000, epochs=12,
                                         cap=60000, log=lambda s: None)
     # the network learned something it did not know at initialisation
     assert rep["heldout_loss"] < 0.5 * rep["train_loss"][0]
