@@ -193,6 +193,48 @@ __device__ __forceinline__ uint32_t tc_off(int row, int k) {
   return (uint32_t)((((row >> 3) << 3) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
 }
 
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Stage rows [r0, r0 + NR) x k [k0, k0 + 64) of a strided FP32 matrix
+// (element (r, k) at src[r * s_row + k * s_k], zero outside nrows x K) as
+// BF16 in the canonical layout.  One unit = (row, group of 8 k) = one
+// 16-byte shared store; consecutive threads take consecutive rows, so each
+// quarter-warp's eight stores fill all 32 banks of one core matrix.
+template <int NR>
+__device__ __forceinline__ void tc_stage(unsigned char* dst, const float* src, int nrows, int r0,
+                                         long long s_row, long long s_k, int k0, int K, int tid) {
+  constexpr int UNITS = NR * (TC_BK / 8);
+  for (int u = tid; u < UNITS; u += TC_T) {
+    const int kg = u / NR, row = u - kg * NR;
+    const int r = r0 + row, k = k0 + kg * 8;
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = 0.f;
+    if (r < nrows && k < K) {
+      const float* p = src + r * s_row + (long long)k * s_k;
+      if (s_k == 1 && k + 8 <= K && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        const float4 y = *reinterpret_cast<const float4*>(p + 4);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (k + i < K) v[i] = p[(long long)i * s_k];
+      }
+    }
+    uint4 q;
+    q.x = pack_bf2(v[0], v[1]);
+    q.y = pack_bf2(v[2], v[3]);
+    q.z = pack_bf2(v[4], v[5]);
+    q.w = pack_bf2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(dst + tc_off(row, kg * 8)) = q;
+  }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(TC_T) gemm_tc_kernel(const GemmDesc d, int* err) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -236,45 +278,8 @@ __global__ void __launch_bounds__(TC_T) gemm_tc_kernel(const GemmDesc d, int* er
     const int st = kc & 1;
     if (kc >= 2 && ok) ok = tc_wait(&mbar[st], (uint32_t)(((kc - 2) >> 1) & 1));
     const int k0 = kc * TC_BK;
-    // stage A (pairs of k per thread -> one 4-byte shared store)
-    for (int e = tid; e < TC_BM * TC_BK / 2; e += TC_T) {
-      int row, kp;
-      if (d.a_k == 1) {
-        row = e / (TC_BK / 2);
-        kp = e - row * (TC_BK / 2);
-      } else {
-        kp = e / TC_BM;
-        row = e - kp * TC_BM;
-      }
-      const int m = m0 + row, k = k0 + 2 * kp;
-      float v0 = 0.f, v1 = 0.f;
-      if (m < d.M) {
-        const float* ap = A + m * d.a_m;
-        if (k < K) v0 = ap[k * d.a_k];
-        if (k + 1 < K) v1 = ap[(k + 1) * d.a_k];
-      }
-      __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-      *reinterpret_cast<__nv_bfloat162*>(sA(st) + tc_off(row, 2 * kp)) = h;
-    }
-    for (int e = tid; e < BN * TC_BK / 2; e += TC_T) {
-      int col, kp;
-      if (d.b_k == 1) {
-        col = e / (TC_BK / 2);
-        kp = e - col * (TC_BK / 2);
-      } else {
-        kp = e / BN;
-        col = e - kp * BN;
-      }
-      const int n = n0 + col, k = k0 + 2 * kp;
-      float v0 = 0.f, v1 = 0.f;
-      if (n < d.N) {
-        const float* bp = B + n * d.b_n;
-        if (k < K) v0 = bp[k * d.b_k];
-        if (k + 1 < K) v1 = bp[(k + 1) * d.b_k];
-      }
-      __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-      *reinterpret_cast<__nv_bfloat162*>(sB(st) + tc_off(col, 2 * kp)) = h;
-    }
+    tc_stage<TC_BM>(sA(st), A, d.M, m0, d.a_m, d.a_k, k0, K, tid);
+    tc_stage<BN>(sB(st), B, d.N, n0, d.b_n, d.b_k, k0, K, tid);
     // generic-proxy shared stores -> visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -316,13 +321,30 @@ __global__ void __launch_bounds__(TC_T) gemm_tc_kernel(const GemmDesc d, int* er
           : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (m < d.M) {
+        float* row = C + m * d.c_m + (long long)(n0 + c0) * d.c_n;
+        if (d.c_n == 1 && n0 + c0 + 16 <= d.N && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = n0 + c0 + j;
-          if (n < d.N) {
-            float* p = C + m * d.c_m + n * d.c_n;
-            const float v = d.alpha * __uint_as_float(r[j]);
-            *p = d.beta == 0.f ? v : v + d.beta * *p;
+          for (int q = 0; q < 4; ++q) {
+            float4 o = make_float4(d.alpha * __uint_as_float(r[4 * q]),
+                                   d.alpha * __uint_as_float(r[4 * q + 1]),
+                                   d.alpha * __uint_as_float(r[4 * q + 2]),
+                                   d.alpha * __uint_as_float(r[4 * q + 3]));
+            float4* p4 = reinterpret_cast<float4*>(row) + q;
+            if (d.beta != 0.f) {
+              const float4 c = *p4;
+              o.x += d.beta * c.x; o.y += d.beta * c.y; o.z += d.beta * c.z; o.w += d.beta * c.w;
+            }
+            *p4 = o;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < d.N) {
+              float* p = C + m * d.c_m + n * d.c_n;
+              const float v = d.alpha * __uint_as_float(r[j]);
+              *p = d.beta == 0.f ? v : v + d.beta * *p;
+            }
           }
         }
       }
