@@ -135,12 +135,11 @@ def workload(name, seed_offset=0, grid=1024):
 STEP_KERNEL_SOURCES = ("phx_internal.h", "phx_noise.cuh", "rk4_generic.cuh", "rk4_tma.h",
                        "rk4_tma_kernel.cuh", "rk4_tma.cu", "rk4_tma_cfg1.cu", "rk4_tma_cfg2.cu",
                        "rk4_tma_cfg3.cu", "rk4_tma_cfg4.cu", "rk4_tma_cfg5.cu", "rk4_tma_cfg6.cu",
-                       "rk4_tma_cfg7.cu",
-                       "rk4_f32.cu", "rk4_f64.cu")
+                       "rk4_tma_cfg7.cu")
 
 
 def kernel_hash():
-    """Hash of the sources the fused step kernels are compiled from."""
+    """Hash of the sources the TMA-fed scalar step kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_18341_gb300", "csrc")
     for f in STEP_KERNEL_SOURCES:

@@ -75,7 +75,10 @@ typedef struct phx_params {
                                 changing it, synchronising the stream once; the
                                 choice is cached per grid shape), 1..7 = a fixed
                                 shared-memory region and thread shape of the
-                                TMA-fed persistent kernel, 9 = generic kernel */
+                                TMA-fed persistent kernel, 9 = generic kernel;
+                                for the generic kernels of the FP32 spinor +
+                                reservoir + TE-TM and FP64 scalar reservoir
+                                models 10..12 select other tile shapes */
   double hbar2_over_2m;      /* hbar^2/2m, meV um^2 */
   double g, g_x, g_r;        /* meV um^2 */
   double R;                  /* ps^-1 um^2 */

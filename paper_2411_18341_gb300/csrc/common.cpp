@@ -184,21 +184,22 @@ bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* c
   const int nc = p.spinor ? 2 : 1;
   std::memset(&I, 0, sizeof I);
   for (int k = 0; k < 2; ++k) {
+    // the two-component kernel fetches both component planes in one box
     if (!encode_map_f32(&I.psi[k], psi[k], 2ull * g.pitch, g.prow, nc,
                         (unsigned long long)g.pitch * 8, (unsigned long long)g.plane * 8,
-                        b.psi_w, b.psi_h))
+                        b.psi_w, b.psi_h, nc))
       return false;
     I.psi_buf[k] = static_cast<float2*>(psi[k]);
     if (p.reservoir) {
       if (!encode_map_f32(&I.n[k], n[k], g.pitch, g.prow, nc, (unsigned long long)g.pitch * 4,
-                          (unsigned long long)g.plane * 4, b.f_w, b.f_h))
+                          (unsigned long long)g.plane * 4, b.f_w, b.f_h, nc))
         return false;
       I.n_buf[k] = static_cast<float*>(n[k]);
     }
   }
   if (p.reservoir &&
       !encode_map_f32(&I.P, P, g.pitch, g.prow, nc, (unsigned long long)g.pitch * 4,
-                      (unsigned long long)g.plane * 4, b.f_w, b.f_h))
+                      (unsigned long long)g.plane * 4, b.f_w, b.f_h, nc))
     return false;
   if (V && !encode_map_f32(&I.V, V, g.pitch, g.prow, 1, (unsigned long long)g.pitch * 4,
                            (unsigned long long)g.plane * 4, b.f_w, b.f_h))

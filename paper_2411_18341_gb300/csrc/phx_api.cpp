@@ -63,6 +63,8 @@ bool periodic(const phx_params& p) {
   return p.bc_x == PHX_BC_PERIODIC && p.bc_y == PHX_BC_PERIODIC;
 }
 
+bool spinor_tma_cfg(int cfg) { return cfg >= TILE_SPINOR_64x16 && cfg <= TILE_SPINOR_64x32; }
+
 phx_status fail(phx_handle* h, phx_status s, const std::string& msg) {
   if (h)
     h->err = msg;
@@ -156,12 +158,20 @@ std::map<std::tuple<int, int, int, int, int, int, int>, int> g_tune;
 bool encode_maps(phx_handle* h);
 TileArgs tile_args(phx_handle* h, int inj);
 
+// One persistent TMA-fed step launch in configuration cfg.
+cudaError_t launch_tma(phx_handle* h, int cfg, const TileArgs& ta, int grid) {
+  if (spinor_tma_cfg(cfg))
+    return launch_rk4_tma_spinor(cfg, h->has_V, periodic(h->p), h->m.tetm, ta, h->stream, grid);
+  return launch_rk4_tma_f32(cfg, h->m.reservoir, h->has_V, periodic(h->p), ta, h->stream, grid);
+}
+
 // Time every tile configuration of the FP32 scalar kernel on this handle's
 // own state and keep the fastest.  A step reads the current buffer and writes
 // the other one, so repeating it without swapping leaves the state intact.
 phx_status autotune(phx_handle* h) {
   const auto key = std::make_tuple(h->device, h->p.nx, h->p.ny, h->p.bc_x, h->p.bc_y,
-                                   (int)h->m.reservoir, (int)h->has_V);
+                                   (int)h->m.reservoir + 2 * h->m.ncomp + 8 * (int)h->m.tetm,
+                                   (int)h->has_V);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -171,14 +181,17 @@ phx_status autotune(phx_handle* h) {
       return PHX_OK;
     }
   }
-  const int cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64, TILE_64x32,
-                       TILE_64x32_M2_2, TILE_64x32_M4_2};
+  const int scalar_cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64,
+                              TILE_64x32, TILE_64x32_M2_2, TILE_64x32_M4_2};
+  const int spinor_cands[] = {TILE_SPINOR_64x24, TILE_SPINOR_64x16, TILE_SPINOR_64x32};
+  const bool sp = h->m.ncomp == 2;
+  const int* cands = sp ? spinor_cands : scalar_cands;
   cudaEvent_t e0, e1;
   PHX_CK(h, cudaEventCreate(&e0));
   PHX_CK(h, cudaEventCreate(&e1));
   // three interleaved rounds; each configuration keeps its fastest round
-  const int nc = (int)(sizeof cands / sizeof cands[0]);
-  float cfg_ms[sizeof cands / sizeof cands[0]];
+  const int nc = sp ? 3 : 7;
+  float cfg_ms[7];
   for (int c = 0; c < nc; ++c) cfg_ms[c] = 1e30f;
   for (int round = 0; round < 3; ++round) {
     for (int c = 0; c < nc; ++c) {
@@ -189,10 +202,7 @@ phx_status autotune(phx_handle* h) {
       const TileArgs ta = tile_args(h, 0);
       const int slots = h->num_sms * tma_ctas_per_sm(cfg);
       const int grid = ta.ntiles < slots ? ta.ntiles : slots;
-      auto launch = [&]() {
-        return launch_rk4_tma_f32(cfg, h->m.reservoir, h->has_V, periodic(h->p), ta, h->stream,
-                                  grid);
-      };
+      auto launch = [&]() { return launch_tma(h, cfg, ta, grid); };
       cudaError_t e = cudaSuccess;
       for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch();
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
@@ -209,7 +219,7 @@ phx_status autotune(phx_handle* h) {
     }
   }
   float best_ms = 1e30f;
-  int best = TILE_64x48_M2;
+  int best = cands[0];
   for (int c = 0; c < nc; ++c)
     if (cfg_ms[c] < best_ms) {
       best_ms = cfg_ms[c];
@@ -243,6 +253,7 @@ TileArgs tile_args(phx_handle* h, int inj) {
   ta.inst = h->d_inst;
   ta.tile_info = nullptr;
   ta.one = scalars_of(h->h_inst);
+  ta.one.p_shared = h->P_stride == 0;
   ta.ntiles = h->h_inst.tiles_x * h->h_inst.tiles_y;
   ta.ninst = 1;
   ta.cur = h->cur;
@@ -372,7 +383,13 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
     delete h;
     return fail(nullptr, ce == cudaErrorMemoryAllocation ? PHX_ENOMEM : PHX_ECUDA, msg);
   }
-  h->tile_cfg = (p->precision == 32 && !p->spinor) ? choose_tile(h) : TILE_GENERIC;
+  if (p->precision == 32 && !p->spinor)
+    h->tile_cfg = choose_tile(h);
+  else if (p->precision == 32 && p->spinor && p->reservoir &&
+           (p->tile == 0 || spinor_tma_cfg(p->tile)))
+    h->tile_cfg = p->tile ? p->tile : TILE_SPINOR_64x24;
+  else
+    h->tile_cfg = TILE_GENERIC;
   *out = h;
   return PHX_OK;
 }
@@ -478,7 +495,8 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.clock = h->clock;
       a.parity = h->parity;
       a.inject_timeout = inj;
-      if (h->tile_cfg != TILE_GENERIC && h->m.ncomp == 1) {
+      if (h->tile_cfg != TILE_GENERIC &&
+          (h->m.ncomp == 1 || spinor_tma_cfg(h->tile_cfg))) {
         if (!h->tuned) {
           if (h->p.tile == 0) {
             phx_status ts = autotune(h);
@@ -492,8 +510,7 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
         const TileArgs ta = tile_args(h, inj);
         const int slots = h->num_sms * tma_ctas_per_sm(h->tile_cfg);
         const int grid = ta.ntiles < slots ? ta.ntiles : slots;
-        e = launch_rk4_tma_f32(h->tile_cfg, h->m.reservoir, h->has_V, periodic(h->p), ta,
-                               h->stream, grid);
+        e = launch_tma(h, h->tile_cfg, ta, grid);
       } else {
         e = launch_rk4_step_f32(h->m, a, h->stream, h->p.tile);
       }

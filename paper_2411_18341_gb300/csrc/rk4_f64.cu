@@ -5,9 +5,15 @@ namespace phx {
 
 cudaError_t launch_rk4_step_f64(const ModelKey& m, const StepArgs<double>& a,
                                 cudaStream_t s, int tile) {
-  (void)tile;
   if (m.ncomp == 1) {
-    if (m.reservoir) return launch_generic<double, 1, true, false, 16, 16, 128>(a, s);
+    if (m.reservoir) {
+      // tile shapes of the scalar reservoir kernel (phx_params.tile 10..12;
+      // the default 32 x 32 was the fastest at 2048^2: less halo recompute)
+      if (tile == 10) return launch_generic<double, 1, true, false, 32, 16, 256>(a, s);
+      if (tile == 11) return launch_generic<double, 1, true, false, 16, 16, 128>(a, s);
+      if (tile == 12) return launch_generic<double, 1, true, false, 64, 16, 256>(a, s);
+      return launch_generic<double, 1, true, false, 32, 32, 256>(a, s);
+    }
     return launch_generic<double, 1, false, false, 16, 16, 128>(a, s);
   }
   if (m.tetm) {

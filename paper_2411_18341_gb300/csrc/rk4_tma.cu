@@ -21,6 +21,9 @@ TmaBox tma_box(int tile_cfg) {
   if (tile_cfg == TILE_64x64_M2) { MR = 2; WY = 32; }
   if (tile_cfg == TILE_64x32_M2_2) { MR = 2; WY = 16; }
   if (tile_cfg == TILE_64x32_M4_2) { MR = 4; WY = 8; }
+  if (tile_cfg == TILE_SPINOR_64x16) { MR = 2; WY = 8; }
+  if (tile_cfg == TILE_SPINOR_64x24) { MR = 2; WY = 12; }
+  if (tile_cfg == TILE_SPINOR_64x32) { MR = 2; WY = 16; }
   const int RW = 64, RH = MR * WY;
   b.psi_w = 2 * (RW + 4);  // floats (interleaved complex)
   b.psi_h = RH + 2;
@@ -68,12 +71,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 bool encode_map_f32(CUtensorMap* map, void* base, unsigned long long w,
                     unsigned long long h, unsigned long long planes,
                     unsigned long long row_bytes, unsigned long long plane_bytes,
-                    unsigned box_w, unsigned box_h) {
+                    unsigned box_w, unsigned box_h, unsigned box_d) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {w, h, planes};
   cuuint64_t strides[2] = {row_bytes, plane_bytes};
-  cuuint32_t box[3] = {box_w, box_h, 1};
+  cuuint32_t box[3] = {box_w, box_h, box_d};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -18,6 +18,10 @@ enum {
   TILE_64x64_M2 = 5,  // 2 x 2, 32 warps
   TILE_64x32_M2_2 = 6,  // 2 x 2, 16 warps, two CTAs per SM
   TILE_64x32_M4_2 = 7,  // 4 x 2, 8 warps, two CTAs per SM
+  // two-component field with reservoirs (2 x 2 micro-tiles of both components)
+  TILE_SPINOR_64x16 = 21,  // 8 warps
+  TILE_SPINOR_64x24 = 22,  // 12 warps
+  TILE_SPINOR_64x32 = 23,  // 16 warps
   TILE_GENERIC = 9
 };
 
@@ -41,6 +45,7 @@ struct alignas(128) TileInst {
 // The scalar part of one instance, passed by value in the kernel parameters
 // when a launch covers a single instance.
 struct InstScalars {
+  int p_shared;  // two-component field: both components read pump plane 0
   Geometry geo;
   CoeffsT<float> k;
   NoiseKey noise;
@@ -51,6 +56,7 @@ struct InstScalars {
 
 inline InstScalars scalars_of(const TileInst& I) {
   InstScalars s;
+  s.p_shared = 0;
   s.geo = I.geo;
   s.k = I.k;
   s.noise = I.noise;
@@ -90,7 +96,7 @@ int tma_ctas_per_sm(int tile_cfg);
 bool encode_map_f32(CUtensorMap* map, void* base, unsigned long long w,
                     unsigned long long h, unsigned long long planes,
                     unsigned long long row_bytes, unsigned long long plane_bytes,
-                    unsigned box_w, unsigned box_h);
+                    unsigned box_w, unsigned box_h, unsigned box_d = 1);
 
 // Build the descriptor of one instance (host memory) for a tile
 // configuration; false if a tensor map cannot be encoded.
@@ -101,6 +107,10 @@ bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* c
 // never forces stage values to zero).
 cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per, const TileArgs& ta,
                                cudaStream_t s, int grid);
+
+// Two-component field with reservoirs (rk4_tma_spinor.cu); tetm: TE-TM coupling.
+cudaError_t launch_rk4_tma_spinor(int tile_cfg, bool pot, bool per, bool tetm,
+                                  const TileArgs& ta, cudaStream_t s, int grid);
 
 // One per tile configuration (rk4_tma_cfgN.cu): every model variant of it.
 cudaError_t launch_tma_cfg1(bool res, bool pot, bool per, bool one, const TileArgs& ta,

@@ -326,3 +326,52 @@ def test_fp32_scalar_noise_bit_path():
     re, im = noise.noise_field(5, 7, 0, 1, 61, 70, 2e-3)
     assert np.array_equal(g.real.astype(np.float32), re)
     assert np.array_equal(g.imag.astype(np.float32), im)
+
+
+SPINOR_TILES = [0, 21, 22, 23, 9, 10, 11, 12]  # auto, TMA-fed 21..23, generic shapes 9..12
+
+
+@pytest.mark.parametrize("tile", SPINOR_TILES)
+@pytest.mark.parametrize("tetm", [True, False])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1), (1, 0)])
+@pytest.mark.parametrize("size", [(131, 77), (58, 58), (70, 45), (5, 3)])
+def test_fp32_spinor_tile_configs(tile, tetm, bc, size):
+    """Every configuration of the FP32 two-component reservoir kernels (with
+    and without TE-TM, separate pump planes, a potential) against the oracle."""
+    m = phx()
+    d = model("spinor_res_tetm", *size, bc=bc)
+    if not tetm:
+        d["delta_lt"] = 0.0
+        d["dt"] = min(0.45 * gp.stability_dt_max(gp.Params(**d)), 0.05)
+    psi0, n0, P, V = synth.random_state(2, size[1], size[0], 6, amp=0.7, smooth=True)
+    psi0, n0, P, V = (rounded(x, 32) for x in (psi0, n0, P, V))
+    h = m.phx_create(m.params_from_dict(d, precision=32, tile=tile))
+    m.phx_set_pump(h, np.ascontiguousarray(P[0], np.float32), np.ascontiguousarray(P[1], np.float32))
+    m.phx_set_potential(h, np.ascontiguousarray(V, np.float32))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, np.complex64), np.ascontiguousarray(n0, np.float32))
+    m.phx_step_n(h, 9)
+    g_psi, g_n = get_state(h, 32)
+    o_psi, o_n = gp.run(psi0, n0, P, V, gp.Params(**d), 9)
+    assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
+    assert rel_l2(g_n, o_n) <= 1e-4, rel_l2(g_n, o_n)
+    if tile in (21, 22, 23) or (tile == 0 and size[0] >= 8):
+        assert m.phx_tile(h) in (21, 22, 23)
+
+
+@pytest.mark.parametrize("tile", [21, 22, 23])
+def test_fp32_spinor_shared_pump_and_noise(tile):
+    """TMA-fed two-component kernel with one pump plane for both components
+    and per-step noise: against the oracle (which adds the same Philox bits)."""
+    m = phx()
+    d = model("spinor_res_tetm", 97, 66, noise_var=1e-4)
+    psi0, n0, P, V = synth.random_state(2, 66, 97, 8, amp=0.7, smooth=True)
+    psi0, n0, P, V = (rounded(x, 32) for x in (psi0, n0, P, V))
+    h = m.phx_create(m.params_from_dict(d, precision=32, tile=tile))
+    m.phx_set_pump(h, np.ascontiguousarray(P[0], np.float32))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, np.complex64), np.ascontiguousarray(n0, np.float32))
+    m.phx_step_n(h, 6)
+    g_psi, g_n = get_state(h, 32)
+    Pboth = np.stack([P[0], P[0]])
+    o_psi, o_n = gp.run(psi0, n0, Pboth, None, gp.Params(**d), 6)
+    assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
+    assert rel_l2(g_n, o_n) <= 1e-4
