@@ -1,17 +1,18 @@
 #pragma once
-// Kernel template of the persistent, TMA-fed fused RK4 step for the FP32 scalar field (Eq. 1 /
-// Eq. PULSE_psi with one component, optionally with the reservoir of
-// Eq. PULSE_res and a potential V).
+// Kernel template of the persistent, TMA-fed fused RK4 step for the FP32
+// scalar field (Eq. 1 / Eq. PULSE_psi with one component, optionally with the
+// reservoir of Eq. PULSE_res and a potential V).
 //
-// Per CTA (one per SM, 32*WY threads) a loop over output tiles:
-//   * the next tile's psi box (tile + depth-4 halo) and its n, P, V boxes are
-//     fetched by cp.async.bulk.tensor into the other half of a double buffer
+// Per CTA (one or two per SM, 32*WY threads) a loop over output tiles:
+//   * the next tiles' psi box (tile + depth-4 halo) and n, P, V boxes are
+//     fetched by cp.async.bulk.tensor into a ring of two or three buffers
 //     while the current tile is computed (mbarrier completion, bounded waits);
 //   * thread (lane, warp) owns a 2-column x MR-row micro-tile of the ring-3
 //     region: psi0, the running stage value, the accumulator sum_k w_k K_k and
-//     the reservoir values stay in registers across the four stages; only the
-//     micro-tile's neighbours cross shared memory (16-byte row loads above and
-//     below, 8-byte column loads left and right, one 16-byte store per row);
+//     the reservoir values stay in registers across the four stages; between
+//     stages only the micro-tile's first and last rows cross shared memory
+//     (read by the warps above and below, 16-byte accesses), east/west
+//     neighbours come from the neighbouring lanes by warp shuffles;
 //   * complex arithmetic uses the packed FP32x2 instructions of sm_100+
 //     (__ffma2_rn / __fadd2_rn / __fmul2_rn on (re, im) pairs);
 //   * psi' = psi0 + (K1 + 2K2 + 2K3 + K4) dt/6 (+ noise) is stored with

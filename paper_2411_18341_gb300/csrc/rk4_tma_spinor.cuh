@@ -343,19 +343,51 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
         }
       }
     }
+    // Interior tiles (no ghost image, no clipping): 16-byte psi and 8-byte n
+    // stores per micro-tile row and component.
+    const int ox0 = xp - 1, oy0 = cc.ky * C::TY;
+    const bool interior = ox0 >= HALO && ox0 + C::TX <= g.nx - HALO && oy0 >= HALO &&
+                          oy0 + C::TY <= g.ny - HALO;
+    if (interior) {
+      const bool lo = c0 >= 3 && c0 < 3 + C::TX;
+      const bool hi = c0 + 1 >= 3 && c0 + 1 < 3 + C::TX;
 #pragma unroll
-    for (int j = 0; j < MR; ++j) {
-      const int r = r0 + j;
-      const int gy = gy0 + j;
-      if (r < 3 || r >= 3 + C::TY || gy >= g.ny) continue;
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int cix = c0 + i, gx = gx0 + i;
-        if (cix < 3 || cix >= 3 + C::TX || gx < 0 || gx >= g.nx) continue;
+      for (int j = 0; j < MR; ++j) {
+        const int r = r0 + j;
+        if (r < 3 || r >= 3 + C::TY) continue;  // warp-uniform
+        const long long roff = (long long)(gy0 + j + HALO) * g.pitch + gx0 + HALO;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          store_with_ghosts(psi_out + c * g.plane, g, gx, gy, o[j][i][c]);
-          store_with_ghosts(n_out + c * g.plane, g, gx, gy, on[j][i][c]);
+          float2* po = psi_out + c * g.plane + roff;
+          float* pn = n_out + c * g.plane + roff;
+          if (lo && hi) {
+            *reinterpret_cast<float4*>(po) =
+                make_float4(o[j][0][c].x, o[j][0][c].y, o[j][1][c].x, o[j][1][c].y);
+            *reinterpret_cast<float2*>(pn) = f2(on[j][0][c], on[j][1][c]);
+          } else if (lo) {
+            po[0] = o[j][0][c];
+            pn[0] = on[j][0][c];
+          } else if (hi) {
+            po[1] = o[j][1][c];
+            pn[1] = on[j][1][c];
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < MR; ++j) {
+        const int r = r0 + j;
+        const int gy = gy0 + j;
+        if (r < 3 || r >= 3 + C::TY || gy >= g.ny) continue;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int cix = c0 + i, gx = gx0 + i;
+          if (cix < 3 || cix >= 3 + C::TX || gx < 0 || gx >= g.nx) continue;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            store_with_ghosts(psi_out + c * g.plane, g, gx, gy, o[j][i][c]);
+            store_with_ghosts(n_out + c * g.plane, g, gx, gy, on[j][i][c]);
+          }
         }
       }
     }

@@ -96,3 +96,22 @@ def test_status_strings(phx):
     assert L.phx_status_string(0) == b"PHX_OK"
     assert L.phx_status_string(5) == b"PHX_ETIMEOUT"
     assert L.phx_last_error(None)
+
+
+def test_fno_config_struct_layout_matches_c(phx):
+    """phx_fno_config_init fills the binding's struct: size and defaults agree
+    (256 x 256, C = 32, 4 layers, 16 x 32 modes, P = 64)."""
+    c = phx.phx_fno_config()
+    assert phx.lib().phx_fno_config_init(ctypes.byref(c)) == 0
+    assert c.struct_size == ctypes.sizeof(phx.phx_fno_config)
+    assert (c.height, c.width, c.channels, c.layers, c.modes_x, c.modes_y) == (256, 256, 32, 4, 16, 32)
+    assert (c.in_channels, c.out_channels, c.proj_hidden, c.max_batch) == (3, 3, 64, 8)
+
+
+def test_fno_invalid_config_rejected_before_device(phx):
+    c = phx.phx_fno_config()
+    phx.lib().phx_fno_config_init(ctypes.byref(c))
+    c.modes_y = 3  # must be even
+    out = ctypes.c_void_p()
+    assert phx.lib().phx_fno_create(ctypes.byref(c), ctypes.byref(out)) == 1  # PHX_EINVAL
+    assert not out.value
