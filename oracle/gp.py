@@ -58,6 +58,7 @@ class Params:
     delta_lt: float = 0.0     # meV um^2
     dt: float = 0.0           # ps
     noise_var: float = 0.0    # E|xi|^2 added per site per step
+    wigner_nu: float = 0.0    # truncated-Wigner noise intensity nu (0: off)
     seed: int = 0
     instance: int = 0
 
@@ -153,8 +154,16 @@ def hamiltonian_apply(psi, n, V, p):
 
 def rhs(psi, n, P, V, p):
     """Time derivatives (f_psi, f_n) of Eqs. (PULSE_psi)/(PULSE_res), E = 0,
-    without dW.  f_n is None without a reservoir."""
+    without dW.  f_n is None without a reservoir.
+
+    Truncated-Wigner mode (Sec. V, Example 4; wigner_nu > 0): the equations
+    are solved for the renormalised density |psi|^2 - 1/dV (dV the cell
+    area) in the Kerr, cross-Kerr and reservoir-depletion terms."""
     h = hamiltonian_apply(psi, n, V, p)
+    w = 1.0 / (p.dx * p.dy) if p.wigner_nu > 0.0 else 0.0
+    if w:
+        gsum = p.g + (p.g_x if p.spinor else 0.0)
+        h = h - (gsum * w) * psi
     f_psi = -1j / HBAR * h
     for c in range(p.ncomp):
         gain = -0.5 * p.gamma_c
@@ -166,7 +175,7 @@ def rhs(psi, n, P, V, p):
         f_n = np.empty_like(n)
         dens = np.abs(psi) ** 2
         for c in range(p.ncomp):
-            f_n[c] = P[c] - (p.gamma_r + p.R * dens[c]) * n[c]
+            f_n[c] = P[c] - (p.gamma_r + p.R * (dens[c] - w)) * n[c]
     return f_psi, f_n
 
 
@@ -189,13 +198,36 @@ def rk4_step(psi, n, P, V, p):
     return psi_new, n_new
 
 
-def add_noise(psi, step, p, fp32_state=False):
+def wigner_scale(n_start, p):
+    """Per-site, per-quadrature standard deviation of the truncated-Wigner
+    increment, float32: E|xi_c|^2 = noise_var + nu (R n_c + gamma_c) dt / (2 dV)
+    (<dW dW*> = (R n + gamma_c) delta / (2 dV) per unit time, Sec. V,
+    Example 4; Ito: n_c at the start of the step), evaluated as
+    v = ((R n + gamma_c) kw) + noise_var with kw = nu dt / (2 dV), each
+    operation rounded to float32, then sqrt(max(v, 0) / 2)."""
+    F = np.float32
+    kw = F(p.wigner_nu * p.dt / (2.0 * p.dx * p.dy))
+    n32 = (np.zeros((p.ncomp, p.ny, p.nx)) if n_start is None else np.asarray(n_start)).astype(F)
+    a = (F(p.R) * n32).astype(F)
+    b = (a + F(p.gamma_c)).astype(F)
+    c = (b * kw).astype(F)
+    v = (c + F(p.noise_var)).astype(F)
+    v = np.maximum(v, F(0.0))
+    return np.sqrt((v * F(0.5)).astype(F)).astype(F)
+
+
+def add_noise(psi, step, p, fp32_state=False, n_start=None):
     """psi_c += xi_c(seed, step, instance, site) after the deterministic step
-    (reading: operator splitting with fixed variance per step)."""
-    if p.noise_var == 0.0:
+    (reading: operator splitting; fixed variance per step, or the
+    truncated-Wigner variance of wigner_scale)."""
+    if p.noise_var == 0.0 and p.wigner_nu == 0.0:
         return psi
-    re, im = _noise.noise_field(p.seed, step, p.instance, p.ncomp, p.ny, p.nx,
-                                p.noise_var)
+    if p.wigner_nu > 0.0:
+        re, im = _noise.noise_field_scaled(p.seed, step, p.instance, p.ncomp, p.ny, p.nx,
+                                           wigner_scale(n_start, p))
+    else:
+        re, im = _noise.noise_field(p.seed, step, p.instance, p.ncomp, p.ny, p.nx,
+                                    p.noise_var)
     if fp32_state:
         return (psi.real.astype(np.float32) + re) + 1j * (
             psi.imag.astype(np.float32) + im)
@@ -217,8 +249,9 @@ def run(psi, n, P, V, p, nsteps, step0=0):
         elif P.shape[0] != p.ncomp:
             P = np.broadcast_to(P, (p.ncomp, p.ny, p.nx))
     for k in range(nsteps):
+        n_start = n
         psi, n = rk4_step(psi, n, P, V, p)
-        psi = add_noise(psi, step0 + k, p)
+        psi = add_noise(psi, step0 + k, p, n_start=n_start)
     return psi, n
 
 
@@ -357,8 +390,15 @@ def step_at_sites(psi, n, P, V, p, sites_ji, step, radius=5):
         out_psi[:, k] = a[:, cj, ci]
         if p.reservoir:
             out_n[:, k] = b[:, cj, ci]
-    if p.noise_var != 0.0:
-        sites = np.array([j * p.nx + i for j, i in sites_ji])
+    sites = np.array([j * p.nx + i for j, i in sites_ji])
+    if p.wigner_nu > 0.0:
+        js = np.array([j for j, _ in sites_ji])
+        is_ = np.array([i for _, i in sites_ji])
+        n_s = n[:, js, is_] if p.reservoir else np.zeros((nc, len(sites_ji)))
+        re, im = _noise.noise_at_scaled(p.seed, step, p.instance, sites, nc,
+                                        wigner_scale(n_s, p.with_(nx=len(sites_ji), ny=1)))
+        out_psi = out_psi + (re.astype(np.float64) + 1j * im.astype(np.float64))
+    elif p.noise_var != 0.0:
         re, im = _noise.noise_at(p.seed, step, p.instance, sites, nc, p.noise_var)
         out_psi = out_psi + (re.astype(np.float64) + 1j * im.astype(np.float64))
     return out_psi, out_n

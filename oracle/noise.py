@@ -149,7 +149,7 @@ def box_muller_f32(wa, wb, scale):
     c, s = cos_sin_2pi_f32(u2)
     z1 = rho * c
     z2 = rho * s
-    sc = F32(scale)
+    sc = np.asarray(scale, F32)
     return (sc * z1).astype(F32), (sc * z2).astype(F32)
 
 
@@ -172,6 +172,40 @@ def noise_field(seed, step, instance, ncomp, ny, nx, var):
     re[0], im[0] = box_muller_f32(w0, w1, sc)
     if ncomp == 2:
         re[1], im[1] = box_muller_f32(w2, w3, sc)
+    return re, im
+
+
+def noise_field_scaled(seed, step, instance, ncomp, ny, nx, scale):
+    """As noise_field with a per-site, per-component float32 scale array of
+    shape (ncomp, ny, nx) (the per-quadrature standard deviation)."""
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    step = int(step) & 0xFFFFFFFFFFFFFFFF
+    site = np.arange(ny * nx, dtype=np.uint64).astype(U32).reshape(ny, nx)
+    w0, w1, w2, w3 = philox4x32_10(site, U32(instance), U32(step & 0xFFFFFFFF),
+                                   U32(step >> 32), seed & 0xFFFFFFFF, seed >> 32)
+    scale = np.asarray(scale, F32)
+    re = np.empty((ncomp, ny, nx), F32)
+    im = np.empty((ncomp, ny, nx), F32)
+    re[0], im[0] = box_muller_f32(w0, w1, scale[0])
+    if ncomp == 2:
+        re[1], im[1] = box_muller_f32(w2, w3, scale[1])
+    return re, im
+
+
+def noise_at_scaled(seed, step, instance, sites, ncomp, scale):
+    """As noise_at with a per-site, per-component float32 scale array of
+    shape (ncomp,) + sites.shape."""
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    step = int(step) & 0xFFFFFFFFFFFFFFFF
+    sites = np.asarray(sites).astype(np.uint64).astype(U32)
+    w0, w1, w2, w3 = philox4x32_10(sites, U32(instance), U32(step & 0xFFFFFFFF),
+                                   U32(step >> 32), seed & 0xFFFFFFFF, seed >> 32)
+    scale = np.asarray(scale, F32).reshape((ncomp,) + sites.shape)
+    re = np.empty((ncomp,) + sites.shape, F32)
+    im = np.empty((ncomp,) + sites.shape, F32)
+    re[0], im[0] = box_muller_f32(w0, w1, scale[0])
+    if ncomp == 2:
+        re[1], im[1] = box_muller_f32(w2, w3, scale[1])
     return re, im
 
 
