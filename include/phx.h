@@ -19,6 +19,11 @@
  *   Gaussian of E|xi|^2 = noise_var from Philox4x32-10 keyed by
  *   (seed, step, instance, site) (Salmon et al., SC'11), so runs and
  *   resumes are reproducible bit for bit.
+ *   Truncated-Wigner mode (Sec. V, Example 4; wigner_nu > 0): the variance
+ *   becomes E|xi_c|^2 = noise_var + nu (R n_c + gamma_c) dt / (2 dV) per
+ *   site, n_c taken at the start of the step and dV = dx dy, and the Kerr,
+ *   cross-Kerr and depletion terms use the renormalised density
+ *   |psi|^2 - 1/dV.  Norm, energy and residual stay the plain functionals.
  *
  * Conventions
  *   - Every call returns a phx_status; on error the handle's state is left
@@ -44,7 +49,7 @@
 extern "C" {
 #endif
 
-#define PHX_ABI_VERSION 1
+#define PHX_ABI_VERSION 2
 
 typedef enum phx_status {
   PHX_OK = 0,
@@ -86,6 +91,7 @@ typedef struct phx_params {
   double delta_lt;           /* TE-TM splitting Delta_LT, meV um^2 (spinor only) */
   double dt;                 /* RK4 step, ps; rejected above the stability limit */
   double noise_var;          /* E|xi|^2 added per site and step; 0 = off */
+  double wigner_nu;          /* truncated-Wigner noise intensity nu >= 0; 0 = off */
   uint64_t seed;             /* Philox key */
   uint32_t instance;         /* Philox counter word 1 (ensemble member id) */
   uint32_t reserved;

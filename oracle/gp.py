@@ -395,8 +395,9 @@ def step_at_sites(psi, n, P, V, p, sites_ji, step, radius=5):
         js = np.array([j for j, _ in sites_ji])
         is_ = np.array([i for _, i in sites_ji])
         n_s = n[:, js, is_] if p.reservoir else np.zeros((nc, len(sites_ji)))
+        row = p.with_(nx=len(sites_ji), ny=1, lx=len(sites_ji) * p.dx, ly=p.dy)  # same dV
         re, im = _noise.noise_at_scaled(p.seed, step, p.instance, sites, nc,
-                                        wigner_scale(n_s, p.with_(nx=len(sites_ji), ny=1)))
+                                        wigner_scale(n_s, row))
         out_psi = out_psi + (re.astype(np.float64) + 1j * im.astype(np.float64))
     elif p.noise_var != 0.0:
         re, im = _noise.noise_at(p.seed, step, p.instance, sites, nc, p.noise_var)

@@ -48,6 +48,7 @@ class phx_params(ctypes.Structure):
         ("delta_lt", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("noise_var", ctypes.c_double),
+        ("wigner_nu", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("instance", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
         ("stream", ctypes.c_void_p),
@@ -455,7 +456,7 @@ def phx_batch_destroy(b):
 
 PARAM_KEYS = ("nx", "ny", "lx", "ly", "bc_x", "bc_y", "spinor", "reservoir",
               "kappa", "g", "g_x", "g_r", "R", "gamma_c", "gamma_r", "delta_lt",
-              "dt", "noise_var", "seed", "instance")
+              "dt", "noise_var", "wigner_nu", "seed", "instance")
 
 
 def params_from_dict(d, precision=32, stream=None, tile=0):

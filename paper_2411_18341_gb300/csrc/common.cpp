@@ -75,12 +75,13 @@ const char* check_params(const phx_params* p, double* dtmax_out) {
   if ((p->spinor != 0 && p->spinor != 1) || (p->reservoir != 0 && p->reservoir != 1))
     return "spinor and reservoir must be 0 or 1";
   const double c[] = {p->hbar2_over_2m, p->g, p->g_x, p->g_r, p->R, p->gamma_c,
-                      p->gamma_r, p->delta_lt, p->dt, p->noise_var};
+                      p->gamma_r, p->delta_lt, p->dt, p->noise_var, p->wigner_nu};
   for (double v : c)
     if (!std::isfinite(v)) return "coefficients must be finite";
   if (p->hbar2_over_2m < 0) return "hbar2_over_2m must be >= 0";
   if (!p->spinor && (p->g_x != 0.0 || p->delta_lt != 0.0)) return "g_x and delta_lt need spinor = 1";
   if (p->noise_var < 0) return "noise_var must be >= 0";
+  if (p->wigner_nu < 0) return "wigner_nu must be >= 0";
   double lam = spectral_radius(*p);
   double dtmax = lam > 0 ? 2.0 * std::sqrt(2.0) * HBAR / lam : INFINITY;
   if (dtmax_out) *dtmax_out = dtmax;
@@ -106,7 +107,29 @@ Coeffs make_coeffs(const phx_params& p) {
   k.ty = p.delta_lt / (HBAR * dy * dy);
   k.txy = p.delta_lt / (2.0 * HBAR * dx * dy);
   k.dt = p.dt;
+  if (p.wigner_nu > 0.0) {
+    // truncated-Wigner renormalisation |psi|^2 -> |psi|^2 - 1/dV in the Kerr,
+    // cross-Kerr and depletion terms: constant shifts of the diagonal
+    const double w = 1.0 / (dx * dy);
+    k.a0 -= (p.g + (p.spinor ? p.g_x : 0.0)) * w / HBAR;
+    k.gamma_r -= p.R * w;
+  }
   return k;
+}
+
+NoiseKey make_noise_key(const phx_params& p) {
+  NoiseKey z;
+  z.seed = p.seed;
+  z.instance = p.instance;
+  z.on = p.noise_var > 0.0 || p.wigner_nu > 0.0;
+  z.scale = (float)std::sqrt(p.noise_var / 2.0);
+  z.twa = p.wigner_nu > 0.0;
+  const double dx = p.lx / p.nx, dy = p.ly / p.ny;
+  z.kw = (float)(p.wigner_nu * p.dt / (2.0 * dx * dy));
+  z.R = (float)p.R;
+  z.gc = (float)p.gamma_c;
+  z.var = (float)p.noise_var;
+  return z;
 }
 
 Geometry padded_geometry(const phx_params& p) {
@@ -206,10 +229,7 @@ bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* c
     return false;
   I.geo = g;
   I.k = cast_coeffs<float>(make_coeffs(p));
-  I.noise.seed = p.seed;
-  I.noise.instance = p.instance;
-  I.noise.on = p.noise_var > 0.0;
-  I.noise.scale = (float)std::sqrt(p.noise_var / 2.0);
+  I.noise = make_noise_key(p);
   I.dt64 = p.dt;
   I.tiles_x = (g.nx + 1 + b.tx - 1) / b.tx;
   I.tiles_y = (g.ny + b.ty - 1) / b.ty;

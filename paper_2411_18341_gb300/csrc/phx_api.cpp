@@ -469,11 +469,7 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, PHX_EINVAL, "nsteps must be >= 0");
   DeviceGuard dg(h->device);
   const Coeffs k = make_coeffs(h->p);
-  NoiseKey nz;
-  nz.seed = h->p.seed;
-  nz.instance = h->p.instance;
-  nz.on = h->p.noise_var > 0.0;
-  nz.scale = (float)std::sqrt(h->p.noise_var / 2.0);
+  const NoiseKey nz = make_noise_key(h->p);
   for (int64_t s = 0; s < nsteps; ++s) {
     cudaError_t e;
     if (take_injection(INJ_LAUNCH))

@@ -69,8 +69,11 @@ inline CoeffsT<R> cast_coeffs(const Coeffs& c) {
 struct NoiseKey {
   unsigned long long seed;
   unsigned int instance;
-  int on;
-  float scale;            // float32(sqrt(var/2))
+  int on;                 // noise_var > 0 or wigner_nu > 0
+  float scale;            // float32(sqrt(noise_var/2)), the fixed-variance mode
+  int twa;                // truncated-Wigner variance per site (nu > 0)
+  float kw;               // float32(nu dt / (2 dx dy))
+  float R, gc, var;       // float32 R, gamma_c, noise_var
 };
 
 template <typename R>
@@ -147,6 +150,7 @@ bool take_injection(unsigned what);
 const char* check_params(const phx_params* p, double* dtmax);
 double spectral_radius(const phx_params& p);
 Coeffs make_coeffs(const phx_params& p);
+NoiseKey make_noise_key(const phx_params& p);
 Geometry padded_geometry(const phx_params& p);
 cudaError_t upload_field(void* dst, const void* src, int nplanes, size_t elem,
                          const Geometry& g, int on_device, cudaStream_t s);

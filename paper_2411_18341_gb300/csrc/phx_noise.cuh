@@ -132,12 +132,13 @@ __device__ __forceinline__ float2 nz_box_muller(uint32_t wa, uint32_t wb,
   return make_float2(__fmul_rn(scale, z1), __fmul_rn(scale, z2));
 }
 
-// Noise of site `site` at step `step`: xi_+ (and xi_- for spinors).
-__device__ __forceinline__ void nz_site(unsigned long long seed,
-                                        unsigned int instance,
-                                        long long step, uint32_t site,
-                                        float scale, float2& xi0, float2& xi1,
-                                        bool two) {
+// Noise of site `site` at step `step`: xi_+ (and xi_- for spinors), each
+// component with its own per-quadrature standard deviation.
+__device__ __forceinline__ void nz_site2(unsigned long long seed,
+                                         unsigned int instance,
+                                         long long step, uint32_t site,
+                                         float scale0, float scale1,
+                                         float2& xi0, float2& xi1, bool two) {
   U4 c;
   c.x = site;
   c.y = instance;
@@ -145,8 +146,27 @@ __device__ __forceinline__ void nz_site(unsigned long long seed,
   c.w = (uint32_t)((unsigned long long)step >> 32);
   U4 w = philox4x32_10(c, (uint32_t)(seed & 0xFFFFFFFFull),
                        (uint32_t)(seed >> 32));
-  xi0 = nz_box_muller(w.x, w.y, scale);
-  if (two) xi1 = nz_box_muller(w.z, w.w, scale);
+  xi0 = nz_box_muller(w.x, w.y, scale0);
+  if (two) xi1 = nz_box_muller(w.z, w.w, scale1);
+}
+
+__device__ __forceinline__ void nz_site(unsigned long long seed,
+                                        unsigned int instance,
+                                        long long step, uint32_t site,
+                                        float scale, float2& xi0, float2& xi1,
+                                        bool two) {
+  nz_site2(seed, instance, step, site, scale, scale, xi0, xi1, two);
+}
+
+// Truncated-Wigner per-quadrature standard deviation (Sec. V, Example 4):
+// E|xi|^2 = nu (R n + gamma_c) dt / (2 dV) + noise_var, evaluated in float32
+// as v = ((R n + gamma_c) kw) + var with kw = nu dt / (2 dV), each operation
+// separately rounded, then sqrt(max(v, 0) / 2).
+__device__ __forceinline__ float nz_wigner_scale(float R, float gc, float kw,
+                                                 float var, float n) {
+  float v = __fadd_rn(__fmul_rn(__fadd_rn(__fmul_rn(R, n), gc), kw), var);
+  v = fmaxf(v, 0.0f);
+  return __fsqrt_rn(__fmul_rn(v, 0.5f));
 }
 
 #endif  // __CUDACC__

@@ -248,9 +248,17 @@ rk4_step_generic(const StepArgs<R> a) {
       int ry = idx / RXN, rx = idx - ry * RXN;
       int gx = x0 - 3 + rx, gy = y0 - 3 + ry;
       xi[k][0] = xi[k][1] = make_float2(0.f, 0.f);
-      if (valid[k] && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny)
-        nz_site(a.noise.seed, a.noise.instance, step, (uint32_t)(gy * g.nx + gx),
-                a.noise.scale, xi[k][0], xi[k][1], NC == 2);
+      if (valid[k] && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) {
+        float s0 = a.noise.scale, s1 = a.noise.scale;
+        if (a.noise.twa) {  // variance from the reservoir at the step's start
+          const NoiseKey& z = a.noise;
+          s0 = nz_wigner_scale(z.R, z.gc, z.kw, z.var, RES ? (float)n0[k][0] : 0.f);
+          if (NC == 2)
+            s1 = nz_wigner_scale(z.R, z.gc, z.kw, z.var, RES ? (float)n0[k][NC - 1] : 0.f);
+        }
+        nz_site2(a.noise.seed, a.noise.instance, step, (uint32_t)(gy * g.nx + gx),
+                 s0, s1, xi[k][0], xi[k][1], NC == 2);
+      }
     }
   }
 #pragma unroll

@@ -402,7 +402,9 @@ rk4_f32_tma(const TileArgs ta) {
           const uint32_t site = (uint32_t)(((gy % g.ny + g.ny) % g.ny) * g.nx +
                                            (gx % g.nx + g.nx) % g.nx);
           float2 xi, unused;
-          nz_site(nz.seed, nz.instance, step, site, nz.scale, xi, unused, false);
+          const float sc = nz.twa ? nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var, n0[j][i])
+                                  : nz.scale;
+          nz_site(nz.seed, nz.instance, step, site, sc, xi, unused, false);
           o[j][i].x = o[j][i].x + xi.x;
           o[j][i].y = o[j][i].y + xi.y;
         }

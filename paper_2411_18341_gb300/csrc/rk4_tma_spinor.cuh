@@ -335,7 +335,12 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
           const uint32_t site = (uint32_t)(((gy % g.ny + g.ny) % g.ny) * g.nx +
                                            (gx % g.nx + g.nx) % g.nx);
           float2 xp_, xm_;
-          nz_site(nz.seed, nz.instance, step, site, nz.scale, xp_, xm_, true);
+          float s0 = nz.scale, s1 = nz.scale;
+          if (nz.twa) {
+            s0 = nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var, n0[j][i][0]);
+            s1 = nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var, n0[j][i][1]);
+          }
+          nz_site2(nz.seed, nz.instance, step, site, s0, s1, xp_, xm_, true);
           o[j][i][0].x = o[j][i][0].x + xp_.x;
           o[j][i][0].y = o[j][i][0].y + xp_.y;
           o[j][i][1].x = o[j][i][1].x + xm_.x;

@@ -74,6 +74,7 @@ def test_stability_dt_matches_oracle(phx, case):
 def test_invalid_params_rejected_before_device(phx):
     bad = [dict(nx=0), dict(ny=-3), dict(lx=0.0), dict(bc_x=2), dict(precision=16),
            dict(g_x=0.1), dict(delta_lt=0.1), dict(noise_var=-1.0),
+           dict(wigner_nu=-0.5), dict(wigner_nu=float("inf")),
            dict(dt=0.0), dict(dt=1.0), dict(g=float("nan")), dict(spinor=2)]
     for kw in bad:
         base = dict(nx=16, ny=16, lx=4.0, ly=4.0, dt=1e-3)

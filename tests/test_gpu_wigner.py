@@ -1,0 +1,152 @@
+"""Truncated-Wigner mode (Sec. V, Example 4) through the C ABI against the
+oracle: the per-site noise variance nu (R n + gamma_c) dt / (2 dV) is
+reproduced bit for bit (kappa = 0 from psi = 0, so the step returns exactly
+the increment), and multi-step runs with the renormalised density match at
+the FP64 (1e-11) and FP32 (1e-4) tolerances on every kernel family: the
+generic kernels (FP64; FP32 tile 9), the TMA-fed scalar kernel and the
+TMA-fed two-component kernel, single handles and batches.
+
+A multi-step FP64 run can differ from the oracle by more than 1e-11 only if
+float32(n) rounds differently on the two sides at some site and step (the
+variance is taken from float32 n, and the two n agree to ~1e-15); on these
+inputs that does not happen."""
+import numpy as np
+import pytest
+
+from oracle import gp, noise
+import synth
+from gpu_util import phx, make_handle, get_state, rel_l2, rounded, TOL
+
+pytestmark = pytest.mark.gpu
+
+
+def twa_model(kind, nx, ny, bc=(0, 0), nu=1.0, noise_var=0.0, L=None):
+    L = L or (0.3 * nx, 0.3 * ny)
+    d = synth.base_params(nx, ny, L[0], L[1], bc_x=bc[0], bc_y=bc[1])
+    if kind == "loss":
+        d.update(g=0.3, gamma_c=0.2)
+    elif kind == "reservoir":
+        d.update(synth.reservoir_physics())
+        d.update(g=0.3, g_r=0.5, R=0.3, gamma_r=4.0)
+    elif kind == "spinor_res_tetm":
+        d.update(synth.reservoir_physics())
+        d.update(spinor=True, g=0.3, g_x=0.1, g_r=0.4, R=0.3, gamma_r=4.0, delta_lt=0.2)
+    d.update(wigner_nu=nu, noise_var=noise_var, seed=23, instance=3)
+    d["dt"] = min(0.45 * gp.stability_dt_max(gp.Params(**d)), 0.05)
+    return d
+
+
+def make(d, prec, tile, psi0, n0, P, V=None):
+    m = phx()
+    real, cplx = (np.float64, np.complex128) if prec == 64 else (np.float32, np.complex64)
+    h = m.phx_create(m.params_from_dict(d, precision=prec, tile=tile))
+    if d.get("reservoir"):
+        m.phx_set_pump(h, *[np.ascontiguousarray(P[c], real) for c in range(P.shape[0])])
+    if V is not None:
+        m.phx_set_potential(h, np.ascontiguousarray(V, real))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, cplx),
+                    None if n0 is None else np.ascontiguousarray(n0, real))
+    return h
+
+
+# (precision, kind, tile): generic FP64; FP32 TMA scalar (auto, fixed 3, 6),
+# FP32 generic scalar (9); FP32 TMA two-component (22) and generic (9)
+CASES = [(64, "reservoir", 0), (64, "loss", 0), (64, "spinor_res_tetm", 0),
+         (32, "reservoir", 0), (32, "reservoir", 3), (32, "reservoir", 6),
+         (32, "reservoir", 9), (32, "loss", 0), (32, "loss", 9),
+         (32, "spinor_res_tetm", 22), (32, "spinor_res_tetm", 9)]
+
+
+@pytest.mark.parametrize("prec,kind,tile", CASES)
+def test_wigner_increment_bit_exact(prec, kind, tile):
+    """kappa = 0 and psi = 0: every deterministic term vanishes, so one step
+    returns the increment whose variance follows the reservoir at the start
+    of the step -- equal bit for bit to the oracle's."""
+    nx, ny = 83, 41
+    d = twa_model(kind, nx, ny, nu=1.7, noise_var=2e-4)
+    d["kappa"] = 0.0
+    nc = 2 if d["spinor"] else 1
+    rng = np.random.default_rng(5)
+    n0 = rng.uniform(0.0, 4.0, (nc, ny, nx)).astype(np.float32).astype(np.float64) \
+        if d["reservoir"] else None
+    P = np.zeros((nc, ny, nx)) if d["reservoir"] else None
+    h = make(d, prec, tile, np.zeros((nc, ny, nx)), n0, P)
+    phx().phx_set_time(h, 1234567, 0.0)
+    phx().phx_step_n(h, 1)
+    g, _ = get_state(h, prec)
+    p = gp.Params(**d)
+    sc = gp.wigner_scale(n0, p)
+    re, im = noise.noise_field_scaled(23, 1234567, 3, nc, ny, nx, sc)
+    assert np.array_equal(g.real.astype(np.float32), re)
+    assert np.array_equal(g.imag.astype(np.float32), im)
+    if prec == 64:
+        assert np.array_equal(g.real, re.astype(np.float64))
+        assert np.array_equal(g.imag, im.astype(np.float64))
+
+
+@pytest.mark.parametrize("prec,kind,tile", CASES)
+@pytest.mark.parametrize("bc", [(0, 0), (1, 0)])
+def test_wigner_run_parity(prec, kind, tile, bc):
+    """Nine steps of the full stochastic equations with the renormalised
+    density, a potential and ragged grids spanning several tiles."""
+    nx, ny = 131, 77
+    d = twa_model(kind, nx, ny, bc=bc, nu=0.8)
+    nc = 2 if d["spinor"] else 1
+    psi0, n0, P, V = synth.random_state(nc, ny, nx, 4, amp=0.7,
+                                        reservoir=d["reservoir"], smooth=True)
+    if not d["reservoir"]:
+        n0 = P = None
+    psi0, n0, P, V = (rounded(x, prec) for x in (psi0, n0, P, V))
+    h = make(d, prec, tile, psi0, n0, P, V)
+    phx().phx_set_time(h, 50, 0.0)
+    phx().phx_step_n(h, 9)
+    g_psi, g_n = get_state(h, prec)
+    o_psi, o_n = gp.run(psi0, n0, P, V, gp.Params(**d), 9, step0=50)
+    assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
+    if d["reservoir"]:
+        assert rel_l2(g_n, o_n) <= TOL[prec], rel_l2(g_n, o_n)
+    if prec == 32 and tile in (3, 6, 22):
+        assert phx().phx_tile(h) == tile
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_wigner_off_matches_plain_handle(prec):
+    """wigner_nu = 0 is the plain equation: identical bits to a handle whose
+    parameters never mention the mode."""
+    d = twa_model("reservoir", 70, 45, nu=0.0, noise_var=1e-4)
+    psi0, n0, P, V = synth.random_state(1, 45, 70, 2, amp=0.7, smooth=True)
+    psi0, n0, P = (rounded(x, prec) for x in (psi0, n0, P))
+    a = make(d, prec, 0, psi0, n0, P)
+    d2 = {k: v for k, v in d.items() if k != "wigner_nu"}
+    b = make(d2, prec, 0, psi0, n0, P)
+    phx().phx_step_n(a, 5)
+    phx().phx_step_n(b, 5)
+    ga, na = get_state(a, prec)
+    gb, nb = get_state(b, prec)
+    assert np.array_equal(ga, gb) and np.array_equal(na, nb)
+
+
+def test_wigner_batch_members_match_oracle():
+    """Batched FP32 scalar members, each with its own nu, grid and reservoir,
+    through the persistent batch launch."""
+    m = phx()
+    ms = []
+    for k, (nx, ny, nu) in enumerate([(40, 33, 0.5), (96, 70, 1.0), (130, 57, 0.0),
+                                      (64, 130, 2.0)]):
+        d = twa_model("reservoir", nx, ny, nu=nu, noise_var=1e-5 * k)
+        d.update(seed=60 + k, instance=k)
+        psi0, n0, P, _ = synth.random_state(1, ny, nx, 60 + k, amp=0.6, smooth=True)
+        ms.append((d, rounded(psi0, 32), rounded(n0, 32), rounded(P, 32)))
+    b = m.phx_batch_create([m.params_from_dict(d, precision=32) for d, *_ in ms])
+    for i, (d, psi0, n0, P) in enumerate(ms):
+        m.phx_batch_set_pump(b, i, np.ascontiguousarray(P[0], np.float32))
+        m.phx_batch_set_state(b, i, np.ascontiguousarray(psi0, np.complex64),
+                              np.ascontiguousarray(n0, np.float32))
+    m.phx_batch_step_n(b, 11)
+    for i, (d, psi0, n0, P) in enumerate(ms):
+        psi = np.empty((1, d["ny"], d["nx"]), np.complex64)
+        n = np.empty((1, d["ny"], d["nx"]), np.float32)
+        m.phx_batch_get_state(b, i, psi, n)
+        o_psi, o_n = gp.run(psi0, n0, P, None, gp.Params(**d), 11)
+        assert rel_l2(psi, o_psi) <= 1e-4, (i, rel_l2(psi, o_psi))
+        assert rel_l2(n, o_n) <= 1e-4, (i, rel_l2(n, o_n))

@@ -432,13 +432,15 @@ def test_derived_constants_file_matches_oracle():
     assert c["pump_threshold"] == pytest.approx(0.15 * 0.225 / 0.01)
 
 
-@pytest.mark.parametrize("bc", [gp.PERIODIC, gp.ZERO])
-def test_windowed_step_equals_full_grid_step(bc):
+@pytest.mark.parametrize("bc,nu", [(gp.PERIODIC, 0.0), (gp.ZERO, 0.0), (gp.PERIODIC, 1.5)])
+def test_windowed_step_equals_full_grid_step(bc, nu):
     """oracle.gp.step_at_sites (used for sampled parity at full size) equals
-    the full-grid step at every sampled site, including edges and corners."""
+    the full-grid step at every sampled site, including edges and corners,
+    also in truncated-Wigner mode (renormalised density, per-site variance)."""
     p = gp.Params(nx=23, ny=19, lx=7.0, ly=6.0, bc_x=bc, bc_y=gp.PERIODIC,
                   spinor=True, reservoir=True, g=0.2, g_x=0.05, g_r=0.1, R=0.05,
-                  gamma_c=0.1, gamma_r=0.2, delta_lt=0.07, noise_var=1e-3, seed=4)
+                  gamma_c=0.1, gamma_r=0.2, delta_lt=0.07, noise_var=1e-3, seed=4,
+                  wigner_nu=nu)
     p = p.with_(dt=0.4 * gp.stability_dt_max(p))
     psi, n, P, V = synth.random_state(2, 19, 23, 9)
     full_psi, full_n = gp.run(psi, n, P, V, p, 1, step0=3)
