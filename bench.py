@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--impl", default="phx", choices=["phx", "reference"])
     ap.add_argument("--workload", default="reservoir_1024",
                     choices=["reservoir_1024", "reservoir", "spinor_2048", "conservative_64",
-                             "ensemble"])
+                             "ensemble", "twa_ensemble"])
     ap.add_argument("--grid", type=int, default=1024,
                     help="grid size of the 'reservoir' workload (100 um box, config-2 physics)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -265,6 +265,10 @@ def run_reference(args, world, rank):
     if args.workload == "ensemble":
         cfg, kind, desc = workload("reservoir", grid=128)
         desc = "one 128x128 member of the ensemble workload"
+    elif args.workload == "twa_ensemble":
+        import synth
+        cfg = synth.twa_ensemble(count=1)[0]
+        desc = "one 256x256 realisation of the truncated-Wigner ensemble"
     else:
         cfg, kind, desc = workload(args.workload, grid=args.grid)
     from oracle import gp
@@ -295,11 +299,21 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+TWA_SAMPLE_PS = 5.0   # sampling interval of the truncated-Wigner ensemble
+TWA_SAMPLES = 10      # samples per bench step
+
+
 def run_ensemble(args, world, rank, local, pg):
-    """Ensemble workload: 256 independent reservoir instances on uneven grids
-    (64 each at 128^2, 256^2, 512^2, 1024^2; pumps U[0.8, 3] P_thr, distinct
-    seeds) advanced together, one persistent launch per RK4 step, replayed
-    from a CUDA graph; per-member FP64 norm/energy and residual."""
+    """Batched workloads, one persistent launch per RK4 step for all members,
+    replayed from a CUDA graph.
+
+    ensemble: 256 independent reservoir instances on uneven grids (64 each
+    at 128^2, 256^2, 512^2, 1024^2; pumps U[0.8, 3] P_thr, distinct seeds);
+    per step 500 RK4 steps, then per-member FP64 norm/energy and residual.
+    twa_ensemble: 150 truncated-Wigner realisations (256^2, 200 um,
+    super-Gaussian pump w = 65 um at 2 P_thr, nu = 1, Wigner vacuum start);
+    per step 10 samples, each 5 ps of RK4 steps followed by the per-member
+    FP64 norm/energy read back to the host (the sampled observable)."""
     import torch
     import synth
     import paper_2411_18341_gb300 as phx
@@ -307,8 +321,17 @@ def run_ensemble(args, world, rank, local, pg):
     _build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    members = synth.ensemble(seed0=1000 + 10000 * rank)
-    rk4_steps = args.rk4_steps or 500
+    twa = args.workload == "twa_ensemble"
+    if twa:
+        members = synth.twa_ensemble(seed=7 + rank)
+        dt = members[0]["params"]["dt"]
+        per_sample = args.rk4_steps or int(round(TWA_SAMPLE_PS / dt))
+        samples = TWA_SAMPLES
+    else:
+        members = synth.ensemble(seed0=1000 + 10000 * rank)
+        per_sample = args.rk4_steps or 500
+        samples = 1
+    rk4_steps = per_sample * samples
     stream = torch.cuda.Stream(device=dev)
     b = phx.phx_batch_create([phx.params_from_dict(m["params"], precision=32,
                                                    stream=stream.cuda_stream) for m in members])
@@ -323,6 +346,16 @@ def run_ensemble(args, world, rank, local, pg):
     def one_step(k0=None, k1=None):
         for i in range(len(members)):
             phx.phx_batch_set_state(b, i, psi_d[i], n_d[i])
+        if twa:
+            # kernel time = the first sample's RK4 steps (no host sync inside)
+            for k in range(samples):
+                if k == 0 and k0 is not None:
+                    k0.record(stream)
+                phx.phx_batch_step_n(b, per_sample)
+                if k == 0 and k1 is not None:
+                    k1.record(stream)
+                phx.phx_batch_norm_energy(b)
+            return
         if k0 is not None:
             k0.record(stream)
         phx.phx_batch_step_n(b, rk4_steps)
@@ -353,7 +386,8 @@ def run_ensemble(args, world, rank, local, pg):
     clk = clocks.stop() if clocks else None
     ms, value = aggregate(pg, world, sites * rk4_steps,
                           float(np.mean([x[0].elapsed_time(x[1]) for x in ev])))
-    kern_s = float(np.mean([x[2].elapsed_time(x[3]) for x in ev])) * 1e-3 / rk4_steps
+    kern_steps = per_sample if twa else rk4_steps
+    kern_s = float(np.mean([x[2].elapsed_time(x[3]) for x in ev])) * 1e-3 / kern_steps
 
     # end to end: pinned host inputs in, every member's state out
     psi_h = [t.cpu().pin_memory() for t in psi_d]
@@ -367,33 +401,47 @@ def run_ensemble(args, world, rank, local, pg):
     for i in range(len(members)):
         phx.phx_batch_set_pump(b, i, P_h[i])
         phx.phx_batch_set_state(b, i, psi_h[i], n_h[i])
-    phx.phx_batch_step_n(b, rk4_steps)
-    phx.phx_batch_norm_energy(b)
-    phx.phx_batch_residual(b)
+    if twa:
+        for k in range(samples):
+            phx.phx_batch_step_n(b, per_sample)
+            phx.phx_batch_norm_energy(b)
+    else:
+        phx.phx_batch_step_n(b, rk4_steps)
+        phx.phx_batch_norm_energy(b)
+        phx.phx_batch_residual(b)
     for i in range(len(members)):
         phx.phx_batch_get_state(b, i, out_psi[i], out_n[i])
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
     pk, pk_kind = peaks()
     achieved = 28 * sites / kern_s / 1e9
+    if twa:
+        desc = ("150 truncated-Wigner realisations (nu = 1), 256^2, 200 um periodic, "
+                "super-Gaussian pump w = 65 um at 2 P_thr, Wigner vacuum start")
+        per_step = ("set_state x150 + %d samples, each %d batched RK4 steps (%.2f ps) + "
+                    "per-member FP64 norm/energy to the host" % (samples, per_sample,
+                                                                 per_sample * dt))
+    else:
+        desc = ("256 reservoir instances, 64 each at 128^2/256^2/512^2/1024^2, "
+                "100 um, ring pumps U[0.8,3] P_thr, distinct seeds")
+        per_step = ("set_state x256 + %d batched RK4 steps + per-member FP64 "
+                    "norm/energy + residual" % rk4_steps)
     line = {
         "metric": "RK4 site-updates/s", "value": value, "unit": "site-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "ensemble",
-                   "description": "256 reservoir instances, 64 each at 128^2/256^2/512^2/1024^2, "
-                                  "100 um, ring pumps U[0.8,3] P_thr, distinct seeds",
+        "config": {"workload": args.workload, "description": desc,
                    "sites": sites, "rk4_steps_per_step": rk4_steps, "tile": phx.phx_batch_tile(b),
-                   "per_step": "set_state x256 + %d batched RK4 steps + per-member FP64 "
-                               "norm/energy + residual" % rk4_steps,
-                   "l2": "inputs (%.1f GB) larger than L2" % (28 * sites / 1e9),
+                   "per_step": per_step,
+                   "l2": "inputs (%.2f GB) larger than L2" % (28 * sites / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": world * sites * rk4_steps / e2e_s, "unit": "site-updates/s",
                 "h2d_bytes_per_step": sites * 16, "d2h_bytes_per_step": sites * 12},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": recorded_traffic("ensemble", 32),
+                     "frac": achieved / pk["hbm_gbs"],
+                     "traffic": recorded_traffic(args.workload, 32),
                      "kernel": "rk4_f32_tma (persistent, all members per launch)",
                      "algorithmic_bytes_per_site": 28, "avg_launch_us": kern_s * 1e6,
                      "peak_source": pk_kind},
@@ -401,8 +449,12 @@ def run_ensemble(args, world, rank, local, pg):
         "energy": energy(clk, ms * 1e-3, sites * rk4_steps),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cfg, _, _ = workload("reservoir", grid=128)
-        line["cpu_baseline"] = cpu_baseline("ensemble (one 128x128 member)", cfg)
+        if twa:
+            line["cpu_baseline"] = cpu_baseline("twa_ensemble (one 256x256 member)",
+                                                members[0])
+        else:
+            cfg, _, _ = workload("reservoir", grid=128)
+            line["cpu_baseline"] = cpu_baseline("ensemble (one 128x128 member)", cfg)
     phx.phx_batch_destroy(b)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -424,7 +476,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    if args.workload == "ensemble":
+    if args.workload in ("ensemble", "twa_ensemble"):
         run_ensemble(args, world, rank, local, pg)
         if pg is not None:
             pg.destroy_process_group()

@@ -159,6 +159,37 @@ def ensemble(count_per_size=64, sizes=(128, 256, 512, 1024), seed0=1000):
     return out
 
 
+def super_gaussian(nx, ny, lx, ly, amp, w):
+    """amp * exp(-(r/w)^4): the flat-top pump of the truncated-Wigner example,
+    with the printed exponent r^4/w_p^2 read as (r^2/w_p^2)^2 so that w_p is
+    the width in um."""
+    X, Y = mesh(nx, ny, lx, ly)
+    r2 = (X ** 2 + Y ** 2) / w ** 2
+    return amp * np.exp(-r2 * r2)
+
+
+def twa_ensemble(count=150, n=256, length=200.0, pump_factor=2.0, nu=1.0, seed=7,
+                 width=65.0):
+    """Truncated-Wigner Monte-Carlo ensemble: `count` realisations of one
+    scalar reservoir problem (super-Gaussian pump of width 65 um at
+    pump_factor P_thr, noise intensity nu), one Philox seed, member i drawing
+    counter word `instance` = i.  Each starts from the Wigner vacuum:
+    complex normal psi with E|psi|^2 = 1/(2 dV) per site, n = 0."""
+    c = load_constants()
+    pthr = c["pump_threshold"]
+    dt = c["twa_%d_L%g" % (n, length)]["dt"]
+    P = super_gaussian(n, n, length, length, pump_factor * pthr, width)[None]
+    dv = (length / n) ** 2
+    out = []
+    for i in range(count):
+        p = base_params(n, n, length, length, dt=dt, wigner_nu=nu, seed=seed,
+                        instance=i, **reservoir_physics())
+        psi0 = complex_normal((1, n, n), 0.5 / np.sqrt(dv), seed * 100003 + i)
+        out.append(dict(name="twa_%d" % i, params=p, psi0=psi0,
+                        n0=np.zeros((1, n, n)), P=P, V=None, steps=None))
+    return out
+
+
 def random_gaussian_pumps(n=256, length=128.0, count=1, seed=5000):
     """count pump images, each a sum of 1-4 Gaussians exp(-|r-c|^2/w^2) with
     w ~ U[3, 15] um, peak ~ U[1, 3] P_thr, centres within L/2 - 2w."""

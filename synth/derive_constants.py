@@ -40,6 +40,8 @@ def main():
     # the k ~ 0 condensate.  The stationary state does not depend on dt.
     dmax = 2 * half_limit(nx=256, ny=256, lx=128.0, ly=128.0, **res)
     out["steady_256_L128"] = {"dt": 0.85 * dmax, "dt_max": dmax}
+    # truncated-Wigner ensemble: 256^2 over 200 um, half the limit
+    out["twa_256_L200"] = {"dt": half_limit(nx=256, ny=256, lx=200.0, ly=200.0, **res)}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
                         "constants.json")
     with open(path, "w") as f:

@@ -150,3 +150,56 @@ def test_wigner_batch_members_match_oracle():
         o_psi, o_n = gp.run(psi0, n0, P, None, gp.Params(**d), 11)
         assert rel_l2(psi, o_psi) <= 1e-4, (i, rel_l2(psi, o_psi))
         assert rel_l2(n, o_n) <= 1e-4, (i, rel_l2(n, o_n))
+
+
+def rk4_poly(z):
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+def test_vacuum_ensemble_stationary_density():
+    """Statistics of the batched truncated-Wigner path against a closed form.
+
+    Linear dynamics (g = 0, no reservoir, loss gamma_c, periodic): in the
+    unitary DFT basis each Fourier mode obeys psi_k' = A_k psi_k + xi_k with
+    A_k the RK4 polynomial at z_k = (-i eps_k / hbar - gamma_c/2) dt,
+    eps_k = kappa (K_x^2 + K_y^2), K^2 = 4 sin^2(k d/2)/d^2 (5-point stencil),
+    and E|xi_k|^2 = sigma^2 = nu gamma_c dt / (2 dV).  The stationary mean
+    density is (1/N) sum_k sigma^2 / (1 - |A_k|^2), which tends to the
+    vacuum's 1/(2 dV) as dt -> 0.  96 members on three uneven grids; the mean
+    over members and 20 samples has a statistical error near 2e-4."""
+    m = phx()
+    hbar = gp.HBAR
+    ms = []
+    for k in range(96):
+        nx, ny = [(128, 128), (160, 96), (200, 120)][k % 3]
+        d = synth.base_params(nx, ny, 0.78 * nx, 0.78 * ny, gamma_c=0.5, wigner_nu=1.0,
+                              seed=31, instance=k)
+        d["dt"] = 0.45 * gp.stability_dt_max(gp.Params(**d))
+        ms.append(d)
+    b = m.phx_batch_create([m.params_from_dict(d, precision=32) for d in ms])
+    for i, d in enumerate(ms):
+        m.phx_batch_set_state(b, i, np.zeros((1, d["ny"], d["nx"]), np.complex64), None)
+    exact = []
+    for d in ms:
+        dx, dy = d["lx"] / d["nx"], d["ly"] / d["ny"]
+        kx = 2 * np.pi * np.fft.fftfreq(d["nx"], dx)
+        ky = 2 * np.pi * np.fft.fftfreq(d["ny"], dy)
+        K2 = (4 * np.sin(kx[None, :] * dx / 2) ** 2 / dx ** 2
+              + 4 * np.sin(ky[:, None] * dy / 2) ** 2 / dy ** 2)
+        A = rk4_poly((-1j * d["kappa"] * K2 / hbar - 0.5 * d["gamma_c"]) * d["dt"])
+        sigma2 = d["wigner_nu"] * d["gamma_c"] * d["dt"] / (2 * dx * dy)
+        exact.append(float(np.mean(sigma2 / (1 - np.abs(A) ** 2))))
+    m.phx_batch_step_n(b, 300)  # relaxation: slowest variance decay exp(-gamma t) < 1e-6
+    acc = np.zeros(len(ms))
+    for _ in range(20):
+        m.phx_batch_step_n(b, 10)
+        N, _E = m.phx_batch_norm_energy(b)
+        acc += N
+    dens = [acc[i] / 20 / (d["lx"] * d["ly"]) for i, d in enumerate(ms)]
+    ratio = np.array(dens) / np.array(exact)
+    assert abs(ratio.mean() - 1) < 5e-3, (ratio.mean(), ratio.std())
+    # the closed form sits 5 % below the continuum vacuum 1/(2 dV) at this dt
+    # (RK4's extra damping of the fast lattice modes)
+    dv = [(d["lx"] / d["nx"]) * (d["ly"] / d["ny"]) for d in ms]
+    assert all(0.9 < e * 2 * v < 1.0 for e, v in zip(exact, dv))
+    m.phx_batch_destroy(b)
