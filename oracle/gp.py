@@ -59,6 +59,7 @@ class Params:
     dt: float = 0.0           # ps
     noise_var: float = 0.0    # E|xi|^2 added per site per step
     wigner_nu: float = 0.0    # truncated-Wigner noise intensity nu (0: off)
+    drive_omega: float = 0.0  # angular frequency of the coherent drive, rad/ps
     seed: int = 0
     instance: int = 0
 
@@ -152,9 +153,13 @@ def hamiltonian_apply(psi, n, V, p):
     return out
 
 
-def rhs(psi, n, P, V, p):
-    """Time derivatives (f_psi, f_n) of Eqs. (PULSE_psi)/(PULSE_res), E = 0,
-    without dW.  f_n is None without a reservoir.
+def rhs(psi, n, P, V, p, E=None, t=0.0):
+    """Time derivatives (f_psi, f_n) of Eqs. (PULSE_psi)/(PULSE_res) at time
+    t, without dW.  f_n is None without a reservoir.
+
+    Coherent drive (Sec. V): E is None (E = 0) or the complex amplitude
+    E_c(r) (meV) per component, and the drive term inside the bracket of
+    Eq. (PULSE_psi) is E_c(r) exp(-i drive_omega t).
 
     Truncated-Wigner mode (Sec. V, Example 4; wigner_nu > 0): the equations
     are solved for the renormalised density |psi|^2 - 1/dV (dV the cell
@@ -164,6 +169,8 @@ def rhs(psi, n, P, V, p):
     if w:
         gsum = p.g + (p.g_x if p.spinor else 0.0)
         h = h - (gsum * w) * psi
+    if E is not None:
+        h = h + np.asarray(E) * np.exp(-1j * p.drive_omega * t)
     f_psi = -1j / HBAR * h
     for c in range(p.ncomp):
         gain = -0.5 * p.gamma_c
@@ -179,18 +186,20 @@ def rhs(psi, n, P, V, p):
     return f_psi, f_n
 
 
-def rk4_step(psi, n, P, V, p):
-    """One deterministic RK4 step, Eqs. (rk4_K1)-(rk4_final):
-    K1 = f(y), K2 = f(y + dt/2 K1), K3 = f(y + dt/2 K2), K4 = f(y + dt K3),
-    y' = y + (K1 + 2K2 + 2K3 + K4) dt / 6, on y = (psi, n)."""
+def rk4_step(psi, n, P, V, p, E=None, t=0.0):
+    """One deterministic RK4 step from time t, Eqs. (rk4_K1)-(rk4_final):
+    K1 = f(t, y), K2 = f(t + dt/2, y + dt/2 K1), K3 = f(t + dt/2, y + dt/2 K2),
+    K4 = f(t + dt, y + dt K3), y' = y + (K1 + 2K2 + 2K3 + K4) dt / 6, on
+    y = (psi, n); the only explicit time dependence is the drive's phase."""
     dt = p.dt
-    k1p, k1n = rhs(psi, n, P, V, p)
+    th = t + 0.5 * dt
+    k1p, k1n = rhs(psi, n, P, V, p, E, t)
     k2p, k2n = rhs(psi + 0.5 * dt * k1p,
-                   None if n is None else n + 0.5 * dt * k1n, P, V, p)
+                   None if n is None else n + 0.5 * dt * k1n, P, V, p, E, th)
     k3p, k3n = rhs(psi + 0.5 * dt * k2p,
-                   None if n is None else n + 0.5 * dt * k2n, P, V, p)
+                   None if n is None else n + 0.5 * dt * k2n, P, V, p, E, th)
     k4p, k4n = rhs(psi + dt * k3p,
-                   None if n is None else n + dt * k3n, P, V, p)
+                   None if n is None else n + dt * k3n, P, V, p, E, t + dt)
     psi_new = psi + (k1p + 2.0 * k2p + 2.0 * k3p + k4p) * dt / 6.0
     n_new = None
     if n is not None:
@@ -234,8 +243,9 @@ def add_noise(psi, step, p, fp32_state=False, n_start=None):
     return psi + (re.astype(np.float64) + 1j * im.astype(np.float64))
 
 
-def run(psi, n, P, V, p, nsteps, step0=0):
-    """nsteps RK4 steps (with noise after each) starting at step index step0.
+def run(psi, n, P, V, p, nsteps, step0=0, E=None, t0=0.0):
+    """nsteps RK4 steps (with noise after each) starting at step index step0
+    and time t0 (the time advances by t += dt per step, in FP64).
     Returns (psi, n) in FP64."""
     psi = np.array(psi, dtype=np.complex128)
     n = None if n is None else np.array(n, dtype=np.float64)
@@ -248,10 +258,14 @@ def run(psi, n, P, V, p, nsteps, step0=0):
             P = np.zeros((p.ncomp, p.ny, p.nx))
         elif P.shape[0] != p.ncomp:
             P = np.broadcast_to(P, (p.ncomp, p.ny, p.nx))
+    if E is not None:
+        E = np.broadcast_to(np.asarray(E, dtype=np.complex128), (p.ncomp, p.ny, p.nx))
+    t = t0
     for k in range(nsteps):
         n_start = n
-        psi, n = rk4_step(psi, n, P, V, p)
+        psi, n = rk4_step(psi, n, P, V, p, E, t)
         psi = add_noise(psi, step0 + k, p, n_start=n_start)
+        t = t + p.dt
     return psi, n
 
 
@@ -359,7 +373,7 @@ def pump_threshold(p):
     return p.gamma_c * p.gamma_r / p.R
 
 
-def step_at_sites(psi, n, P, V, p, sites_ji, step, radius=5):
+def step_at_sites(psi, n, P, V, p, sites_ji, step, radius=5, E=None, t=0.0):
     """One RK4 step (plus noise) evaluated only at the given (j, i) sites of
     a large grid.  A step's output at a site depends on the inputs within
     distance 4 (one cell per stage), so each site is computed on its own
@@ -371,6 +385,7 @@ def step_at_sites(psi, n, P, V, p, sites_ji, step, radius=5):
     out_psi = np.empty((nc, len(sites_ji)), complex)
     out_n = np.empty((nc, len(sites_ji))) if p.reservoir else None
     Pb = np.broadcast_to(P, (nc, p.ny, p.nx)) if p.reservoir else None
+    Eb = np.broadcast_to(E, (nc, p.ny, p.nx)) if E is not None else None
 
     def axis(c, N, bc):
         if bc == PERIODIC:
@@ -386,7 +401,8 @@ def step_at_sites(psi, n, P, V, p, sites_ji, step, radius=5):
         win = lambda a: a[..., jj[:, None], ii[None, :]]
         a, b = rk4_step(win(psi), win(n) if p.reservoir else None,
                         win(Pb) if p.reservoir else None,
-                        win(V) if V is not None else None, q)
+                        win(V) if V is not None else None, q,
+                        win(Eb) if E is not None else None, t)
         out_psi[:, k] = a[:, cj, ci]
         if p.reservoir:
             out_n[:, k] = b[:, cj, ci]
