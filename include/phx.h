@@ -4,12 +4,15 @@
  * of PHOENIX (arXiv 2411.18341).
  *
  * What one step computes (all citations are to the paper):
- *   Eq. (PULSE_psi), Sec. V, with coherent drive E = 0:
+ *   Eq. (PULSE_psi), Sec. V:
  *     dpsi_c/dt = -(i/hbar)[ -(hbar^2/2m) Lap psi_c + (V + g|psi_c|^2
- *                 + g_x|psi_o|^2 + g_r n_c) psi_c + J_c psi_o ]
+ *                 + g_x|psi_o|^2 + g_r n_c) psi_c + J_c psi_o + E_c ]
  *                 + (1/2)(R n_c - gamma_c) psi_c  (+ dW)
  *     c in {+} (scalar, Eq. 1) or {+,-} (spinor), o = other component,
- *     J_+ = Delta_LT (d_x - i d_y)^2, J_- = Delta_LT (d_x + i d_y)^2.
+ *     J_+ = Delta_LT (d_x - i d_y)^2, J_- = Delta_LT (d_x + i d_y)^2,
+ *     E_c(r, t) = E_c(r) exp(-i drive_omega t) the coherent drive (zero
+ *     until phx_set_drive), t the handle's FP64 simulated time at the RK4
+ *     stage (t, t + dt/2, t + dt/2, t + dt).
  *   Eq. (PULSE_res): dn_c/dt = P_c - (gamma_r + R|psi_c|^2) n_c.
  *   Lap: the 5-point central-difference stencil of Sec. III.B.6; the TE-TM
  *   operator uses 3-point second differences and the 4-corner mixed
@@ -92,6 +95,7 @@ typedef struct phx_params {
   double dt;                 /* RK4 step, ps; rejected above the stability limit */
   double noise_var;          /* E|xi|^2 added per site and step; 0 = off */
   double wigner_nu;          /* truncated-Wigner noise intensity nu >= 0; 0 = off */
+  double drive_omega;        /* angular frequency of the coherent drive, rad/ps */
   uint64_t seed;             /* Philox key */
   uint32_t instance;         /* Philox counter word 1 (ensemble member id) */
   uint32_t reserved;
@@ -126,6 +130,15 @@ phx_status phx_set_pump(phx_handle* h, const void* P_plus, const void* P_minus,
 
 /* Copy the external potential V (Eq. PULSE_psi); V = NULL removes it. */
 phx_status phx_set_potential(phx_handle* h, const void* V, int on_device);
+
+/* Copy the coherent drive amplitude E_+(r) (and E_-(r); NULL means
+ * E_- = E_+), complex interleaved, meV, one ny x nx plane per component
+ * (Eq. PULSE_psi, Sec. V); the step adds E_c(r) exp(-i drive_omega t) to the
+ * bracket.  E_plus = NULL removes the drive.  While a drive is set the FP32
+ * models step on the generic kernel (phx_tile reports 9).  The energy and
+ * residual reductions stay those of the undriven equations. */
+phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
+                         int on_device);
 
 /* Copy psi (ncomp planes of complex) and n (ncomp planes; ignored / may be
  * NULL without a reservoir, NULL with a reservoir keeps n) into the handle.

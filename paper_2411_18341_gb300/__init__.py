@@ -49,6 +49,7 @@ class phx_params(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("noise_var", ctypes.c_double),
         ("wigner_nu", ctypes.c_double),
+        ("drive_omega", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("instance", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
         ("stream", ctypes.c_void_p),
@@ -75,6 +76,7 @@ _SIGS = {
     "phx_create": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.POINTER(ctypes.c_void_p)]),
     "phx_set_pump": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "phx_set_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_step_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
@@ -250,6 +252,17 @@ def phx_set_pump(h, P_plus, P_minus=None):
 def phx_set_potential(h, V):
     a, dev, k = _ptr(V, h.real, False, h.nx * h.ny)
     _check(lib().phx_set_potential(h.ptr, a, dev), h.ptr)
+
+
+def phx_set_drive(h, E_plus, E_minus=None):
+    """E_plus None removes the drive; E_minus None drives both components
+    with E_plus."""
+    n = h.nx * h.ny
+    a, dev_a, ka = _ptr(E_plus, h.real, True, n)
+    b, dev_b, kb = _ptr(E_minus, h.real, True, n)
+    if a is not None and b is not None and dev_a != dev_b:
+        raise ValueError("E_plus and E_minus must both be host or both device")
+    _check(lib().phx_set_drive(h.ptr, a, b, dev_a if a is not None else 0), h.ptr)
 
 
 def phx_set_state(h, psi, n=None):
@@ -456,7 +469,7 @@ def phx_batch_destroy(b):
 
 PARAM_KEYS = ("nx", "ny", "lx", "ly", "bc_x", "bc_y", "spinor", "reservoir",
               "kappa", "g", "g_x", "g_r", "R", "gamma_c", "gamma_r", "delta_lt",
-              "dt", "noise_var", "wigner_nu", "seed", "instance")
+              "dt", "noise_var", "wigner_nu", "drive_omega", "seed", "instance")
 
 
 def params_from_dict(d, precision=32, stream=None, tile=0):

@@ -75,7 +75,7 @@ const char* check_params(const phx_params* p, double* dtmax_out) {
   if ((p->spinor != 0 && p->spinor != 1) || (p->reservoir != 0 && p->reservoir != 1))
     return "spinor and reservoir must be 0 or 1";
   const double c[] = {p->hbar2_over_2m, p->g, p->g_x, p->g_r, p->R, p->gamma_c,
-                      p->gamma_r, p->delta_lt, p->dt, p->noise_var, p->wigner_nu};
+                      p->gamma_r, p->delta_lt, p->dt, p->noise_var, p->wigner_nu, p->drive_omega};
   for (double v : c)
     if (!std::isfinite(v)) return "coefficients must be finite";
   if (p->hbar2_over_2m < 0) return "hbar2_over_2m must be >= 0";

@@ -35,6 +35,9 @@ struct phx_handle {
   long long P_stride = 0;    // elements between P_+ and P_- planes (0 = shared)
   void* V = nullptr;
   bool has_V = false;
+  void* E = nullptr;         // coherent drive amplitude, ncomp complex planes
+  long long E_stride = 0;    // complex elements between E_+ and E_- (0 = shared)
+  bool has_E = false;
   DevClock* clock = nullptr;
   double* partials = nullptr;
   double* red_dev = nullptr;
@@ -105,6 +108,7 @@ void free_all(phx_handle* h) {
   }
   if (h->P) cudaFree(h->P);
   if (h->V) cudaFree(h->V);
+  if (h->E) cudaFree(h->E);
   if (h->clock) cudaFree(h->clock);
   if (h->partials) cudaFree(h->partials);
   if (h->red_dev) cudaFree(h->red_dev);
@@ -434,6 +438,33 @@ phx_status phx_set_potential(phx_handle* h, const void* V, int on_device) {
   return PHX_OK;
 }
 
+phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
+                         int on_device) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  DeviceGuard dg(h->device);
+  if (!E_plus) {
+    h->has_E = false;
+    return PHX_OK;
+  }
+  const Geometry& g = h->geo;
+  const size_t cplx = 2 * h->esize;
+  if (!h->E) {
+    size_t bytes = (size_t)g.plane * cplx * h->m.ncomp;
+    PHX_CK(h, cudaMalloc(&h->E, bytes));
+    PHX_CK(h, cudaMemsetAsync(h->E, 0, bytes, h->stream));
+  }
+  phx_status st = upload(h, h->E, E_plus, 1, cplx, on_device);
+  if (st != PHX_OK) return st;
+  h->E_stride = 0;
+  if (h->m.ncomp == 2 && E_minus) {
+    st = upload(h, static_cast<char*>(h->E) + (size_t)g.plane * cplx, E_minus, 1, cplx, on_device);
+    if (st != PHX_OK) return st;
+    h->E_stride = g.plane;
+  }
+  h->has_E = true;
+  return PHX_OK;
+}
+
 phx_status phx_set_state(phx_handle* h, const void* psi, const void* n, int on_device) {
   if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
   DeviceGuard dg(h->device);
@@ -485,13 +516,16 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.P = static_cast<const float*>(h->P);
       a.P_comp_stride = h->P_stride;
       a.V = h->has_V ? static_cast<const float*>(h->V) : nullptr;
+      a.E = h->has_E ? static_cast<const float2*>(h->E) : nullptr;
+      a.E_comp_stride = h->E_stride;
+      a.omega = h->p.drive_omega;
       a.k = cast_coeffs<float>(k);
       a.dt64 = k.dt;
       a.noise = nz;
       a.clock = h->clock;
       a.parity = h->parity;
       a.inject_timeout = inj;
-      if (h->tile_cfg != TILE_GENERIC &&
+      if (h->tile_cfg != TILE_GENERIC && !h->has_E &&
           (h->m.ncomp == 1 || spinor_tma_cfg(h->tile_cfg))) {
         if (!h->tuned) {
           if (h->p.tile == 0) {
@@ -520,6 +554,9 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.P = static_cast<const double*>(h->P);
       a.P_comp_stride = h->P_stride;
       a.V = h->has_V ? static_cast<const double*>(h->V) : nullptr;
+      a.E = h->has_E ? static_cast<const double2*>(h->E) : nullptr;
+      a.E_comp_stride = h->E_stride;
+      a.omega = h->p.drive_omega;
       a.k = k;
       a.dt64 = k.dt;
       a.noise = nz;
@@ -619,7 +656,10 @@ phx_status phx_debug_inject(uint32_t mask) {
   return PHX_OK;
 }
 
-int32_t phx_tile(const phx_handle* h) { return h ? h->tile_cfg : 0; }
+int32_t phx_tile(const phx_handle* h) {
+  if (!h) return 0;
+  return (h->has_E && h->m.precision == 32) ? TILE_GENERIC : h->tile_cfg;
+}
 
 const char* phx_last_error(const phx_handle* h) {
   if (h) return h->err.c_str();

@@ -86,6 +86,9 @@ struct StepArgs {
   const R* P;             // ncomp planes (plane 1 may alias plane 0)
   long long P_comp_stride;
   const R* V;             // nullptr when absent
+  const typename Cx<R>::T* E = nullptr;  // coherent drive amplitude E_c(r), meV; nullptr when absent
+  long long E_comp_stride = 0;           // elements between E_+ and E_- planes (0 = shared)
+  double omega = 0.0;                    // drive angular frequency, rad/ps
   CoeffsT<R> k;
   double dt64;            // FP64 time step for the simulated-time accumulator
   NoiseKey noise;

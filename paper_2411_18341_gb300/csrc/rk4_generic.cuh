@@ -14,6 +14,10 @@
 //      argument, with the halo kept on chip);
 //   3. psi' = psi + (K1 + 2K2 + 2K3 + K4) dt/6 (likewise n), plus the noise
 //      xi, is written to the tile and to its periodic ghost images.
+// A coherent drive E_c(r) exp(-i omega t) (when set) is read per site and
+// stage from global memory (cached) with the stage time t, t + dt/2,
+// t + dt/2, t + dt taken from the FP64 device clock; the four phases are
+// evaluated in FP64 by four threads per CTA and shared.
 // Only psi', n' leave the SM; the paper's K buffers and two-/five-term sums
 // never reach memory.
 #pragma once
@@ -75,7 +79,7 @@ __device__ __forceinline__ void store_with_ghosts(T* plane, const Geometry& g,
   }
 }
 
-template <typename R, int NC, bool RES, bool TETM, int TX, int TY, int NT>
+template <typename R, int NC, bool RES, bool TETM, int TX, int TY, int NT, bool DRV>
 __global__ void __launch_bounds__(NT)
 rk4_step_generic(const StepArgs<R> a) {
   using C = typename CxOps<R>::C;
@@ -106,6 +110,18 @@ rk4_step_generic(const StepArgs<R> a) {
       ybuf0[c * LBOX + idx] = v;
       ybuf1[c * LBOX + idx] = v;
     }
+  }
+
+  // Drive phases exp(-i omega t_s) / hbar of the four stages (FP64 sincos on
+  // four threads; published by the barrier below).
+  __shared__ R s_dph[4][2];
+  if (DRV && tid < 4) {
+    const double ts = a.clock->t[a.parity] +
+                      (tid == 0 ? 0.0 : (tid == 3 ? a.dt64 : 0.5 * a.dt64));
+    double sn, cs;
+    sincos(a.omega * ts, &sn, &cs);
+    s_dph[tid][0] = R(cs) * a.k.inv_hbar;
+    s_dph[tid][1] = R(-sn) * a.k.inv_hbar;
   }
 
   // Per-point state (fixed ownership across the four stages).
@@ -160,6 +176,7 @@ rk4_step_generic(const StepArgs<R> a) {
     C* yn = (s & 1) ? ybuf0 : ybuf1;
     const R w = (s == 0 || s == 3) ? R(1) : R(2);
     const R cstep = (s == 2) ? dt : R(0.5) * dt;
+    const R dph_re = DRV ? s_dph[s][0] : R(0), dph_im = DRV ? s_dph[s][1] : R(0);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       if (!valid[k]) continue;
@@ -203,6 +220,15 @@ rk4_step_generic(const StepArgs<R> a) {
           } else {
             H.x += dre - xim;
             H.y += dim + xre;
+          }
+        }
+        if (DRV) {  // + E_c(r) exp(-i omega t_s) / hbar
+          // the box position si is padded site (y0 + si / LX, x0 + si % LX)
+          const int py = y0 + si / LX, px = x0 + si % LX;
+          if (py < g.prow && px < g.pitch) {
+            const C e = __ldg(&a.E[c * a.E_comp_stride + (long long)py * g.pitch + px]);
+            H.x += e.x * dph_re - e.y * dph_im;
+            H.y += e.x * dph_im + e.y * dph_re;
           }
         }
         R G = -hgc;
@@ -287,12 +313,12 @@ rk4_step_generic(const StepArgs<R> a) {
   }
 }
 
-template <typename R, int NC, bool RES, bool TETM, int TX, int TY, int NT>
-cudaError_t launch_generic(const StepArgs<R>& a, cudaStream_t s) {
+template <typename R, int NC, bool RES, bool TETM, int TX, int TY, int NT, bool DRV>
+cudaError_t launch_generic_k(const StepArgs<R>& a, cudaStream_t s) {
   using C = typename CxOps<R>::C;
   constexpr int LBOX = (TX + 2 * HALO) * (TY + 2 * HALO);
   size_t smem = 2 * NC * LBOX * sizeof(C);
-  auto kern = rk4_step_generic<R, NC, RES, TETM, TX, TY, NT>;
+  auto kern = rk4_step_generic<R, NC, RES, TETM, TX, TY, NT, DRV>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(
@@ -304,6 +330,14 @@ cudaError_t launch_generic(const StepArgs<R>& a, cudaStream_t s) {
   kern<<<grid, NT, smem, s>>>(a);
   count_launch();
   return cudaGetLastError();
+}
+
+// The drive term is compiled in only where a drive is set (a.E != nullptr),
+// so undriven steps keep the register budget of the plain equations.
+template <typename R, int NC, bool RES, bool TETM, int TX, int TY, int NT>
+cudaError_t launch_generic(const StepArgs<R>& a, cudaStream_t s) {
+  if (a.E) return launch_generic_k<R, NC, RES, TETM, TX, TY, NT, true>(a, s);
+  return launch_generic_k<R, NC, RES, TETM, TX, TY, NT, false>(a, s);
 }
 
 }  // namespace phx
