@@ -60,6 +60,9 @@ class Params:
     noise_var: float = 0.0    # E|xi|^2 added per site per step
     wigner_nu: float = 0.0    # truncated-Wigner noise intensity nu (0: off)
     drive_omega: float = 0.0  # angular frequency of the coherent drive, rad/ps
+    kfilter_kc: float = 0.0   # k-space smoothing cutoff k_c, 1/um (0: off)
+    kfilter_order: int = 1    # super-Gaussian order p of the smoothing mask
+    kfilter_every: int = 0    # smoothing after every this many steps (0: off)
     seed: int = 0
     instance: int = 0
 
@@ -243,9 +246,28 @@ def add_noise(psi, step, p, fp32_state=False, n_start=None):
     return psi + (re.astype(np.float64) + 1j * im.astype(np.float64))
 
 
+def kfilter_mask(p):
+    """Smoothing mask of Sec. III.B (shape not given; reading: a
+    super-Gaussian low-pass) M(k) = exp(-((k_x^2 + k_y^2) / k_c^2)^p) on the
+    grid's angular wavenumbers k = 2 pi m / L, m in FFT order."""
+    kx = 2.0 * np.pi * np.fft.fftfreq(p.nx, p.dx)
+    ky = 2.0 * np.pi * np.fft.fftfreq(p.ny, p.dy)
+    k2 = ky[:, None] ** 2 + kx[None, :] ** 2
+    return np.exp(-((k2 / p.kfilter_kc ** 2) ** int(p.kfilter_order)))
+
+
+def kfilter(psi, p):
+    """k-space smoothing (Sec. III.B): FFT of each component, product with
+    the mask, inverse FFT (numpy's FFT as the library step)."""
+    M = kfilter_mask(p)
+    return np.stack([np.fft.ifft2(M * np.fft.fft2(psi[c])) for c in range(psi.shape[0])])
+
+
 def run(psi, n, P, V, p, nsteps, step0=0, E=None, t0=0.0):
     """nsteps RK4 steps (with noise after each) starting at step index step0
-    and time t0 (the time advances by t += dt per step, in FP64).
+    and time t0 (the time advances by t += dt per step, in FP64).  With
+    kfilter_every > 0 the smoothing follows every step k (0-based index)
+    with (k + 1) % kfilter_every == 0.
     Returns (psi, n) in FP64."""
     psi = np.array(psi, dtype=np.complex128)
     n = None if n is None else np.array(n, dtype=np.float64)
@@ -265,6 +287,8 @@ def run(psi, n, P, V, p, nsteps, step0=0, E=None, t0=0.0):
         n_start = n
         psi, n = rk4_step(psi, n, P, V, p, E, t)
         psi = add_noise(psi, step0 + k, p, n_start=n_start)
+        if p.kfilter_every > 0 and (step0 + k + 1) % p.kfilter_every == 0:
+            psi = kfilter(psi, p)
         t = t + p.dt
     return psi, n
 
