@@ -140,6 +140,17 @@ phx_status phx_set_potential(phx_handle* h, const void* V, int on_device);
 phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
                          int on_device);
 
+/* k-space smoothing (Sec. III.B): after every `every`-th step (after the step
+ * whose index k, counted as phx_time counts steps, has (k + 1) % every == 0)
+ * each component of psi is Fourier transformed, multiplied by the low-pass
+ * mask M(k) = exp(-((k_x^2 + k_y^2) / k_cut^2)^order), k = 2 pi m / L with m the
+ * FFT index, and transformed back (cuFFT, loaded at the first call).  The
+ * paper does not give the mask; this super-Gaussian is this library's.
+ * every = 0 turns smoothing off (k_cut, order ignored).  EINVAL: every < 0,
+ * k_cut <= 0 or not finite, order outside 1..16.  ECUDA: cuFFT missing or its
+ * plans failed. */
+phx_status phx_set_kfilter(phx_handle* h, double k_cut, int32_t order, int64_t every);
+
 /* Copy psi (ncomp planes of complex) and n (ncomp planes; ignored / may be
  * NULL without a reservoir, NULL with a reservoir keeps n) into the handle.
  * psi may be NULL to keep psi. */

@@ -16,6 +16,7 @@
 #include "../../include/phx.h"
 #include "phx_internal.h"
 #include "rk4_tma.h"
+#include "kfilter.h"
 
 namespace phx {
 unsigned long long launch_total();
@@ -38,6 +39,7 @@ struct phx_handle {
   void* E = nullptr;         // coherent drive amplitude, ncomp complex planes
   long long E_stride = 0;    // complex elements between E_+ and E_- (0 = shared)
   bool has_E = false;
+  KFilter kf;                // k-space smoothing (off unless set)
   DevClock* clock = nullptr;
   double* partials = nullptr;
   double* red_dev = nullptr;
@@ -109,6 +111,7 @@ void free_all(phx_handle* h) {
   if (h->P) cudaFree(h->P);
   if (h->V) cudaFree(h->V);
   if (h->E) cudaFree(h->E);
+  kfilter_release(h->kf);
   if (h->clock) cudaFree(h->clock);
   if (h->partials) cudaFree(h->partials);
   if (h->red_dev) cudaFree(h->red_dev);
@@ -569,7 +572,33 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
     h->cur ^= 1;
     h->parity ^= 1;
     h->host_step += 1;
+    if (h->kf.every > 0 && h->host_step % h->kf.every == 0) {
+      const char* msg = kfilter_apply(h->kf, h->psi[h->cur], h->geo, h->m.ncomp,
+                                      h->m.precision, h->p.lx, h->p.ly, h->stream);
+      if (msg) return fail(h, PHX_ECUDA, msg);
+    }
   }
+  return PHX_OK;
+}
+
+phx_status phx_set_kfilter(phx_handle* h, double k_cut, int32_t order, int64_t every) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  if (every < 0) return fail(h, PHX_EINVAL, "every must be >= 0");
+  DeviceGuard dg(h->device);
+  if (every == 0) {
+    h->kf.every = 0;
+    return PHX_OK;
+  }
+  if (!(k_cut > 0) || !is_finite(k_cut)) return fail(h, PHX_EINVAL, "k_cut must be > 0 and finite");
+  if (order < 1 || order > 16) return fail(h, PHX_EINVAL, "order must be in 1..16");
+  const char* msg = kfilter_setup(h->kf, h->geo, h->m.ncomp, h->m.precision);
+  if (msg) {
+    h->kf.every = 0;
+    return fail(h, PHX_ECUDA, msg);
+  }
+  h->kf.kc = k_cut;
+  h->kf.order = order;
+  h->kf.every = every;
   return PHX_OK;
 }
 
