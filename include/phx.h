@@ -134,9 +134,11 @@ phx_status phx_set_potential(phx_handle* h, const void* V, int on_device);
 /* Copy the coherent drive amplitude E_+(r) (and E_-(r); NULL means
  * E_- = E_+), complex interleaved, meV, one ny x nx plane per component
  * (Eq. PULSE_psi, Sec. V); the step adds E_c(r) exp(-i drive_omega t) to the
- * bracket.  E_plus = NULL removes the drive.  While a drive is set the FP32
- * models step on the generic kernel (phx_tile reports 9).  The energy and
- * residual reductions stay those of the undriven equations. */
+ * bracket.  E_plus = NULL removes the drive.  With a drive set, the FP32 scalar
+ * field without reservoir keeps the TMA-fed kernel; FP32 fields with a
+ * reservoir or two components step on the generic kernel (phx_tile reports
+ * 9).  The energy and residual reductions stay those of the undriven
+ * equations. */
 phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
                          int on_device);
 

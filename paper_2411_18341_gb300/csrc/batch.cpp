@@ -158,7 +158,7 @@ cudaError_t launch_step(const phx_batch* b, int cur, int parity, cudaStream_t s)
   bool per = true;
   for (const phx_params& q : b->p)
     per = per && q.bc_x == PHX_BC_PERIODIC && q.bc_y == PHX_BC_PERIODIC;
-  return launch_rk4_tma_f32(b->tile_cfg, b->reservoir, b->tables_V, per,
+  return launch_rk4_tma_f32(b->tile_cfg, b->reservoir ? 1 : 0, b->tables_V, per,
                             batch_args(b, cur, parity), s, grid);
 }
 

@@ -202,7 +202,7 @@ ReduceArgs reduce_args(const phx_params& p, const Geometry& g, const void* psi, 
 }
 
 bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* const psi[2],
-                    void* const n[2], void* P, void* V, int tile_cfg) {
+                    void* const n[2], void* P, void* V, int tile_cfg, void* E) {
   TmaBox b = tma_box(tile_cfg);
   const int nc = p.spinor ? 2 : 1;
   std::memset(&I, 0, sizeof I);
@@ -227,6 +227,15 @@ bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* c
   if (V && !encode_map_f32(&I.V, V, g.pitch, g.prow, 1, (unsigned long long)g.pitch * 4,
                            (unsigned long long)g.plane * 4, b.f_w, b.f_h))
     return false;
+  if (E) {  // Re and Im planes of the drive (component 0)
+    float* er = static_cast<float*>(E);
+    if (!encode_map_f32(&I.Er, er, g.pitch, g.prow, 1, (unsigned long long)g.pitch * 4,
+                        (unsigned long long)g.plane * 4, b.f_w, b.f_h) ||
+        !encode_map_f32(&I.Ei, er + g.plane, g.pitch, g.prow, 1, (unsigned long long)g.pitch * 4,
+                        (unsigned long long)g.plane * 4, b.f_w, b.f_h))
+      return false;
+  }
+  I.omega = p.drive_omega;
   I.geo = g;
   I.k = cast_coeffs<float>(make_coeffs(p));
   I.noise = make_noise_key(p);

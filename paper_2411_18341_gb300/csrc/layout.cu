@@ -74,6 +74,39 @@ cudaError_t launch_fill_ghosts(void* base, int esize, int nplanes,
   return cudaGetLastError();
 }
 
+// Split nplanes padded planes of interleaved complex values (ghost ring
+// included) into a real and an imaginary plane each: plane c of `src` goes
+// to dst planes 2c (re) and 2c + 1 (im).
+template <typename R, typename C>
+__global__ void split_complex_kernel(const C* src, R* dst, int nplanes, long long plane) {
+  const long long total = plane * nplanes;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = t / plane, r = t - c * plane;
+    const C v = src[t];
+    dst[(2 * c) * plane + r] = v.x;
+    dst[(2 * c + 1) * plane + r] = v.y;
+  }
+}
+
+cudaError_t launch_split_complex(const void* src, void* dst, int esize, int nplanes,
+                                 const Geometry& g, cudaStream_t s) {
+  long long total = g.plane * nplanes;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  if (esize == 4)
+    split_complex_kernel<float, float2><<<blocks, 256, 0, s>>>(
+        static_cast<const float2*>(src), static_cast<float*>(dst), nplanes, g.plane);
+  else if (esize == 8)
+    split_complex_kernel<double, double2><<<blocks, 256, 0, s>>>(
+        static_cast<const double2*>(src), static_cast<double*>(dst), nplanes, g.plane);
+  else
+    return cudaErrorInvalidValue;
+  count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void noise_sample_kernel(unsigned long long seed, long long step,
                                     unsigned int instance, int ncomp, int nx,
                                     int ny, float scale, float* out) {

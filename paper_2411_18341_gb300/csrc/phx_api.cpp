@@ -36,8 +36,8 @@ struct phx_handle {
   long long P_stride = 0;    // elements between P_+ and P_- planes (0 = shared)
   void* V = nullptr;
   bool has_V = false;
-  void* E = nullptr;         // coherent drive amplitude, ncomp complex planes
-  long long E_stride = 0;    // complex elements between E_+ and E_- (0 = shared)
+  void* E = nullptr;         // coherent drive amplitude: Re, Im plane per component
+  long long E_stride = 0;    // elements between the E_+ and E_- plane pairs (0 = shared)
   bool has_E = false;
   KFilter kf;                // k-space smoothing (off unless set)
   DevClock* clock = nullptr;
@@ -169,7 +169,8 @@ TileArgs tile_args(phx_handle* h, int inj);
 cudaError_t launch_tma(phx_handle* h, int cfg, const TileArgs& ta, int grid) {
   if (spinor_tma_cfg(cfg))
     return launch_rk4_tma_spinor(cfg, h->has_V, periodic(h->p), h->m.tetm, ta, h->stream, grid);
-  return launch_rk4_tma_f32(cfg, h->m.reservoir, h->has_V, periodic(h->p), ta, h->stream, grid);
+  const int mode = h->m.reservoir ? 1 : (h->has_E ? 2 : 0);
+  return launch_rk4_tma_f32(cfg, mode, h->has_V, periodic(h->p), ta, h->stream, grid);
 }
 
 // Time every tile configuration of the FP32 scalar kernel on this handle's
@@ -177,7 +178,8 @@ cudaError_t launch_tma(phx_handle* h, int cfg, const TileArgs& ta, int grid) {
 // the other one, so repeating it without swapping leaves the state intact.
 phx_status autotune(phx_handle* h) {
   const auto key = std::make_tuple(h->device, h->p.nx, h->p.ny, h->p.bc_x, h->p.bc_y,
-                                   (int)h->m.reservoir + 2 * h->m.ncomp + 8 * (int)h->m.tetm,
+                                   (int)h->m.reservoir + 2 * h->m.ncomp + 8 * (int)h->m.tetm +
+                                       16 * (int)h->has_E,
                                    (int)h->has_V);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -244,8 +246,10 @@ phx_status autotune(phx_handle* h) {
 // Fill the handle's instance descriptor for the current tile configuration
 // and queue its upload on the handle's stream.
 bool encode_maps(phx_handle* h) {
+  // the TMA-fed drive variant: single-component fields without reservoir
+  void* E = (h->has_E && h->m.ncomp == 1 && !h->m.reservoir) ? h->E : nullptr;
   if (!fill_tile_inst(h->h_inst, h->p, h->geo, h->psi, h->n, h->P, h->has_V ? h->V : nullptr,
-                      h->tile_cfg))
+                      h->tile_cfg, E))
     return false;
   if (cudaMemcpyAsync(h->d_inst, &h->h_inst, sizeof(TileInst), cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess)
@@ -456,15 +460,22 @@ phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
     PHX_CK(h, cudaMalloc(&h->E, bytes));
     PHX_CK(h, cudaMemsetAsync(h->E, 0, bytes, h->stream));
   }
-  phx_status st = upload(h, h->E, E_plus, 1, cplx, on_device);
+  // Stage the interleaved values (ghost ring filled) in the idle half of the
+  // state's double buffer -- the next step overwrites it -- and split them
+  // into Re / Im planes, the layout the step kernels read.
+  void* stage = h->psi[h->cur ^ 1];
+  const int planes = (h->m.ncomp == 2 && E_minus) ? 2 : 1;
+  phx_status st = upload(h, stage, E_plus, 1, cplx, on_device);
   if (st != PHX_OK) return st;
-  h->E_stride = 0;
-  if (h->m.ncomp == 2 && E_minus) {
-    st = upload(h, static_cast<char*>(h->E) + (size_t)g.plane * cplx, E_minus, 1, cplx, on_device);
+  if (planes == 2) {
+    st = upload(h, static_cast<char*>(stage) + (size_t)g.plane * cplx, E_minus, 1, cplx,
+                on_device);
     if (st != PHX_OK) return st;
-    h->E_stride = g.plane;
   }
+  PHX_CK(h, launch_split_complex(stage, h->E, (int)h->esize, planes, g, h->stream));
+  h->E_stride = planes == 2 ? 2 * g.plane : 0;
   h->has_E = true;
+  h->maps_ok = false;
   return PHX_OK;
 }
 
@@ -519,7 +530,7 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.P = static_cast<const float*>(h->P);
       a.P_comp_stride = h->P_stride;
       a.V = h->has_V ? static_cast<const float*>(h->V) : nullptr;
-      a.E = h->has_E ? static_cast<const float2*>(h->E) : nullptr;
+      a.E = h->has_E ? static_cast<const float*>(h->E) : nullptr;
       a.E_comp_stride = h->E_stride;
       a.omega = h->p.drive_omega;
       a.k = cast_coeffs<float>(k);
@@ -528,7 +539,9 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.clock = h->clock;
       a.parity = h->parity;
       a.inject_timeout = inj;
-      if (h->tile_cfg != TILE_GENERIC && !h->has_E &&
+      // drive: TMA-fed for a scalar field without reservoir, else generic
+      const bool drive_ok = !h->has_E || (h->m.ncomp == 1 && !h->m.reservoir);
+      if (h->tile_cfg != TILE_GENERIC && drive_ok &&
           (h->m.ncomp == 1 || spinor_tma_cfg(h->tile_cfg))) {
         if (!h->tuned) {
           if (h->p.tile == 0) {
@@ -557,7 +570,7 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.P = static_cast<const double*>(h->P);
       a.P_comp_stride = h->P_stride;
       a.V = h->has_V ? static_cast<const double*>(h->V) : nullptr;
-      a.E = h->has_E ? static_cast<const double2*>(h->E) : nullptr;
+      a.E = h->has_E ? static_cast<const double*>(h->E) : nullptr;
       a.E_comp_stride = h->E_stride;
       a.omega = h->p.drive_omega;
       a.k = k;
@@ -687,7 +700,8 @@ phx_status phx_debug_inject(uint32_t mask) {
 
 int32_t phx_tile(const phx_handle* h) {
   if (!h) return 0;
-  return (h->has_E && h->m.precision == 32) ? TILE_GENERIC : h->tile_cfg;
+  const bool drive_generic = h->has_E && (h->m.ncomp == 2 || h->m.reservoir);
+  return (drive_generic && h->m.precision == 32) ? TILE_GENERIC : h->tile_cfg;
 }
 
 const char* phx_last_error(const phx_handle* h) {

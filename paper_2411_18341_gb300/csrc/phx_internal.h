@@ -86,8 +86,10 @@ struct StepArgs {
   const R* P;             // ncomp planes (plane 1 may alias plane 0)
   long long P_comp_stride;
   const R* V;             // nullptr when absent
-  const typename Cx<R>::T* E = nullptr;  // coherent drive amplitude E_c(r), meV; nullptr when absent
-  long long E_comp_stride = 0;           // elements between E_+ and E_- planes (0 = shared)
+  // coherent drive amplitude E_c(r), meV, as split planes: Re E_c at
+  // E + c * E_comp_stride, Im E_c one plane further; nullptr when absent
+  const R* E = nullptr;
+  long long E_comp_stride = 0;           // 2 * plane, or 0 when both components share E_+
   double omega = 0.0;                    // drive angular frequency, rad/ps
   CoeffsT<R> k;
   double dt64;            // FP64 time step for the simulated-time accumulator
@@ -109,6 +111,11 @@ cudaError_t launch_rk4_step_f32(const ModelKey& m, const StepArgs<float>& a,
                                 cudaStream_t s, int tile);
 cudaError_t launch_rk4_step_f64(const ModelKey& m, const StepArgs<double>& a,
                                 cudaStream_t s, int tile);
+
+// Split `nplanes` padded planes of interleaved complex values (real element
+// size esize) into a real and an imaginary plane each (dst planes 2c, 2c+1).
+cudaError_t launch_split_complex(const void* src, void* dst, int esize, int nplanes,
+                                 const Geometry& g, cudaStream_t s);
 
 // Fill the ghost ring of `nplanes` planes of element size `esize` bytes.
 cudaError_t launch_fill_ghosts(void* base, int esize, int nplanes,

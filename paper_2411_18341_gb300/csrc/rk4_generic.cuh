@@ -226,7 +226,10 @@ rk4_step_generic(const StepArgs<R> a) {
           // the box position si is padded site (y0 + si / LX, x0 + si % LX)
           const int py = y0 + si / LX, px = x0 + si % LX;
           if (py < g.prow && px < g.pitch) {
-            const C e = __ldg(&a.E[c * a.E_comp_stride + (long long)py * g.pitch + px]);
+            const R* Ec = a.E + c * a.E_comp_stride + (long long)py * g.pitch + px;
+            C e;
+            e.x = __ldg(Ec);
+            e.y = __ldg(Ec + g.plane);
             H.x += e.x * dph_re - e.y * dph_im;
             H.y += e.x * dph_im + e.y * dph_re;
           }

@@ -38,17 +38,17 @@ int tma_ctas_per_sm(int tile_cfg) {
   return tile_cfg == TILE_64x32_M2_2 || tile_cfg == TILE_64x32_M4_2 ? 2 : 1;
 }
 
-cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per,
+cudaError_t launch_rk4_tma_f32(int tile_cfg, int mode, bool pot, bool per,
                                const TileArgs& ta, cudaStream_t s, int grid) {
   const bool one = ta.ninst == 1;
   switch (tile_cfg) {
-    case TILE_64x64: return launch_tma_cfg1(res, pot, per, one, ta, s, grid);
-    case TILE_64x48: return launch_tma_cfg2(res, pot, per, one, ta, s, grid);
-    case TILE_64x32: return launch_tma_cfg3(res, pot, per, one, ta, s, grid);
-    case TILE_64x48_M2: return launch_tma_cfg4(res, pot, per, one, ta, s, grid);
-    case TILE_64x64_M2: return launch_tma_cfg5(res, pot, per, one, ta, s, grid);
-    case TILE_64x32_M2_2: return launch_tma_cfg6(res, pot, per, one, ta, s, grid);
-    case TILE_64x32_M4_2: return launch_tma_cfg7(res, pot, per, one, ta, s, grid);
+    case TILE_64x64: return launch_tma_cfg1(mode, pot, per, one, ta, s, grid);
+    case TILE_64x48: return launch_tma_cfg2(mode, pot, per, one, ta, s, grid);
+    case TILE_64x32: return launch_tma_cfg3(mode, pot, per, one, ta, s, grid);
+    case TILE_64x48_M2: return launch_tma_cfg4(mode, pot, per, one, ta, s, grid);
+    case TILE_64x64_M2: return launch_tma_cfg5(mode, pot, per, one, ta, s, grid);
+    case TILE_64x32_M2_2: return launch_tma_cfg6(mode, pot, per, one, ta, s, grid);
+    case TILE_64x32_M4_2: return launch_tma_cfg7(mode, pot, per, one, ta, s, grid);
     default: break;
   }
   return cudaErrorInvalidValue;

@@ -32,12 +32,14 @@ struct alignas(128) TileInst {
   CUtensorMap psi[2];   // load maps of the psi buffers 0 and 1
   CUtensorMap n[2];     // load maps of the n buffers 0 and 1
   CUtensorMap P, V;
+  CUtensorMap Er, Ei;   // load maps of the coherent drive's Re / Im planes
   float2* psi_buf[2];   // the psi buffers (outputs go to buffer cur ^ 1)
   float* n_buf[2];
   Geometry geo;
   CoeffsT<float> k;
   NoiseKey noise;
   double dt64;          // FP64 step for the simulated-time accumulator
+  double omega;         // drive angular frequency, rad/ps
   int tiles_x, tiles_y; // tiles of this instance for the chosen configuration
   int tile0;            // index of its first tile in the global tile list
 };
@@ -100,12 +102,14 @@ bool encode_map_f32(CUtensorMap* map, void* base, unsigned long long w,
 
 // Build the descriptor of one instance (host memory) for a tile
 // configuration; false if a tensor map cannot be encoded.
+// E: the drive's split Re / Im planes (single-component instances), or nullptr.
 bool fill_tile_inst(TileInst& I, const phx_params& p, const Geometry& g, void* const psi[2],
-                    void* const n[2], void* P, void* V, int tile_cfg);
+                    void* const n[2], void* P, void* V, int tile_cfg, void* E = nullptr);
 
+// mode: 0 = plain, 1 = reservoir, 2 = coherent drive (single instance).
 // per: every instance is periodic in both axes (selects the variant that
 // never forces stage values to zero).
-cudaError_t launch_rk4_tma_f32(int tile_cfg, bool res, bool pot, bool per, const TileArgs& ta,
+cudaError_t launch_rk4_tma_f32(int tile_cfg, int mode, bool pot, bool per, const TileArgs& ta,
                                cudaStream_t s, int grid);
 
 // Two-component field with reservoirs (rk4_tma_spinor.cu); tetm: TE-TM coupling.
@@ -113,19 +117,19 @@ cudaError_t launch_rk4_tma_spinor(int tile_cfg, bool pot, bool per, bool tetm,
                                   const TileArgs& ta, cudaStream_t s, int grid);
 
 // One per tile configuration (rk4_tma_cfgN.cu): every model variant of it.
-cudaError_t launch_tma_cfg1(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_tma_cfg1(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
-cudaError_t launch_tma_cfg2(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_tma_cfg2(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
-cudaError_t launch_tma_cfg3(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_tma_cfg3(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
-cudaError_t launch_tma_cfg4(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_tma_cfg4(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
-cudaError_t launch_tma_cfg5(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_tma_cfg5(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
-cudaError_t launch_tma_cfg6(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_tma_cfg6(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
-cudaError_t launch_tma_cfg7(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_tma_cfg7(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
 
 }  // namespace phx

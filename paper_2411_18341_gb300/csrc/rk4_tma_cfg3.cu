@@ -4,9 +4,9 @@
 
 namespace phx {
 
-cudaError_t launch_tma_cfg3(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_tma_cfg3(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid) {
-  return tma::launch_variants<4, 8, 1>(res, pot, per, one, ta, s, grid);
+  return tma::launch_variants<4, 8, 1>(mode, pot, per, one, ta, s, grid);
 }
 
 }  // namespace phx

@@ -1,7 +1,8 @@
 #pragma once
 // Kernel template of the persistent, TMA-fed fused RK4 step for the FP32
 // scalar field (Eq. 1 / Eq. PULSE_psi with one component, optionally with the
-// reservoir of Eq. PULSE_res and a potential V).
+// reservoir of Eq. PULSE_res or a coherent drive E(r) exp(-i omega t), and a
+// potential V).
 //
 // Per CTA (one or two per SM, 32*WY threads) a loop over output tiles:
 //   * the next tiles' psi box (tile + depth-4 halo) and n, P, V boxes are
@@ -94,7 +95,9 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-template <bool RES, bool POT, int MR, int WY, int MINB = 1>
+// MODE: 0 = no reservoir, 1 = reservoir (n and P planes), 2 = coherent
+// drive without reservoir (Re E and Im E planes in the n and P slots).
+template <int MODE, bool POT, int MR, int WY, int MINB = 1>
 struct Cfg {
   static constexpr int RW = 64;            // region (ring-3) columns: one warp x 2 cols
   static constexpr int RH = MR * WY;       // region rows
@@ -103,7 +106,7 @@ struct Cfg {
   static constexpr int PH = RH + 2;        // psi smem rows: ring, region, ring
   static constexpr int FW = RW + 4;        // n / P / V smem row (4-float aligned box)
   static constexpr int NT = 32 * WY;
-  static constexpr int NF = (RES ? 2 : 0) + (POT ? 1 : 0);
+  static constexpr int NF = (MODE != 0 ? 2 : 0) + (POT ? 1 : 0);
   static constexpr int PSI_BYTES = ((PH * PW * 8) + 127) / 128 * 128;
   static constexpr int F_BYTES = ((RH * FW * 4) + 127) / 128 * 128;
   static constexpr int BUF_BYTES = PSI_BYTES + NF * F_BYTES;
@@ -122,12 +125,14 @@ struct Cfg {
 // (ta.one: constant-bank operands, hoisted out of the tile loop) and whose
 // tile coordinates advance incrementally; otherwise per-tile instance
 // records and precomputed tile coordinates (ta.tile_info).
-template <bool RES, bool POT, bool PER, bool ONE, int MR, int WY, int MINB>
+template <int MODE, bool POT, bool PER, bool ONE, int MR, int WY, int MINB>
 __global__ void __launch_bounds__(32 * WY, MINB)
 rk4_f32_tma(const TileArgs ta) {
-  using C = Cfg<RES, POT, MR, WY, MINB>;
+  constexpr bool RES = MODE == 1, DRV = MODE == 2;
+  using C = Cfg<MODE, POT, MR, WY, MINB>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[3];
+  __shared__ float2 s_dph[4];  // drive phase exp(-i omega t_s) / hbar per stage
   // 128-byte aligned start, by pointer arithmetic on the shared array so that
   // the compiler keeps every derived access in the shared state space
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -204,8 +209,24 @@ rk4_f32_tma(const TileArgs ta) {
       tma_load_3d(f_buf(b, f++), &I->n[ta.cur], xp & ~3, yp + 1, 0, &bar[b]);
       tma_load_3d(f_buf(b, f++), &I->P, xp & ~3, yp + 1, 0, &bar[b]);
     }
+    if (DRV) {
+      tma_load_3d(f_buf(b, f++), &I->Er, xp & ~3, yp + 1, 0, &bar[b]);
+      tma_load_3d(f_buf(b, f++), &I->Ei, xp & ~3, yp + 1, 0, &bar[b]);
+    }
     if (POT) tma_load_3d(f_buf(b, f++), &I->V, xp & ~3, yp + 1, 0, &bar[b]);
   };
+
+  // Drive phases of the four stage times t, t + dt/2, t + dt/2, t + dt
+  // (single instance; FP64 sincos on four threads, published by the barrier
+  // that opens the first tile).
+  if (DRV && tid < 4) {
+    const double ts = ta.clock->t[ta.parity] +
+                      (tid == 0 ? 0.0 : (tid == 3 ? ta.inst[0].dt64 : 0.5 * ta.inst[0].dt64));
+    double sn, cs;
+    sincos(ta.inst[0].omega * ts, &sn, &cs);
+    const float ih = ONE ? ta.one.k.inv_hbar : ta.inst[0].k.inv_hbar;
+    s_dph[tid] = f2((float)cs * ih, (float)(-sn) * ih);
+  }
 
   // FP64 simulated time: instance 0 in the clock, all instances in t_inst
   const long long step = ta.clock->step[ta.parity];
@@ -273,11 +294,13 @@ rk4_f32_tma(const TileArgs ta) {
     float2* P0 = psi_buf(b);
     const float* Nb = RES ? f_buf(b, 0) : nullptr;
     const float* Pb = RES ? f_buf(b, 1) : nullptr;
-    const float* Vb = POT ? f_buf(b, RES ? 2 : 0) : nullptr;
+    const float* Erb = DRV ? f_buf(b, 0) : nullptr;
+    const float* Eib = DRV ? f_buf(b, 1) : nullptr;
+    const float* Vb = POT ? f_buf(b, MODE != 0 ? 2 : 0) : nullptr;
 
     // Registers: psi0, current stage value, accumulator (+ reservoir).
     float2 p0[MR][2], yc[MR][2], acc[MR][2];
-    float n0[MR][2], nc[MR][2], na[MR][2], Pv[MR][2], Vv[MR][2];
+    float n0[MR][2], nc[MR][2], na[MR][2], Pv[MR][2], Vv[MR][2], Er[MR][2], Ei[MR][2];
     bool ins[MR][2];
     const int gx0 = xp - HALO + c0;        // domain column of my first column
     const int gy0 = ky * C::TY - 3 + r0;   // domain row of my first row
@@ -298,6 +321,8 @@ rk4_f32_tma(const TileArgs ta) {
         n0[j][i] = RES ? Nb[fi] : 0.f;
         nc[j][i] = n0[j][i];
         Pv[j][i] = RES ? Pb[fi] : 0.f;
+        Er[j][i] = DRV ? Erb[fi] : 0.f;
+        Ei[j][i] = DRV ? Eib[fi] : 0.f;
         // the stencil's diagonal a0 rides with the local potential
         Vv[j][i] = POT ? fmaf(Vb[fi], cih, q.a0) : q.a0;
       }
@@ -310,6 +335,7 @@ rk4_f32_tma(const TileArgs ta) {
       const float w = (s == 0 || s == 3) ? 1.f : 2.f;
       const float cs = (s == 2) ? dt : 0.5f * dt;
       const float2 w2 = f2(w, w), cs2 = f2(cs, cs);
+      const float2 dph = DRV ? s_dph[s] : f2(0.f, 0.f);
       // neighbours of the micro-tile
       const float4 tv = *reinterpret_cast<const float4*>(&src[(r0)*C::PW + c0 + 2]);
       const float4 bv = *reinterpret_cast<const float4*>(&src[(r0 + MR + 1) * C::PW + c0 + 2]);
@@ -349,7 +375,11 @@ rk4_f32_tma(const TileArgs ta) {
           const float ncur = nc[j][i];
           float loc = fmaf(cg, dens, Vv[j][i]);
           if (RES) loc = fmaf(cgr, ncur, loc);
-          const float2 H = __ffma2_rn(f2(loc, loc), Cc, lap);
+          float2 H = __ffma2_rn(f2(loc, loc), Cc, lap);
+          if (DRV) {  // + E exp(-i omega t_s) / hbar
+            H = __ffma2_rn(f2(Er[j][i], Er[j][i]), dph, H);
+            H = __ffma2_rn(f2(-Ei[j][i], Ei[j][i]), f2(dph.y, dph.x), H);
+          }
           const float G = RES ? fmaf(hR, ncur, -hgc) : -hgc;
           float2 K;
           K.x = fmaf(G, Cc.x, H.y);
@@ -402,7 +432,8 @@ rk4_f32_tma(const TileArgs ta) {
           const uint32_t site = (uint32_t)(((gy % g.ny + g.ny) % g.ny) * g.nx +
                                            (gx % g.nx + g.nx) % g.nx);
           float2 xi, unused;
-          const float sc = nz.twa ? nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var, n0[j][i])
+          const float sc = nz.twa ? nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var,
+                                                    RES ? n0[j][i] : 0.f)
                                   : nz.scale;
           nz_site(nz.seed, nz.instance, step, site, sc, xi, unused, false);
           o[j][i].x = o[j][i].x + xi.x;
@@ -468,10 +499,10 @@ rk4_f32_tma(const TileArgs ta) {
   }
 }
 
-template <bool RES, bool POT, bool PER, bool ONE, int MR, int WY, int MINB>
+template <int MODE, bool POT, bool PER, bool ONE, int MR, int WY, int MINB>
 cudaError_t launch_cfg(const TileArgs& ta, cudaStream_t s, int grid) {
-  using C = Cfg<RES, POT, MR, WY, MINB>;
-  auto kern = rk4_f32_tma<RES, POT, PER, ONE, MR, WY, MINB>;
+  using C = Cfg<MODE, POT, MR, WY, MINB>;
+  auto kern = rk4_f32_tma<MODE, POT, PER, ONE, MR, WY, MINB>;
   static int configured_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -497,25 +528,32 @@ cudaError_t launch_cfg(const TileArgs& ta, cudaStream_t s, int grid) {
   return cudaGetLastError();
 }
 
-// All model variants of one tile configuration.
+// All model variants of one tile configuration (mode as in Cfg; the drive
+// variant exists for single instances only).
 template <int MR, int WY, int MINB>
-cudaError_t launch_variants(bool res, bool pot, bool per, bool one, const TileArgs& ta,
+cudaError_t launch_variants(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid) {
-#define PHX_TMA_V(ONE_)                                                                      \
-  if (per) {                                                                                 \
-    if (res && pot) return launch_cfg<true, true, true, ONE_, MR, WY, MINB>(ta, s, grid);    \
-    if (res) return launch_cfg<true, false, true, ONE_, MR, WY, MINB>(ta, s, grid);          \
-    if (pot) return launch_cfg<false, true, true, ONE_, MR, WY, MINB>(ta, s, grid);          \
-    return launch_cfg<false, false, true, ONE_, MR, WY, MINB>(ta, s, grid);                  \
-  }                                                                                          \
-  if (res && pot) return launch_cfg<true, true, false, ONE_, MR, WY, MINB>(ta, s, grid);     \
-  if (res) return launch_cfg<true, false, false, ONE_, MR, WY, MINB>(ta, s, grid);           \
-  if (pot) return launch_cfg<false, true, false, ONE_, MR, WY, MINB>(ta, s, grid);           \
-  return launch_cfg<false, false, false, ONE_, MR, WY, MINB>(ta, s, grid);
+#define PHX_TMA_V(M_, ONE_)                                                             \
+  if (per) {                                                                            \
+    if (pot) return launch_cfg<M_, true, true, ONE_, MR, WY, MINB>(ta, s, grid);        \
+    return launch_cfg<M_, false, true, ONE_, MR, WY, MINB>(ta, s, grid);                \
+  }                                                                                     \
+  if (pot) return launch_cfg<M_, true, false, ONE_, MR, WY, MINB>(ta, s, grid);         \
+  return launch_cfg<M_, false, false, ONE_, MR, WY, MINB>(ta, s, grid);
   if (one) {
-    PHX_TMA_V(true)
+    if (mode == 2) {
+      PHX_TMA_V(2, true)
+    }
+    if (mode == 1) {
+      PHX_TMA_V(1, true)
+    }
+    PHX_TMA_V(0, true)
   }
-  PHX_TMA_V(false)
+  if (mode == 2) return cudaErrorInvalidValue;
+  if (mode == 1) {
+    PHX_TMA_V(1, false)
+  }
+  PHX_TMA_V(0, false)
 #undef PHX_TMA_V
 }
 

@@ -190,6 +190,50 @@ def twa_ensemble(count=150, n=256, length=200.0, pump_factor=2.0, nu=1.0, seed=7
     return out
 
 
+def driven_lattice(n=9000, dx=0.1, seed=11, wells=272, a1=2.8, a2=3.8, depth=4.0,
+                   width=1.2, aah=0.2, e0=5.6856e-3, omega=-5.6883, spot=10.0):
+    """Coherently driven potential lattice with the shapes of the paper's
+    topological corner-state example (9000^2 grid, 272^2 wells, resonant
+    drive omega = -5.6883 ps^-1, E0 = 5.6856 ueV); its own parameters are not
+    available, so these stand in: an SSH lattice (alternating spacings a1, a2
+    um) of super-Gaussian wells -depth exp(-(r/width)^4) meV whose depths
+    carry an Aubry-Andre-Harper modulation 1 + aah cos(2 pi beta (i + j)),
+    beta the golden ratio's fractional part, and a Gaussian drive spot of
+    waist `spot` um on the corner well.  Scalar, no reservoir, loss
+    gamma_c = 0.15 ps^-1, g = 6e-3 meV um^2, periodic."""
+    c = load_constants()
+    length = n * dx
+    p = base_params(n, n, length, length, g=G_C, gamma_c=GAMMA_C,
+                    dt=c["driven_%d_L%g" % (n, length)]["dt"], drive_omega=omega)
+    gaps = np.where(np.arange(wells - 1) % 2 == 0, a1, a2)
+    pos = np.concatenate([[0.0], np.cumsum(gaps)])
+    pos = pos - 0.5 * pos[-1]                  # lattice centred in the box
+    x = coords(n, length)
+    k = np.clip(np.searchsorted(pos, x), 1, wells - 1)
+    near = np.where(np.abs(x - pos[k - 1]) < np.abs(x - pos[k]), k - 1, k)
+    d = x - pos[near]                          # distance to the nearest well per axis
+    beta = 0.5 * (np.sqrt(5.0) - 1.0)
+    amp = depth * (1.0 + aah * np.cos(2 * np.pi * beta * (near[:, None] + near[None, :])))
+    r2 = (d[:, None] ** 2 + d[None, :] ** 2) / width ** 2
+    V = (-amp * np.exp(-r2 * r2)).astype(np.float32)
+    del r2, amp
+    E = gaussian(n, n, length, length, e0, spot, pos[0], pos[0]).astype(np.complex64)[None]
+    psi0 = complex_normal((1, n, n), 1e-3, seed).astype(np.complex64)
+    return dict(name="driven_%d" % n, params=p, psi0=psi0, n0=None, P=None, V=V, E=E,
+                steps=None)
+
+
+def crop(cfg, m):
+    """The m x m corner window of a workload (same cell size and physics,
+    periodic over the window): a bounded sample for CPU timing."""
+    d = dict(cfg["params"])
+    dx, dy = d["lx"] / d["nx"], d["ly"] / d["ny"]
+    d.update(nx=m, ny=m, lx=m * dx, ly=m * dy)
+    win = lambda a: None if a is None else np.ascontiguousarray(np.asarray(a)[..., :m, :m])
+    return dict(cfg, params=d, psi0=win(cfg["psi0"]), n0=win(cfg["n0"]), P=win(cfg["P"]),
+                V=win(cfg.get("V")), E=win(cfg.get("E")))
+
+
 def random_gaussian_pumps(n=256, length=128.0, count=1, seed=5000):
     """count pump images, each a sum of 1-4 Gaussians exp(-|r-c|^2/w^2) with
     w ~ U[3, 15] um, peak ~ U[1, 3] P_thr, centres within L/2 - 2w."""

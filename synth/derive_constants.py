@@ -42,6 +42,9 @@ def main():
     out["steady_256_L128"] = {"dt": 0.85 * dmax, "dt_max": dmax}
     # truncated-Wigner ensemble: 256^2 over 200 um, half the limit
     out["twa_256_L200"] = {"dt": half_limit(nx=256, ny=256, lx=200.0, ly=200.0, **res)}
+    # driven lattice: 9000^2 cells of 0.1 um, scalar with loss and g
+    out["driven_9000_L900"] = {"dt": half_limit(nx=9000, ny=9000, lx=900.0, ly=900.0,
+                                                kappa=KAPPA, g=6e-3, gamma_c=0.15)}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
                         "constants.json")
     with open(path, "w") as f:

@@ -133,3 +133,29 @@ def test_drive_fp32_spinor_generic_shapes(tile):
     h, (g_psi, g_n), (o_psi, o_n) = run_driven(d, 32, E, False, steps=7, tile=tile)
     assert rel_l2(g_psi, o_psi) <= 1e-4
     assert rel_l2(g_n, o_n) <= 1e-4
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1), (0, 1)])
+def test_drive_tma_scalar_kernel(tile, bc):
+    """FP32 scalar field without reservoir: the drive runs in the TMA-fed
+    persistent kernel (Re / Im planes staged like the reservoir's) in every
+    tile configuration, ragged grid, with a potential."""
+    m = phx()
+    d = drive_model("loss", 131, 77, bc=bc)
+    E = smooth_field(1, 77, 131, 8, 0.4)
+    h, (g_psi, _), (o_psi, _) = run_driven(d, 32, E, False, steps=11, tile=tile)
+    assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
+    assert m.phx_tile(h) in range(1, 8)
+    if tile:
+        assert m.phx_tile(h) == tile
+
+
+@pytest.mark.parametrize("tile", [0, 6])
+def test_drive_tma_with_truncated_wigner_noise(tile):
+    d = drive_model("loss", 97, 66)
+    d.update(wigner_nu=1.2, noise_var=1e-5)
+    E = smooth_field(1, 66, 97, 9, 0.3)
+    h, (g_psi, _), (o_psi, _) = run_driven(d, 32, E, False, steps=9, tile=tile)
+    assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
+    assert phx().phx_tile(h) in range(1, 8)
