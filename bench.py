@@ -455,7 +455,7 @@ def run_ensemble(args, world, rank, local, pg):
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
-                     "traffic": recorded_traffic(args.workload, 32),
+                     "traffic": recorded_traffic(args.workload, 32, phx.phx_batch_tile(b)),
                      "kernel": "rk4_f32_tma (persistent, all members per launch)",
                      "algorithmic_bytes_per_site": 28, "avg_launch_us": kern_s * 1e6,
                      "peak_source": pk_kind},
