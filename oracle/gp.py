@@ -263,6 +263,50 @@ def kfilter(psi, p):
     return np.stack([np.fft.ifft2(M * np.fft.fft2(psi[c])) for c in range(psi.shape[0])])
 
 
+def ssf_local(psi, V, p, tau):
+    """Exact solution over time tau of the local part of Eq. (PULSE_psi) for a
+    scalar field without reservoir, dpsi/dt = (-(i/hbar)(V + g|psi|^2) -
+    gamma_c/2) psi: |psi|^2 decays as e^{-gamma_c t}, so
+    psi(tau) = psi e^{-gamma_c tau/2} exp(-(i/hbar)(V tau + g |psi|^2 F)),
+    F = (1 - e^{-gamma_c tau})/gamma_c (F = tau without loss)."""
+    a = np.abs(psi) ** 2
+    if p.gamma_c != 0.0:
+        F = -np.expm1(-p.gamma_c * tau) / p.gamma_c
+    else:
+        F = tau
+    phase = p.g * a * F
+    if V is not None:
+        phase = phase + V * tau
+    return psi * np.exp(-0.5 * p.gamma_c * tau) * np.exp(-1j / HBAR * phase)
+
+
+def ssf_kinetic(psi, p, tau):
+    """Exact kinetic propagation exp(-(i/hbar) kappa k^2 tau) in Fourier
+    space (spectral kinetic energy, k = 2 pi m / L, periodic)."""
+    kx = 2.0 * np.pi * np.fft.fftfreq(p.nx, p.dx)
+    ky = 2.0 * np.pi * np.fft.fftfreq(p.ny, p.dy)
+    k2 = ky[:, None] ** 2 + kx[None, :] ** 2
+    U = np.exp(-1j / HBAR * p.kappa * k2 * tau)
+    return np.stack([np.fft.ifft2(U * np.fft.fft2(psi[c])) for c in range(psi.shape[0])])
+
+
+def run_ssf(psi, V, p, nsteps, step0=0):
+    """The split-step Fourier method (conclusions: the conventional
+    alternative to RK4 the paper's code also offers; no details given).
+    Reading: Strang splitting of a scalar field without reservoir,
+    psi <- L(dt/2) K(dt) L(dt/2) psi per step with the exact local (ssf_local)
+    and kinetic (ssf_kinetic) propagators, then the same per-step noise as
+    run().  Periodic boundaries only."""
+    psi = np.array(psi, dtype=np.complex128)
+    V = None if V is None else np.asarray(V, dtype=np.float64)
+    for k in range(nsteps):
+        psi = ssf_local(psi, V, p, 0.5 * p.dt)
+        psi = ssf_kinetic(psi, p, p.dt)
+        psi = ssf_local(psi, V, p, 0.5 * p.dt)
+        psi = add_noise(psi, step0 + k, p)
+    return psi
+
+
 def run(psi, n, P, V, p, nsteps, step0=0, E=None, t0=0.0):
     """nsteps RK4 steps (with noise after each) starting at step index step0
     and time t0 (the time advances by t += dt per step, in FP64).  With
