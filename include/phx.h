@@ -142,6 +142,19 @@ phx_status phx_set_potential(phx_handle* h, const void* V, int on_device);
 phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
                          int on_device);
 
+/* nsteps steps of the split-step Fourier method instead of RK4 (the
+ * conventional alternative the paper's conclusions name, without details):
+ * Strang splitting psi <- L(dt/2) K(dt) L(dt/2) psi with the exact local
+ * propagator L(tau) psi = psi e^{-gamma_c tau/2} exp(-(i/hbar)(V tau + g|psi|^2 F)),
+ * F = (1 - e^{-gamma_c tau})/gamma_c (tau without loss), and the exact
+ * spectral kinetic propagator K(tau) = exp(-(i/hbar) kappa k^2 tau), k = 2 pi m / L
+ * (cuFFT, loaded at the first call); then the step's noise as in phx_step_n.
+ * Same dt, clock and state as phx_step_n (the two may alternate).  ESTATE
+ * unless the handle is a scalar field without reservoir, periodic in x and
+ * y, without drive and without truncated-Wigner noise; ECUDA if cuFFT is
+ * missing. */
+phx_status phx_step_ssf(phx_handle* h, int64_t nsteps);
+
 /* k-space smoothing (Sec. III.B): after every `every`-th step (after the step
  * whose index k, counted as phx_time counts steps, has (k + 1) % every == 0)
  * each component of psi is Fourier transformed, multiplied by the low-pass

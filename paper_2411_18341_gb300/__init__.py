@@ -78,6 +78,7 @@ _SIGS = {
     "phx_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_set_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_set_kfilter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64]),
+    "phx_step_ssf": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "phx_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_step_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
@@ -264,6 +265,10 @@ def phx_set_drive(h, E_plus, E_minus=None):
     if a is not None and b is not None and dev_a != dev_b:
         raise ValueError("E_plus and E_minus must both be host or both device")
     _check(lib().phx_set_drive(h.ptr, a, b, dev_a if a is not None else 0), h.ptr)
+
+
+def phx_step_ssf(h, nsteps):
+    _check(lib().phx_step_ssf(h.ptr, int(nsteps)), h.ptr)
 
 
 def phx_set_kfilter(h, k_cut, order=1, every=1):

@@ -70,7 +70,7 @@ __global__ void kfilter_mask_kernel(C* d, int nx, int ny, int ncomp, R dkx, R dk
 
 }  // namespace
 
-void kfilter_release(KFilter& f) {
+void fft_pair_release(FftPair& f) {
   const FftApi& api = fft_api();
   if (f.have_plans && api.ok) {
     api.destroy(f.plan_fwd);
@@ -79,24 +79,19 @@ void kfilter_release(KFilter& f) {
   f.have_plans = false;
   if (f.scratch) cudaFree(f.scratch);
   f.scratch = nullptr;
-  f.every = 0;
 }
 
-const char* kfilter_setup(KFilter& f, const Geometry& g, int ncomp, int precision) {
+const char* fft_pair_setup(FftPair& f, const Geometry& g, int ncomp, int precision) {
   const FftApi& api = fft_api();
   if (!api.ok) return "cuFFT (libcufft.so.12) could not be loaded";
-  if (g.plane * ncomp >= (1ll << 31)) return "grid too large for the smoothing transform";
-  if (f.have_plans) {
-    api.destroy(f.plan_fwd);
-    api.destroy(f.plan_inv);
-    f.have_plans = false;
-  }
+  if (f.have_plans) return nullptr;
+  if (g.plane * ncomp >= (1ll << 31)) return "grid too large for the FFT plans";
   if (!f.scratch) {
     const size_t bytes = (size_t)g.nx * g.ny * ncomp * (precision == 64 ? 16 : 8);
     if (cudaMalloc(&f.scratch, bytes) != cudaSuccess) {
       cudaGetLastError();
       f.scratch = nullptr;
-      return "cudaMalloc of the smoothing scratch failed";
+      return "cudaMalloc of the FFT scratch failed";
     }
   }
   int n[2] = {g.ny, g.nx};
@@ -116,45 +111,60 @@ const char* kfilter_setup(KFilter& f, const Geometry& g, int ncomp, int precisio
   return nullptr;
 }
 
-const char* kfilter_apply(const KFilter& f, void* psi, const Geometry& g, int ncomp,
-                          int precision, double lx, double ly, cudaStream_t s) {
+const char* fft_transform(const FftPair& f, void* psi, const Geometry& g, int precision,
+                          bool forward, cudaStream_t s) {
   const FftApi& api = fft_api();
-  if (!f.have_plans) return "smoothing not set up";
-  if (api.set_stream(f.plan_fwd, s) != CUFFT_SUCCESS ||
-      api.set_stream(f.plan_inv, s) != CUFFT_SUCCESS)
-    return "cufftSetStream failed";
+  if (!f.have_plans) return "FFT plans not set up";
+  const int plan = forward ? f.plan_fwd : f.plan_inv;
+  if (api.set_stream(plan, s) != CUFFT_SUCCESS) return "cufftSetStream failed";
   const long long origin = (long long)HALO * g.pitch + HALO;
-  const double pi = 3.14159265358979323846;
-  const long long total = (long long)g.nx * g.ny * ncomp;
-  const int threads = 256;
-  const int blocks = (int)((total + threads - 1) / threads < 4096 ? (total + threads - 1) / threads
-                                                                    : 4096);
-  const double scale = 1.0 / ((double)g.nx * g.ny);
-  const double inv_kc2 = 1.0 / (f.kc * f.kc);
+  cufftResult r;
   if (precision == 64) {
     auto* base = static_cast<cufftDoubleComplex*>(psi) + origin;
     auto* sc = static_cast<cufftDoubleComplex*>(f.scratch);
-    if (api.exec_z2z(f.plan_fwd, base, sc, CUFFT_FORWARD) != CUFFT_SUCCESS)
-      return "cufftExecZ2Z (forward) failed";
-    kfilter_mask_kernel<double, double2><<<blocks, threads, 0, s>>>(
-        reinterpret_cast<double2*>(sc), g.nx, g.ny, ncomp, 2 * pi / lx, 2 * pi / ly, inv_kc2,
-        f.order, scale);
-    count_launch();
-    if (api.exec_z2z(f.plan_inv, sc, base, CUFFT_INVERSE) != CUFFT_SUCCESS)
-      return "cufftExecZ2Z (inverse) failed";
+    r = forward ? api.exec_z2z(plan, base, sc, CUFFT_FORWARD)
+                : api.exec_z2z(plan, sc, base, CUFFT_INVERSE);
   } else {
     auto* base = static_cast<cufftComplex*>(psi) + origin;
     auto* sc = static_cast<cufftComplex*>(f.scratch);
-    if (api.exec_c2c(f.plan_fwd, base, sc, CUFFT_FORWARD) != CUFFT_SUCCESS)
-      return "cufftExecC2C (forward) failed";
-    kfilter_mask_kernel<float, float2><<<blocks, threads, 0, s>>>(
-        reinterpret_cast<float2*>(sc), g.nx, g.ny, ncomp, (float)(2 * pi / lx),
-        (float)(2 * pi / ly), (float)inv_kc2, f.order, (float)scale);
-    count_launch();
-    if (api.exec_c2c(f.plan_inv, sc, base, CUFFT_INVERSE) != CUFFT_SUCCESS)
-      return "cufftExecC2C (inverse) failed";
+    r = forward ? api.exec_c2c(plan, base, sc, CUFFT_FORWARD)
+                : api.exec_c2c(plan, sc, base, CUFFT_INVERSE);
   }
+  return r == CUFFT_SUCCESS ? nullptr : "cuFFT execution failed";
+}
+
+void kfilter_release(KFilter& f) {
+  fft_pair_release(f.fft);
+  f.every = 0;
+}
+
+const char* kfilter_setup(KFilter& f, const Geometry& g, int ncomp, int precision) {
+  return fft_pair_setup(f.fft, g, ncomp, precision);
+}
+
+const char* kfilter_apply(const KFilter& f, void* psi, const Geometry& g, int ncomp,
+                          int precision, double lx, double ly, cudaStream_t s) {
+  const char* msg = fft_transform(f.fft, psi, g, precision, true, s);
+  if (msg) return msg;
+  const double pi = 3.14159265358979323846;
+  const long long total = (long long)g.nx * g.ny * ncomp;
+  const int threads = 256;
+  const long long want = (total + threads - 1) / threads;
+  const int blocks = (int)(want < 4096 ? want : 4096);
+  const double scale = 1.0 / ((double)g.nx * g.ny);
+  const double inv_kc2 = 1.0 / (f.kc * f.kc);
+  if (precision == 64)
+    kfilter_mask_kernel<double, double2><<<blocks, threads, 0, s>>>(
+        static_cast<double2*>(f.fft.scratch), g.nx, g.ny, ncomp, 2 * pi / lx, 2 * pi / ly,
+        inv_kc2, f.order, scale);
+  else
+    kfilter_mask_kernel<float, float2><<<blocks, threads, 0, s>>>(
+        static_cast<float2*>(f.fft.scratch), g.nx, g.ny, ncomp, (float)(2 * pi / lx),
+        (float)(2 * pi / ly), (float)inv_kc2, f.order, (float)scale);
+  count_launch();
   if (cudaGetLastError() != cudaSuccess) return "smoothing mask launch failed";
+  msg = fft_transform(f.fft, psi, g, precision, false, s);
+  if (msg) return msg;
   if (launch_fill_ghosts(psi, precision == 64 ? 16 : 8, ncomp, g, s) != cudaSuccess)
     return "ghost refill after smoothing failed";
   return nullptr;

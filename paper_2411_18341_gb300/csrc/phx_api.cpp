@@ -17,6 +17,7 @@
 #include "phx_internal.h"
 #include "rk4_tma.h"
 #include "kfilter.h"
+#include "ssf.h"
 
 namespace phx {
 unsigned long long launch_total();
@@ -40,6 +41,7 @@ struct phx_handle {
   long long E_stride = 0;    // elements between the E_+ and E_- plane pairs (0 = shared)
   bool has_E = false;
   KFilter kf;                // k-space smoothing (off unless set)
+  FftPair ssf_fft;           // FFT plans of the split-step integrator (made at first use)
   DevClock* clock = nullptr;
   double* partials = nullptr;
   double* red_dev = nullptr;
@@ -112,6 +114,7 @@ void free_all(phx_handle* h) {
   if (h->V) cudaFree(h->V);
   if (h->E) cudaFree(h->E);
   kfilter_release(h->kf);
+  fft_pair_release(h->ssf_fft);
   if (h->clock) cudaFree(h->clock);
   if (h->partials) cudaFree(h->partials);
   if (h->red_dev) cudaFree(h->red_dev);
@@ -591,6 +594,32 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       if (msg) return fail(h, PHX_ECUDA, msg);
     }
   }
+  return PHX_OK;
+}
+
+phx_status phx_step_ssf(phx_handle* h, int64_t nsteps) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(h, PHX_EINVAL, "nsteps must be >= 0");
+  if (h->m.ncomp != 1 || h->m.reservoir)
+    return fail(h, PHX_ESTATE, "split-step needs a scalar field without reservoir");
+  if (h->p.bc_x != PHX_BC_PERIODIC || h->p.bc_y != PHX_BC_PERIODIC)
+    return fail(h, PHX_ESTATE, "split-step needs periodic boundaries");
+  if (h->has_E || h->p.wigner_nu > 0.0)
+    return fail(h, PHX_ESTATE, "split-step supports neither a drive nor truncated-Wigner noise");
+  if (nsteps == 0) return PHX_OK;
+  DeviceGuard dg(h->device);
+  const char* msg = fft_pair_setup(h->ssf_fft, h->geo, 1, h->m.precision);
+  if (msg) return fail(h, PHX_ECUDA, msg);
+  const SsfCoeffs k = ssf_coeffs(h->p);
+  const NoiseKey nz = make_noise_key(h->p);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    msg = ssf_step(h->ssf_fft, h->psi[h->cur], h->geo, h->m.precision,
+                   h->has_V ? h->V : nullptr, k, nz, h->clock, h->parity, h->stream);
+    if (msg) return fail(h, PHX_ECUDA, msg);
+    h->parity ^= 1;
+    h->host_step += 1;
+  }
+  PHX_CK(h, launch_fill_ghosts(h->psi[h->cur], (int)(2 * h->esize), 1, h->geo, h->stream));
   return PHX_OK;
 }
 

@@ -1,0 +1,124 @@
+// Split-step Fourier integrator (the conventional alternative to RK4 the
+// paper's conclusions name; no details given): Strang splitting
+//   psi <- L(dt/2) K(dt) L(dt/2) psi
+// of a scalar field without reservoir, with the exact local propagator
+//   L(tau) psi = psi e^{-gamma_c tau/2} exp(-(i/hbar)(V tau + g |psi|^2 F)),
+//   F = (1 - e^{-gamma_c tau}) / gamma_c   (F = tau without loss),
+// which holds because |psi|^2 only decays under the local equation, and the
+// exact kinetic propagator K(tau) = exp(-(i/hbar) kappa k^2 tau) applied in
+// Fourier space (cuFFT, via the FFT pair of kfilter.cu).  The second local
+// half step of each step also adds the step's noise (same Philox stream as
+// the RK4 path) and advances the FP64 device clock.
+#include "phx_noise.cuh"
+#include "ssf.h"
+
+namespace phx {
+
+namespace {
+
+__device__ __forceinline__ int fft_index_ssf(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
+
+template <typename R, typename C>
+__global__ void ssf_local_kernel(C* psi, Geometry g, const R* V, R gF, R tau_h, R damp,
+                                 NoiseKey nz, DevClock* clock, int parity, int last,
+                                 double dt64) {
+  const long long sites = (long long)g.nx * g.ny;
+  const long long step = clock->step[parity];
+  if (last && blockIdx.x == 0 && threadIdx.x == 0) {
+    clock->step[parity ^ 1] = step + 1;
+    clock->t[parity ^ 1] = clock->t[parity] + dt64;
+  }
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < sites;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
+    const long long off = (long long)(j + HALO) * g.pitch + i + HALO;
+    C v = psi[off];
+    // angle of exp(-(i/hbar)(V tau + g |psi|^2 F)): gF = g F / hbar, tau_h = tau / hbar
+    R ph = gF * (v.x * v.x + v.y * v.y);
+    if (V) ph += tau_h * V[off];
+    R sn, cs;
+    sincos(ph, &sn, &cs);
+    C o;
+    o.x = damp * (v.x * cs + v.y * sn);
+    o.y = damp * (v.y * cs - v.x * sn);
+    if (last && nz.on) {
+      float2 xi, unused;
+      nz_site(nz.seed, nz.instance, step, (uint32_t)t, nz.scale, xi, unused, false);
+      o.x = o.x + R(xi.x);
+      o.y = o.y + R(xi.y);
+    }
+    psi[off] = o;
+  }
+}
+
+template <typename R, typename C>
+__global__ void ssf_kinetic_kernel(C* d, int nx, int ny, R dkx, R dky, R c, R scale) {
+  const long long total = (long long)nx * ny;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / nx), i = (int)(t - (long long)j * nx);
+    const R kx = dkx * R(fft_index_ssf(i, nx)), ky = dky * R(fft_index_ssf(j, ny));
+    R sn, cs;
+    sincos(c * (ky * ky + kx * kx), &sn, &cs);  // exp(-i c k^2) = cs - i sn
+    C v = d[t], o;
+    o.x = scale * (v.x * cs + v.y * sn);
+    o.y = scale * (v.y * cs - v.x * sn);
+    d[t] = o;
+  }
+}
+
+int grid_for(long long n) {
+  const long long b = (n + 255) / 256;
+  return (int)(b < 8192 ? (b < 1 ? 1 : b) : 8192);
+}
+
+template <typename R, typename C>
+const char* ssf_step_t(FftPair& fft, void* psi, const Geometry& g, const void* V,
+                       const SsfCoeffs& k, const NoiseKey& nz, DevClock* clock, int parity,
+                       cudaStream_t s) {
+  C* p = static_cast<C*>(psi);
+  const R* v = static_cast<const R*>(V);
+  const int blocks = grid_for((long long)g.nx * g.ny);
+  ssf_local_kernel<R, C><<<blocks, 256, 0, s>>>(p, g, v, (R)k.gF_half, (R)k.tau_half_h,
+                                                (R)k.damp_half, nz, clock, parity, 0, k.dt);
+  count_launch();
+  const char* msg = fft_transform(fft, psi, g, sizeof(R) == 8 ? 64 : 32, true, s);
+  if (msg) return msg;
+  ssf_kinetic_kernel<R, C><<<blocks, 256, 0, s>>>(static_cast<C*>(fft.scratch), g.nx, g.ny,
+                                                  (R)k.dkx, (R)k.dky, (R)k.kin, (R)k.scale);
+  count_launch();
+  msg = fft_transform(fft, psi, g, sizeof(R) == 8 ? 64 : 32, false, s);
+  if (msg) return msg;
+  ssf_local_kernel<R, C><<<blocks, 256, 0, s>>>(p, g, v, (R)k.gF_half, (R)k.tau_half_h,
+                                                (R)k.damp_half, nz, clock, parity, 1, k.dt);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? nullptr : "split-step kernel launch failed";
+}
+
+}  // namespace
+
+SsfCoeffs ssf_coeffs(const phx_params& p) {
+  SsfCoeffs k;
+  const double tau = 0.5 * p.dt;
+  const double F = p.gamma_c != 0.0 ? -std::expm1(-p.gamma_c * tau) / p.gamma_c : tau;
+  k.gF_half = p.g * F / HBAR;
+  k.tau_half_h = tau / HBAR;
+  k.damp_half = std::exp(-0.5 * p.gamma_c * tau);
+  const double pi = 3.14159265358979323846;
+  k.dkx = 2.0 * pi / p.lx;
+  k.dky = 2.0 * pi / p.ly;
+  k.kin = p.hbar2_over_2m * p.dt / HBAR;
+  k.scale = 1.0 / ((double)p.nx * p.ny);
+  k.dt = p.dt;
+  return k;
+}
+
+const char* ssf_step(FftPair& fft, void* psi, const Geometry& g, int precision, const void* V,
+                     const SsfCoeffs& k, const NoiseKey& nz, DevClock* clock, int parity,
+                     cudaStream_t s) {
+  if (precision == 64)
+    return ssf_step_t<double, double2>(fft, psi, g, V, k, nz, clock, parity, s);
+  return ssf_step_t<float, float2>(fft, psi, g, V, k, nz, clock, parity, s);
+}
+
+}  // namespace phx

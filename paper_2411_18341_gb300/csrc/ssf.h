@@ -1,0 +1,30 @@
+// Split-step Fourier integrator for a scalar field without reservoir; see ssf.cu.
+#pragma once
+
+#include <cmath>
+
+#include "kfilter.h"
+#include "phx_internal.h"
+
+namespace phx {
+
+// Host-computed coefficients of one Strang step (FP64; cast per precision).
+struct SsfCoeffs {
+  double gF_half;     // g F(dt/2) / hbar
+  double tau_half_h;  // (dt/2) / hbar, multiplies V
+  double damp_half;   // exp(-gamma_c dt/4)
+  double dkx, dky;    // 2 pi / L
+  double kin;         // kappa dt / hbar
+  double scale;       // 1 / (nx ny), the inverse transform's normalisation
+  double dt;
+};
+
+SsfCoeffs ssf_coeffs(const phx_params& p);
+
+// One step on the padded state psi (interior; the ghost ring is left stale),
+// queued on stream s.  nullptr on success, else a message.
+const char* ssf_step(FftPair& fft, void* psi, const Geometry& g, int precision, const void* V,
+                     const SsfCoeffs& k, const NoiseKey& nz, DevClock* clock, int parity,
+                     cudaStream_t s);
+
+}  // namespace phx

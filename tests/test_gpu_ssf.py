@@ -1,0 +1,87 @@
+"""Split-step Fourier steps (phx_step_ssf) through the C ABI against the
+oracle's run_ssf: FP64 (1e-11) and FP32 (1e-4), prime and power-of-two,
+non-square grids, potential, loss, Kerr term and per-step noise; RK4 and
+split-step steps alternating on one handle; the states it refuses."""
+import numpy as np
+import pytest
+
+from oracle import gp
+import synth
+from gpu_util import phx, get_state, rel_l2, rounded, TOL
+
+pytestmark = pytest.mark.gpu
+
+
+def params(nx, ny, **kw):
+    d = synth.base_params(nx, ny, 0.3 * nx, 0.3 * ny, g=0.3, gamma_c=0.1)
+    d.update(kw)
+    d["dt"] = min(0.45 * gp.stability_dt_max(gp.Params(**d)), 0.05)
+    return d
+
+
+def start(d, prec, seed=3, with_V=True):
+    m = phx()
+    real, cplx = (np.float64, np.complex128) if prec == 64 else (np.float32, np.complex64)
+    psi0, _, _, V = synth.random_state(1, d["ny"], d["nx"], seed, amp=0.7, reservoir=False,
+                                       smooth=True)
+    V = V if with_V else None
+    psi0, V = rounded(psi0, prec), rounded(V, prec)
+    h = m.phx_create(m.params_from_dict(d, precision=prec))
+    if V is not None:
+        m.phx_set_potential(h, np.ascontiguousarray(V, real))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, cplx))
+    return h, psi0, V
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("size", [(131, 77), (64, 48), (45, 90)])
+@pytest.mark.parametrize("noise_var", [0.0, 1e-4])
+def test_ssf_parity(prec, size, noise_var):
+    d = params(*size, noise_var=noise_var, seed=41)
+    h, psi0, V = start(d, prec)
+    phx().phx_set_time(h, 17, 0.0)
+    phx().phx_step_ssf(h, 12)
+    g_psi, _ = get_state(h, prec)
+    o_psi = gp.run_ssf(psi0, V, gp.Params(**d), 12, step0=17)
+    assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
+    s, t = phx().phx_time(h)
+    assert s == 29 and abs(t - 12 * d["dt"]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_ssf_conservative_keeps_norm_and_alternates_with_rk4(prec):
+    """gamma_c = 0: the split-step is unitary (norm kept to rounding); then
+    RK4 steps continue from the split-step state (ghost ring refilled) and
+    match the oracle doing the same."""
+    m = phx()
+    d = params(96, 70, gamma_c=0.0)
+    h, psi0, V = start(d, prec, seed=5)
+    N0, _ = m.phx_norm_energy(h)
+    m.phx_step_ssf(h, 20)
+    N1, _ = m.phx_norm_energy(h)
+    assert abs(N1 / N0 - 1) < (1e-12 if prec == 64 else 2e-5)
+    m.phx_step_n(h, 5)
+    m.phx_step_ssf(h, 3)
+    g_psi, _ = get_state(h, prec)
+    p = gp.Params(**d)
+    o = gp.run_ssf(psi0, V, p, 20)
+    o, _ = gp.run(o, None, None, V, p, 5, step0=20)
+    o = gp.run_ssf(o, V, p, 3, step0=25)
+    assert rel_l2(g_psi, o) <= TOL[prec], rel_l2(g_psi, o)
+
+
+def test_ssf_refuses_unsupported_states():
+    m = phx()
+    for kw in (dict(reservoir=True, R=0.1, gamma_r=0.2), dict(spinor=True), dict(bc_x=1),
+               dict(wigner_nu=1.0)):
+        d = params(40, 36, **kw)
+        h = m.phx_create(m.params_from_dict(d, precision=64))
+        with pytest.raises(m.PhxError) as e:
+            m.phx_step_ssf(h, 1)
+        assert e.value.status == 6, kw  # PHX_ESTATE
+    d = params(40, 36)
+    h = m.phx_create(m.params_from_dict(d, precision=64))
+    m.phx_set_drive(h, np.ones((36, 40), np.complex128))
+    with pytest.raises(m.PhxError) as e:
+        m.phx_step_ssf(h, 1)
+    assert e.value.status == 6
