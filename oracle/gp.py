@@ -307,6 +307,35 @@ def run_ssf(psi, V, p, nsteps, step0=0):
     return psi
 
 
+def run_imag(psi, V, p, nsteps):
+    """Imaginary-time propagation (named in the conclusions; no details
+    given).  Reading: t -> -i tau in the conservative part of Eq. (PULSE_psi)
+    for a scalar field without reservoir, split like run_ssf --
+    psi <- exp(-(V + g|psi|^2) dt/(2 hbar)) exp(-kappa k^2 dt/hbar) exp(-(V + g|psi|^2) dt/(2 hbar)) psi,
+    the density frozen within each local factor -- then rescaled to the norm
+    N = dV sum |psi|^2 it had at the start.  Loss, gain and noise take no part.
+    Converges to the ground state of the (spectral) Hamiltonian."""
+    psi = np.array(psi, dtype=np.complex128)
+    V = None if V is None else np.asarray(V, dtype=np.float64)
+    N0 = norm(psi, p)
+
+    def local(u):
+        ph = p.g * np.abs(u) ** 2
+        if V is not None:
+            ph = ph + V
+        return u * np.exp(-0.5 * p.dt / HBAR * ph)
+
+    kx = 2.0 * np.pi * np.fft.fftfreq(p.nx, p.dx)
+    ky = 2.0 * np.pi * np.fft.fftfreq(p.ny, p.dy)
+    K = np.exp(-p.kappa * (ky[:, None] ** 2 + kx[None, :] ** 2) * p.dt / HBAR)
+    for _ in range(nsteps):
+        psi = local(psi)
+        psi = np.stack([np.fft.ifft2(K * np.fft.fft2(psi[c])) for c in range(psi.shape[0])])
+        psi = local(psi)
+        psi = psi * np.sqrt(N0 / norm(psi, p))
+    return psi
+
+
 def run(psi, n, P, V, p, nsteps, step0=0, E=None, t0=0.0):
     """nsteps RK4 steps (with noise after each) starting at step index step0
     and time t0 (the time advances by t += dt per step, in FP64).  With
