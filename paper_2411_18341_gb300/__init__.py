@@ -79,6 +79,7 @@ _SIGS = {
     "phx_set_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_set_kfilter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64]),
     "phx_step_ssf": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "phx_step_imag": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "phx_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_step_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
@@ -269,6 +270,10 @@ def phx_set_drive(h, E_plus, E_minus=None):
 
 def phx_step_ssf(h, nsteps):
     _check(lib().phx_step_ssf(h.ptr, int(nsteps)), h.ptr)
+
+
+def phx_step_imag(h, nsteps):
+    _check(lib().phx_step_imag(h.ptr, int(nsteps)), h.ptr)
 
 
 def phx_set_kfilter(h, k_cut, order=1, every=1):

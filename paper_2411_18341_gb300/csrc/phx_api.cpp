@@ -42,6 +42,7 @@ struct phx_handle {
   bool has_E = false;
   KFilter kf;                // k-space smoothing (off unless set)
   FftPair ssf_fft;           // FFT plans of the split-step integrator (made at first use)
+  double* imag_red = nullptr;  // norm scratch of the imaginary-time steps
   DevClock* clock = nullptr;
   double* partials = nullptr;
   double* red_dev = nullptr;
@@ -115,6 +116,7 @@ void free_all(phx_handle* h) {
   if (h->E) cudaFree(h->E);
   kfilter_release(h->kf);
   fft_pair_release(h->ssf_fft);
+  if (h->imag_red) cudaFree(h->imag_red);
   if (h->clock) cudaFree(h->clock);
   if (h->partials) cudaFree(h->partials);
   if (h->red_dev) cudaFree(h->red_dev);
@@ -619,6 +621,25 @@ phx_status phx_step_ssf(phx_handle* h, int64_t nsteps) {
     h->parity ^= 1;
     h->host_step += 1;
   }
+  PHX_CK(h, launch_fill_ghosts(h->psi[h->cur], (int)(2 * h->esize), 1, h->geo, h->stream));
+  return PHX_OK;
+}
+
+phx_status phx_step_imag(phx_handle* h, int64_t nsteps) {
+  if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(h, PHX_EINVAL, "nsteps must be >= 0");
+  if (h->m.ncomp != 1 || h->m.reservoir)
+    return fail(h, PHX_ESTATE, "imaginary time needs a scalar field without reservoir");
+  if (h->p.bc_x != PHX_BC_PERIODIC || h->p.bc_y != PHX_BC_PERIODIC)
+    return fail(h, PHX_ESTATE, "imaginary time needs periodic boundaries");
+  if (nsteps == 0) return PHX_OK;
+  DeviceGuard dg(h->device);
+  const char* msg = fft_pair_setup(h->ssf_fft, h->geo, 1, h->m.precision);
+  if (msg) return fail(h, PHX_ECUDA, msg);
+  if (!h->imag_red) PHX_CK(h, cudaMalloc(&h->imag_red, imag_scratch_doubles() * sizeof(double)));
+  msg = imag_steps(h->ssf_fft, h->imag_red, h->psi[h->cur], h->geo, h->m.precision,
+                   h->has_V ? h->V : nullptr, h->p, nsteps, h->stream);
+  if (msg) return fail(h, PHX_ECUDA, msg);
   PHX_CK(h, launch_fill_ghosts(h->psi[h->cur], (int)(2 * h->esize), 1, h->geo, h->stream));
   return PHX_OK;
 }

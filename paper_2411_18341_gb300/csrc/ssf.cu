@@ -67,6 +67,95 @@ __global__ void ssf_kinetic_kernel(C* d, int nx, int ny, R dkx, R dky, R c, R sc
   }
 }
 
+// Imaginary time (t -> -i tau, conservative part): real factors
+// exp(-(g|psi|^2 + V) tau / hbar) locally and exp(-kappa k^2 tau / hbar) in
+// Fourier space.
+template <typename R, typename C>
+__global__ void imag_local_kernel(C* psi, Geometry g, const R* V, R cg, R cv) {
+  const long long sites = (long long)g.nx * g.ny;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < sites;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
+    const long long off = (long long)(j + HALO) * g.pitch + i + HALO;
+    C v = psi[off];
+    R e = cg * (v.x * v.x + v.y * v.y);
+    if (V) e += cv * V[off];
+    const R f = exp(-e);
+    v.x *= f;
+    v.y *= f;
+    psi[off] = v;
+  }
+}
+
+template <typename R, typename C>
+__global__ void imag_kinetic_kernel(C* d, int nx, int ny, R dkx, R dky, R c, R scale) {
+  const long long total = (long long)nx * ny;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / nx), i = (int)(t - (long long)j * nx);
+    const R kx = dkx * R(fft_index_ssf(i, nx)), ky = dky * R(fft_index_ssf(j, ny));
+    const R f = scale * exp(-c * (ky * ky + kx * kx));
+    C v = d[t];
+    v.x *= f;
+    v.y *= f;
+    d[t] = v;
+  }
+}
+
+constexpr int RED_BLOCKS = 512, RED_THREADS = 256;
+
+// Block partials of sum |psi|^2 (FP64, fixed grid and order: deterministic).
+template <typename C>
+__global__ void __launch_bounds__(RED_THREADS) sumsq_kernel(const C* psi, Geometry g,
+                                                             double* partials) {
+  __shared__ double sh[RED_THREADS / 32];
+  const long long sites = (long long)g.nx * g.ny;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < sites;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
+    const C v = psi[(long long)(j + HALO) * g.pitch + i + HALO];
+    acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < RED_THREADS / 32; ++w) s += sh[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+// Sum of the block partials in a fixed order (every caller the same way).
+__device__ __forceinline__ double sum_partials(const double* partials) {
+  double s = 0.0;
+  for (int b = 0; b < RED_BLOCKS; ++b) s += partials[b];
+  return s;
+}
+
+__global__ void store_target_kernel(const double* partials, double* target) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *target = sum_partials(partials);
+}
+
+// psi *= sqrt(target / sum): the norm back to its value at the start.
+template <typename R, typename C>
+__global__ void rescale_kernel(C* psi, Geometry g, const double* partials, const double* target) {
+  __shared__ R f;
+  if (threadIdx.x == 0) f = (R)sqrt(*target / sum_partials(partials));
+  __syncthreads();
+  const long long sites = (long long)g.nx * g.ny;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < sites;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
+    const long long off = (long long)(j + HALO) * g.pitch + i + HALO;
+    C v = psi[off];
+    v.x *= f;
+    v.y *= f;
+    psi[off] = v;
+  }
+}
+
 int grid_for(long long n) {
   const long long b = (n + 255) / 256;
   return (int)(b < 8192 ? (b < 1 ? 1 : b) : 8192);
@@ -95,7 +184,51 @@ const char* ssf_step_t(FftPair& fft, void* psi, const Geometry& g, const void* V
   return cudaGetLastError() == cudaSuccess ? nullptr : "split-step kernel launch failed";
 }
 
+template <typename R, typename C>
+const char* imag_steps_t(FftPair& fft, double* red, void* psi, const Geometry& g, const void* V,
+                         const phx_params& p, long long nsteps, cudaStream_t s) {
+  C* ps = static_cast<C*>(psi);
+  const R* v = static_cast<const R*>(V);
+  const int blocks = grid_for((long long)g.nx * g.ny);
+  const int prec = sizeof(R) == 8 ? 64 : 32;
+  const double pi = 3.14159265358979323846;
+  const R cg = (R)(p.g * 0.5 * p.dt / HBAR), cv = (R)(0.5 * p.dt / HBAR);
+  const R ck = (R)(p.hbar2_over_2m * p.dt / HBAR);
+  const R dkx = (R)(2.0 * pi / p.lx), dky = (R)(2.0 * pi / p.ly);
+  const R scale = (R)(1.0 / ((double)p.nx * p.ny));
+  double* partials = red;
+  double* target = red + RED_BLOCKS;
+  sumsq_kernel<C><<<RED_BLOCKS, RED_THREADS, 0, s>>>(ps, g, partials);
+  store_target_kernel<<<1, 32, 0, s>>>(partials, target);
+  count_launch(2);
+  for (long long k = 0; k < nsteps; ++k) {
+    imag_local_kernel<R, C><<<blocks, 256, 0, s>>>(ps, g, v, cg, cv);
+    count_launch();
+    const char* msg = fft_transform(fft, psi, g, prec, true, s);
+    if (msg) return msg;
+    imag_kinetic_kernel<R, C><<<blocks, 256, 0, s>>>(static_cast<C*>(fft.scratch), g.nx, g.ny,
+                                                     dkx, dky, ck, scale);
+    count_launch();
+    msg = fft_transform(fft, psi, g, prec, false, s);
+    if (msg) return msg;
+    imag_local_kernel<R, C><<<blocks, 256, 0, s>>>(ps, g, v, cg, cv);
+    sumsq_kernel<C><<<RED_BLOCKS, RED_THREADS, 0, s>>>(ps, g, partials);
+    rescale_kernel<R, C><<<blocks, 256, 0, s>>>(ps, g, partials, target);
+    count_launch(3);
+  }
+  return cudaGetLastError() == cudaSuccess ? nullptr : "imaginary-time kernel launch failed";
+}
+
 }  // namespace
+
+size_t imag_scratch_doubles() { return RED_BLOCKS + 1; }
+
+const char* imag_steps(FftPair& fft, double* red, void* psi, const Geometry& g, int precision,
+                       const void* V, const phx_params& p, long long nsteps, cudaStream_t s) {
+  if (precision == 64)
+    return imag_steps_t<double, double2>(fft, red, psi, g, V, p, nsteps, s);
+  return imag_steps_t<float, float2>(fft, red, psi, g, V, p, nsteps, s);
+}
 
 SsfCoeffs ssf_coeffs(const phx_params& p) {
   SsfCoeffs k;

@@ -27,4 +27,11 @@ const char* ssf_step(FftPair& fft, void* psi, const Geometry& g, int precision, 
                      const SsfCoeffs& k, const NoiseKey& nz, DevClock* clock, int parity,
                      cudaStream_t s);
 
+// Imaginary-time split-step steps with the norm kept at its value at the
+// start (the ground state of the conservative scalar Hamiltonian); red is
+// device scratch of imag_scratch_doubles() doubles.  The clock does not move.
+size_t imag_scratch_doubles();
+const char* imag_steps(FftPair& fft, double* red, void* psi, const Geometry& g, int precision,
+                       const void* V, const phx_params& p, long long nsteps, cudaStream_t s);
+
 }  // namespace phx
