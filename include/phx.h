@@ -123,6 +123,24 @@ phx_status phx_stability_dt(const phx_params* p, double* dt_max);
  * ENOMEM / ECUDA on allocation failure.  *out is NULL on error. */
 phx_status phx_create(const phx_params* p, phx_handle** out);
 
+/* Bytes of the five state buffers a handle with parameters p holds, for
+ * callers that own the device memory (a caching allocator, a memory pool):
+ * sizes[0], sizes[1] = psi (two buffers, ncomp padded complex planes each),
+ * sizes[2], sizes[3] = n, sizes[4] = P (0 without reservoir).  The padded
+ * layout carries a ghost ring; use phx_set_state / phx_get_state to move
+ * dense arrays in and out.  Host-only; EINVAL on bad parameters. */
+phx_status phx_buffer_sizes(const phx_params* p, size_t sizes[5]);
+
+/* As phx_create, but the state buffers are the caller's device memory:
+ * buffers[i] of at least sizes[i] bytes (phx_buffer_sizes; entries of size 0
+ * are ignored), 256-byte aligned, device memory of the current device.  The
+ * handle zeroes them, uses them and never frees them: they must outlive it.
+ * The potential, drive, FFT scratch and small work arrays are still
+ * allocated by the handle.  EINVAL: a NULL, misaligned or non-device buffer;
+ * otherwise as phx_create. */
+phx_status phx_create_with_buffers(const phx_params* p, void* const buffers[5],
+                                   phx_handle** out);
+
 /* Copy the pump P_+ (and P_-; NULL means P_- = P_+) into the handle
  * (Eq. PULSE_res).  ESTATE if the handle has no reservoir. */
 phx_status phx_set_pump(phx_handle* h, const void* P_plus, const void* P_minus,

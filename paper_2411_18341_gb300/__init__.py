@@ -74,6 +74,9 @@ _SIGS = {
     "phx_params_init": (ctypes.c_int, [ctypes.POINTER(phx_params)]),
     "phx_stability_dt": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.POINTER(ctypes.c_double)]),
     "phx_create": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.POINTER(ctypes.c_void_p)]),
+    "phx_buffer_sizes": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.POINTER(ctypes.c_size_t)]),
+    "phx_create_with_buffers": (ctypes.c_int, [ctypes.POINTER(phx_params), ctypes.POINTER(ctypes.c_void_p),
+                                               ctypes.POINTER(ctypes.c_void_p)]),
     "phx_set_pump": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_set_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -241,6 +244,24 @@ def phx_create(p):
     out = ctypes.c_void_p()
     _check(lib().phx_create(ctypes.byref(p), ctypes.byref(out)))
     return Handle(out, p)
+
+
+def phx_buffer_sizes(p):
+    """Bytes of the five state buffers (psi 0/1, n 0/1, P) for params p."""
+    out = (ctypes.c_size_t * 5)()
+    _check(lib().phx_buffer_sizes(ctypes.byref(p), out))
+    return [int(v) for v in out]
+
+
+def phx_create_with_buffers(p, buffers):
+    """Handle on caller-owned device buffers (five CUDA tensors or None for
+    the zero-size entries); the tensors must outlive the handle."""
+    ptrs = (ctypes.c_void_p * 5)(*[None if b is None else b.data_ptr() for b in buffers])
+    out = ctypes.c_void_p()
+    _check(lib().phx_create_with_buffers(ctypes.byref(p), ptrs, ctypes.byref(out)))
+    h = Handle(out, p)
+    h.buffers = list(buffers)  # keep the tensors alive with the handle
+    return h
 
 
 def phx_set_pump(h, P_plus, P_minus=None):

@@ -37,6 +37,7 @@ struct phx_handle {
   long long P_stride = 0;    // elements between P_+ and P_- planes (0 = shared)
   void* V = nullptr;
   bool has_V = false;
+  bool owns_state = true;    // psi, n, P allocated here (false: the caller's buffers)
   void* E = nullptr;         // coherent drive amplitude: Re, Im plane per component
   long long E_stride = 0;    // elements between the E_+ and E_- plane pairs (0 = shared)
   bool has_E = false;
@@ -107,11 +108,13 @@ void free_all(phx_handle* h) {
   cudaGetDevice(&prev);
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (int b = 0; b < 2; ++b) {
-    if (h->psi[b]) cudaFree(h->psi[b]);
-    if (h->n[b]) cudaFree(h->n[b]);
+  if (h->owns_state) {
+    for (int b = 0; b < 2; ++b) {
+      if (h->psi[b]) cudaFree(h->psi[b]);
+      if (h->n[b]) cudaFree(h->n[b]);
+    }
+    if (h->P) cudaFree(h->P);
   }
-  if (h->P) cudaFree(h->P);
   if (h->V) cudaFree(h->V);
   if (h->E) cudaFree(h->E);
   kfilter_release(h->kf);
@@ -306,6 +309,16 @@ struct DeviceGuard {
   }
 };
 
+// Bytes of the five state buffers (psi 0/1, n 0/1, P) for parameters p.
+void state_sizes(const phx_params& p, size_t sizes[5]) {
+  const Geometry g = padded_geometry(p);
+  const size_t es = p.precision == 32 ? 4 : 8, nc = p.spinor ? 2 : 1;
+  sizes[0] = sizes[1] = nc * (size_t)g.plane * 2 * es;
+  sizes[2] = sizes[3] = sizes[4] = p.reservoir ? nc * (size_t)g.plane * es : 0;
+}
+
+phx_status create_impl(const phx_params* p, void* const* ext, phx_handle** out);
+
 }  // namespace
 
 extern "C" {
@@ -331,6 +344,51 @@ phx_status phx_stability_dt(const phx_params* p, double* dt_max) {
 }
 
 phx_status phx_create(const phx_params* p, phx_handle** out) {
+  return create_impl(p, nullptr, out);
+}
+
+phx_status phx_buffer_sizes(const phx_params* p, size_t sizes[5]) {
+  if (!sizes) return fail(nullptr, PHX_EINVAL, "sizes is NULL");
+  double dtmax = 0;
+  phx_status st = validate(p, &dtmax);
+  if (st != PHX_OK) return st;
+  state_sizes(*p, sizes);
+  return PHX_OK;
+}
+
+phx_status phx_create_with_buffers(const phx_params* p, void* const buffers[5],
+                                   phx_handle** out) {
+  if (!out) return fail(nullptr, PHX_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!buffers) return fail(nullptr, PHX_EINVAL, "buffers is NULL");
+  double dtmax = 0;
+  phx_status st = validate(p, &dtmax);
+  if (st != PHX_OK) return st;
+  size_t sizes[5];
+  state_sizes(*p, sizes);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, PHX_ENODEV, "no CUDA device");
+  for (int i = 0; i < 5; ++i) {
+    if (!sizes[i]) continue;
+    if (!buffers[i]) return fail(nullptr, PHX_EINVAL, "buffers[" + std::to_string(i) + "] is NULL");
+    if (reinterpret_cast<uintptr_t>(buffers[i]) % 256)
+      return fail(nullptr, PHX_EINVAL, "buffers[" + std::to_string(i) + "] is not 256-byte aligned");
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, buffers[i]) != cudaSuccess || a.type != cudaMemoryTypeDevice ||
+        a.device != dev) {
+      cudaGetLastError();
+      return fail(nullptr, PHX_EINVAL,
+                  "buffers[" + std::to_string(i) + "] is not device memory of the current device");
+    }
+  }
+  return create_impl(p, buffers, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+phx_status create_impl(const phx_params* p, void* const* ext, phx_handle** out) {
   if (!out) return fail(nullptr, PHX_EINVAL, "out is NULL");
   *out = nullptr;
   double dtmax = 0;
@@ -365,6 +423,7 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
   h->m.tetm = (p->spinor && p->delta_lt != 0.0) ? 1 : 0;
   h->esize = p->precision == 32 ? 4 : 8;
   h->geo = padded_geometry(*p);
+  h->owns_state = ext == nullptr;
   const Geometry& g = h->geo;
 
   auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
@@ -373,15 +432,21 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
     if (r != cudaSuccess) return r;
     return cudaMemsetAsync(*ptr, 0, bytes, h->stream);
   };
+  // a state buffer: the caller's (zeroed here) or a new allocation
+  auto state = [&](void** ptr, int idx, size_t bytes) -> cudaError_t {
+    if (!ext) return alloc(ptr, bytes);
+    *ptr = ext[idx];
+    return cudaMemsetAsync(*ptr, 0, bytes, h->stream);
+  };
   const int nc = h->m.ncomp;
   const size_t cplx = 2 * h->esize, real = h->esize;
   cudaError_t ce = cudaSuccess;
   for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
-    ce = alloc(&h->psi[b], (size_t)nc * g.plane * cplx);
-    if (ce == cudaSuccess && h->m.reservoir) ce = alloc(&h->n[b], (size_t)nc * g.plane * real);
+    ce = state(&h->psi[b], b, (size_t)nc * g.plane * cplx);
+    if (ce == cudaSuccess && h->m.reservoir) ce = state(&h->n[b], 2 + b, (size_t)nc * g.plane * real);
   }
   if (ce == cudaSuccess && h->m.reservoir) {
-    ce = alloc(&h->P, (size_t)nc * g.plane * real);
+    ce = state(&h->P, 4, (size_t)nc * g.plane * real);
     h->P_stride = (nc == 2) ? g.plane : 0;
   }
   if (ce == cudaSuccess) ce = alloc((void**)&h->clock, sizeof(DevClock));
@@ -409,6 +474,10 @@ phx_status phx_create(const phx_params* p, phx_handle** out) {
   *out = h;
   return PHX_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 phx_status phx_set_pump(phx_handle* h, const void* P_plus, const void* P_minus,
                         int on_device) {

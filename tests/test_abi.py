@@ -116,3 +116,21 @@ def test_fno_invalid_config_rejected_before_device(phx):
     out = ctypes.c_void_p()
     assert phx.lib().phx_fno_create(ctypes.byref(c), ctypes.byref(out)) == 1  # PHX_EINVAL
     assert not out.value
+
+
+def test_buffer_sizes_are_the_padded_layout(phx):
+    """Caller-owned state buffers: psi is ncomp planes of (ny + 8) rows x
+    pitch complex elements, pitch = nx + 8 rounded up to 32; n and P are
+    real planes, absent without reservoir (host-only call)."""
+    for kw, es, nc, res in [(dict(nx=100, ny=37, lx=10.0, ly=3.7), 4, 1, False),
+                            (dict(nx=64, ny=64, lx=5.0, ly=5.0, precision=64, reservoir=1), 8, 1, True),
+                            (dict(nx=33, ny=9, lx=3.3, ly=0.9, spinor=1, reservoir=1), 4, 2, True)]:
+        kw = dict(kw, dt=1e-4)
+        sizes = phx.phx_buffer_sizes(phx.phx_params_init(**kw))
+        pitch = -(-(kw["nx"] + 8) // 32) * 32
+        plane = pitch * (kw["ny"] + 8)
+        assert sizes[0] == sizes[1] == nc * plane * 2 * es
+        assert sizes[2] == sizes[3] == sizes[4] == (nc * plane * es if res else 0)
+    with pytest.raises(phx.PhxError) as e:
+        phx.phx_buffer_sizes(phx.phx_params_init(nx=0))
+    assert e.value.status == 1

@@ -375,3 +375,39 @@ def test_fp32_spinor_shared_pump_and_noise(tile):
     o_psi, o_n = gp.run(psi0, n0, Pboth, None, gp.Params(**d), 6)
     assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
     assert rel_l2(g_n, o_n) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_caller_owned_state_buffers(prec):
+    """phx_create_with_buffers on torch device tensors gives bit-identical
+    steps to a handle that allocates its own state; bad buffers are refused."""
+    import torch
+    m = phx()
+    d = model("reservoir", 97, 66)
+    psi0, n0, P, V = synth.random_state(1, 66, 97, 3, amp=0.7, smooth=True)
+    psi0, n0, P, V = (rounded(x, prec) for x in (psi0, n0, P, V))
+    p = m.params_from_dict(d, precision=prec)
+    sizes = m.phx_buffer_sizes(p)
+    bufs = [torch.empty(s, dtype=torch.uint8, device="cuda") if s else None for s in sizes]
+    real, cplx = types(prec)
+    hs = []
+    for h in (m.phx_create_with_buffers(p, bufs), m.phx_create(p)):
+        m.phx_set_pump(h, np.ascontiguousarray(P[0], real))
+        m.phx_set_potential(h, np.ascontiguousarray(V, real))
+        m.phx_set_state(h, np.ascontiguousarray(psi0, cplx), np.ascontiguousarray(n0, real))
+        m.phx_step_n(h, 13)
+        hs.append(get_state(h, prec))
+    assert np.array_equal(hs[0][0], hs[1][0]) and np.array_equal(hs[0][1], hs[1][1])
+    o_psi, _ = gp.run(psi0, n0, P, V, gp.Params(**d), 13)
+    assert rel_l2(hs[0][0], o_psi) <= TOL[prec]
+    # misaligned and host buffers are refused
+    bad = list(bufs)
+    bad[0] = bufs[0][1:]
+    with pytest.raises(m.PhxError) as e:
+        m.phx_create_with_buffers(p, bad)
+    assert e.value.status == 1
+    bad = list(bufs)
+    bad[2] = torch.empty(sizes[2], dtype=torch.uint8).pin_memory()
+    with pytest.raises(m.PhxError) as e:
+        m.phx_create_with_buffers(p, bad)
+    assert e.value.status == 1
