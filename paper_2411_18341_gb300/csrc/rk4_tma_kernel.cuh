@@ -285,9 +285,13 @@ rk4_f32_tma(const TileArgs ta) {
     const NoiseKey nz = ONE ? ta.one.noise : I->noise;
     advance(cc, t + (int)gridDim.x);
     const float2 ax2 = f2(q.ax, q.ax), ay2 = f2(q.ay, q.ay);
-    const float cg = q.g, cgr = q.gr, cih = q.inv_hbar;
-    const float hR = q.half_R, hgc = q.half_gc, cR = q.R_;
-    const float cgam = q.gamma_r, dt = q.dt;
+    // real coefficients as pairs: the thread's two columns go through the
+    // real-valued terms (density, local term, gain, reservoir) together
+    const float2 cg2 = f2(q.g, q.g), cgr2 = f2(q.gr, q.gr), cih2 = f2(q.inv_hbar, q.inv_hbar);
+    const float2 hR2 = f2(q.half_R, q.half_R), nhgc2 = f2(-q.half_gc, -q.half_gc);
+    const float2 ncR2 = f2(-q.R_, -q.R_), ncgam2 = f2(-q.gamma_r, -q.gamma_r);
+    const float2 a02 = f2(q.a0, q.a0);
+    const float dt = q.dt;
     const float dt6 = dt / 6.0f;
     const int xp = kx * C::TX;
     const int foff = xp & 3;
@@ -298,9 +302,10 @@ rk4_f32_tma(const TileArgs ta) {
     const float* Eib = DRV ? f_buf(b, 1) : nullptr;
     const float* Vb = POT ? f_buf(b, MODE != 0 ? 2 : 0) : nullptr;
 
-    // Registers: psi0, current stage value, accumulator (+ reservoir).
+    // Registers: psi0, current stage value, accumulator (+ reservoir).  Real
+    // fields hold the micro-tile row's two columns as one pair (.x, .y).
     float2 p0[MR][2], yc[MR][2], acc[MR][2];
-    float n0[MR][2], nc[MR][2], na[MR][2], Pv[MR][2], Vv[MR][2], Er[MR][2], Ei[MR][2];
+    float2 n0[MR], nc[MR], na[MR], Pv[MR], Vv[MR], Er[MR], Ei[MR];
     bool ins[MR][2];
     const int gx0 = xp - HALO + c0;        // domain column of my first column
     const int gy0 = ky * C::TY - 3 + r0;   // domain row of my first row
@@ -313,19 +318,21 @@ rk4_f32_tma(const TileArgs ta) {
       for (int i = 0; i < 2; ++i) {
         yc[j][i] = p0[j][i];
         acc[j][i] = f2(0.f, 0.f);
-        na[j][i] = 0.f;
         const int gx = gx0 + i, gy = gy0 + j;
         ins[j][i] = PER || ((g.bc_x == BC_PERIODIC || (gx >= 0 && gx < g.nx)) &&
                             (g.bc_y == BC_PERIODIC || (gy >= 0 && gy < g.ny)));
-        const int fi = (r0 + j) * C::FW + foff + c0 + i;
-        n0[j][i] = RES ? Nb[fi] : 0.f;
-        nc[j][i] = n0[j][i];
-        Pv[j][i] = RES ? Pb[fi] : 0.f;
-        Er[j][i] = DRV ? Erb[fi] : 0.f;
-        Ei[j][i] = DRV ? Eib[fi] : 0.f;
-        // the stencil's diagonal a0 rides with the local potential
-        Vv[j][i] = POT ? fmaf(Vb[fi], cih, q.a0) : q.a0;
       }
+      // foff + c0 is even: the pair of a row is one 8-byte load
+      const int fi = (r0 + j) * C::FW + foff + c0;
+      auto ld2 = [&](const float* b) { return *reinterpret_cast<const float2*>(&b[fi]); };
+      n0[j] = RES ? ld2(Nb) : f2(0.f, 0.f);
+      nc[j] = n0[j];
+      na[j] = f2(0.f, 0.f);
+      Pv[j] = RES ? ld2(Pb) : f2(0.f, 0.f);
+      Er[j] = DRV ? ld2(Erb) : f2(0.f, 0.f);
+      Ei[j] = DRV ? ld2(Eib) : f2(0.f, 0.f);
+      // the stencil's diagonal a0 rides with the local potential
+      Vv[j] = POT ? __ffma2_rn(ld2(Vb), cih2, a02) : a02;
     }
 
 #pragma unroll
@@ -357,9 +364,11 @@ rk4_f32_tma(const TileArgs ta) {
         }
       }
       float2 ny[MR][2];
-      float nn[MR][2];
+      float2 nn[MR];
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
+        float2 lap[2];
+        float2 dens;  // |psi|^2 of the row's two sites
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           const float2 Cc = yc[j][i];
@@ -369,30 +378,37 @@ rk4_f32_tma(const TileArgs ta) {
           const float2 N = (j < MR - 1) ? yc[j + 1][i] : (i ? f2(bv.z, bv.w) : f2(bv.x, bv.y));
           // H/hbar: off-diagonal stencil ax (E+W) + ay (N+S), plus the local
           // term (a0 + V/hbar + g|psi|^2 + g_r n) psi
-          float2 lap = __fmul2_rn(ay2, __fadd2_rn(N, S));
-          lap = __ffma2_rn(ax2, __fadd2_rn(E, W), lap);
-          const float dens = fmaf(Cc.x, Cc.x, Cc.y * Cc.y);
-          const float ncur = nc[j][i];
-          float loc = fmaf(cg, dens, Vv[j][i]);
-          if (RES) loc = fmaf(cgr, ncur, loc);
-          float2 H = __ffma2_rn(f2(loc, loc), Cc, lap);
+          lap[i] = __fmul2_rn(ay2, __fadd2_rn(N, S));
+          lap[i] = __ffma2_rn(ax2, __fadd2_rn(E, W), lap[i]);
+          const float d = fmaf(Cc.x, Cc.x, Cc.y * Cc.y);
+          if (i) dens.y = d; else dens.x = d;
+        }
+        float2 loc = __ffma2_rn(cg2, dens, Vv[j]);
+        if (RES) loc = __ffma2_rn(cgr2, nc[j], loc);
+        const float2 G = RES ? __ffma2_rn(hR2, nc[j], nhgc2) : nhgc2;  // (R n - gamma_c)/2
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const float2 Cc = yc[j][i];
+          const float li = i ? loc.y : loc.x, Gi = i ? G.y : G.x;
+          float2 H = __ffma2_rn(f2(li, li), Cc, lap[i]);
           if (DRV) {  // + E exp(-i omega t_s) / hbar
-            H = __ffma2_rn(f2(Er[j][i], Er[j][i]), dph, H);
-            H = __ffma2_rn(f2(-Ei[j][i], Ei[j][i]), f2(dph.y, dph.x), H);
+            const float er = i ? Er[j].y : Er[j].x, ei = i ? Ei[j].y : Ei[j].x;
+            H = __ffma2_rn(f2(er, er), dph, H);
+            H = __ffma2_rn(f2(-ei, ei), f2(dph.y, dph.x), H);
           }
-          const float G = RES ? fmaf(hR, ncur, -hgc) : -hgc;
           float2 K;
-          K.x = fmaf(G, Cc.x, H.y);
-          K.y = fmaf(G, Cc.y, -H.x);
+          K.x = fmaf(Gi, Cc.x, H.y);
+          K.y = fmaf(Gi, Cc.y, -H.x);
           acc[j][i] = s == 0 ? K : __ffma2_rn(w2, K, acc[j][i]);
-          float Kn = 0.f;
-          if (RES) {
-            Kn = fmaf(-fmaf(cR, dens, cgam), ncur, Pv[j][i]);
-            na[j][i] = s == 0 ? Kn : fmaf(w, Kn, na[j][i]);
-          }
           ny[j][i] = __ffma2_rn(cs2, K, p0[j][i]);
           if (!PER && !ins[j][i]) ny[j][i] = f2(0.f, 0.f);
-          nn[j][i] = RES ? fmaf(cs, Kn, n0[j][i]) : 0.f;
+        }
+        if (RES) {  // Kn = P - (gamma_r + R|psi|^2) n for both sites
+          const float2 Kn = __ffma2_rn(__ffma2_rn(ncR2, dens, ncgam2), nc[j], Pv[j]);
+          na[j] = s == 0 ? Kn : __ffma2_rn(w2, Kn, na[j]);
+          nn[j] = __ffma2_rn(cs2, Kn, n0[j]);
+        } else {
+          nn[j] = f2(0.f, 0.f);
         }
       }
       if (s < 3) {
@@ -400,8 +416,7 @@ rk4_f32_tma(const TileArgs ta) {
         for (int j = 0; j < MR; ++j) {
           yc[j][0] = ny[j][0];
           yc[j][1] = ny[j][1];
-          nc[j][0] = nn[j][0];
-          nc[j][1] = nn[j][1];
+          nc[j] = nn[j];
           // only the micro-tile's first and last rows are read by other warps
           if (j == 0 || j == MR - 1)
             *reinterpret_cast<float4*>(&dst[(r0 + j + 1) * C::PW + c0 + 2]) =
@@ -414,14 +429,13 @@ rk4_f32_tma(const TileArgs ta) {
     // psi' = psi0 + (K1 + 2K2 + 2K3 + K4) dt/6, written to the output tile
     const float2 d62 = f2(dt6, dt6);
     float2 o[MR][2];
-    float on[MR][2];
+    float2 on[MR];
 #pragma unroll
-    for (int j = 0; j < MR; ++j)
+    for (int j = 0; j < MR; ++j) {
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        o[j][i] = __ffma2_rn(d62, acc[j][i], p0[j][i]);
-        on[j][i] = fmaf(dt6, na[j][i], n0[j][i]);
-      }
+      for (int i = 0; i < 2; ++i) o[j][i] = __ffma2_rn(d62, acc[j][i], p0[j][i]);
+      on[j] = __ffma2_rn(d62, na[j], n0[j]);
+    }
     if (nz.on) {  // grid-uniform branch: the generator is not issued when off
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
@@ -433,7 +447,7 @@ rk4_f32_tma(const TileArgs ta) {
                                            (gx % g.nx + g.nx) % g.nx);
           float2 xi, unused;
           const float sc = nz.twa ? nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var,
-                                                    RES ? n0[j][i] : 0.f)
+                                                    RES ? (i ? n0[j].y : n0[j].x) : 0.f)
                                   : nz.scale;
           nz_site(nz.seed, nz.instance, step, site, sc, xi, unused, false);
           o[j][i].x = o[j][i].x + xi.x;
@@ -458,13 +472,13 @@ rk4_f32_tma(const TileArgs ta) {
         if (lo && hi) {
           *reinterpret_cast<float4*>(psi_out + roff) =
               make_float4(o[j][0].x, o[j][0].y, o[j][1].x, o[j][1].y);
-          if (RES) *reinterpret_cast<float2*>(n_out + roff) = f2(on[j][0], on[j][1]);
+          if (RES) *reinterpret_cast<float2*>(n_out + roff) = on[j];
         } else if (lo) {
           psi_out[roff] = o[j][0];
-          if (RES) n_out[roff] = on[j][0];
+          if (RES) n_out[roff] = on[j].x;
         } else if (hi) {
           psi_out[roff + 1] = o[j][1];
-          if (RES) n_out[roff + 1] = on[j][1];
+          if (RES) n_out[roff + 1] = on[j].y;
         }
       }
     } else {
@@ -485,13 +499,13 @@ rk4_f32_tma(const TileArgs ta) {
         if (ok[0] && ok[1] && !edge_x && !edge_y) {
           *reinterpret_cast<float4*>(psi_out + roff) =
               make_float4(o[j][0].x, o[j][0].y, o[j][1].x, o[j][1].y);
-          if (RES) *reinterpret_cast<float2*>(n_out + roff) = f2(on[j][0], on[j][1]);
+          if (RES) *reinterpret_cast<float2*>(n_out + roff) = on[j];
         } else {
 #pragma unroll
           for (int i = 0; i < 2; ++i) {
             if (!ok[i]) continue;
             store_with_ghosts(psi_out, g, gx0 + i, gy, o[j][i]);
-            if (RES) store_with_ghosts(n_out, g, gx0 + i, gy, on[j][i]);
+            if (RES) store_with_ghosts(n_out, g, gx0 + i, gy, i ? on[j].y : on[j].x);
           }
         }
       }
