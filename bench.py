@@ -458,7 +458,9 @@ def run_ensemble(args, world, rank, local, pg):
                      "traffic": recorded_traffic(args.workload, 32, phx.phx_batch_tile(b)),
                      "kernel": "rk4_f32_tma (persistent, all members per launch)",
                      "algorithmic_bytes_per_site": 28, "avg_launch_us": kern_s * 1e6,
-                     "peak_source": pk_kind},
+                     "peak_source": pk_kind,
+                     **({"note": "per-site Philox + Box-Muller noise every step: the kernel is "
+                                 "bound by instruction issue, not by HBM"} if twa else {})},
         "clocks": clk,
         "energy": energy(clk, ms * 1e-3, sites * rk4_steps),
     }
@@ -628,6 +630,11 @@ def main():
                 "algorithmic_bytes_per_site": bps,
                 "avg_launch_us": kern_s * 1e6,
                 "peak_source": pk_kind}
+        if d.get("noise_var", 0) > 0 or d.get("wigner_nu", 0) > 0:
+            roof["note"] = ("per-site Philox + Box-Muller noise every step: the kernel is bound by "
+                            "instruction issue, not by HBM")
+        elif sites * bps < 129e6:
+            roof["note"] = "state smaller than L2: bound by instruction issue and latency, not by HBM"
     line = {
         "metric": "RK4 site-updates/s",
         "value": value, "unit": "site-updates/s", "n_gpus": world,
