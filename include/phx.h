@@ -21,7 +21,10 @@
  *   Noise dW: after each deterministic step psi_c += xi_c with xi a complex
  *   Gaussian of E|xi|^2 = noise_var from Philox4x32-10 keyed by
  *   (seed, step, instance, site) (Salmon et al., SC'11), so runs and
- *   resumes are reproducible bit for bit.
+ *   resumes are reproducible bit for bit: key = seed, counter = (c, instance,
+ *   step lo, step hi) with c = site for two components (words 0,1 -> xi_+,
+ *   2,3 -> xi_-) and c = site >> 1 for one component (words 0,1 -> the even,
+ *   2,3 -> the odd site of the pair); site = j*nx + i.
  *   Truncated-Wigner mode (Sec. V, Example 4; wigner_nu > 0): the variance
  *   becomes E|xi_c|^2 = noise_var + nu (R n_c + gamma_c) dt / (2 dV) per
  *   site, n_c taken at the start of the step and dV = dx dy, and the Kerr,

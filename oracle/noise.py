@@ -15,8 +15,10 @@ step can be regenerated independently:
   words), permutes and XORs with the round key; the key is bumped by the two
   published Weyl constants between rounds.
 * key = (seed lo 32 bits, seed hi 32 bits);
-  counter = (site = j*nx + i, instance, step lo 32 bits, step hi 32 bits).
-  Words (w0, w1) feed component + (or the scalar field), (w2, w3) component -.
+  two components: counter = (site = j*nx + i, instance, step lo 32 bits,
+  step hi 32 bits), words (w0, w1) feed component +, (w2, w3) component -;
+  one component: counter word 0 = site >> 1, words (w0, w1) feed the even and
+  (w2, w3) the odd site of the pair (one Philox call per two sites).
 * uniform: u = (2*(w >> 9) + 1) * 2**-24, exact in FP32, u in (0, 1).
 * Box-Muller: rho = sqrt(-2 ln u1), theta = 2 pi u2, z1 = rho cos theta,
   z2 = rho sin theta, xi = s*(z1 + i z2) with s = float32(sqrt(var/2)) so that
@@ -158,20 +160,34 @@ def noise_scale(var):
     return F32(np.sqrt(np.float64(var) / 2.0))
 
 
+def _words(sites, ncomp, instance, step, seed):
+    """Philox words of each site: two components use the counter `site` and
+    words (w0, w1) for xi_+ and (w2, w3) for xi_-; one component uses the
+    counter site >> 1 and words (w0, w1) for the even and (w2, w3) for the
+    odd site of the pair, so that one Philox call serves two sites."""
+    sites = np.asarray(sites).astype(np.uint64)
+    ctr = (sites if ncomp == 2 else sites >> np.uint64(1)).astype(U32)
+    w0, w1, w2, w3 = philox4x32_10(ctr, U32(instance), U32(step & 0xFFFFFFFF),
+                                   U32(step >> 32), seed & 0xFFFFFFFF, seed >> 32)
+    if ncomp == 2:
+        return (w0, w1), (w2, w3)
+    odd = (sites & np.uint64(1)).astype(bool)
+    return (np.where(odd, w2, w0), np.where(odd, w3, w1)), None
+
+
 def noise_field(seed, step, instance, ncomp, ny, nx, var):
     """Noise xi_c(site) added after RK4 step `step` (0-based): float32 arrays
     re, im of shape (ncomp, ny, nx)."""
     seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     step = int(step) & 0xFFFFFFFFFFFFFFFF
-    site = np.arange(ny * nx, dtype=np.uint64).astype(U32).reshape(ny, nx)
-    w0, w1, w2, w3 = philox4x32_10(site, U32(instance), U32(step & 0xFFFFFFFF),
-                                   U32(step >> 32), seed & 0xFFFFFFFF, seed >> 32)
+    site = np.arange(ny * nx, dtype=np.uint64).reshape(ny, nx)
+    a, b = _words(site, ncomp, instance, step, seed)
     sc = noise_scale(var)
     re = np.empty((ncomp, ny, nx), F32)
     im = np.empty((ncomp, ny, nx), F32)
-    re[0], im[0] = box_muller_f32(w0, w1, sc)
+    re[0], im[0] = box_muller_f32(a[0], a[1], sc)
     if ncomp == 2:
-        re[1], im[1] = box_muller_f32(w2, w3, sc)
+        re[1], im[1] = box_muller_f32(b[0], b[1], sc)
     return re, im
 
 
@@ -180,15 +196,14 @@ def noise_field_scaled(seed, step, instance, ncomp, ny, nx, scale):
     shape (ncomp, ny, nx) (the per-quadrature standard deviation)."""
     seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     step = int(step) & 0xFFFFFFFFFFFFFFFF
-    site = np.arange(ny * nx, dtype=np.uint64).astype(U32).reshape(ny, nx)
-    w0, w1, w2, w3 = philox4x32_10(site, U32(instance), U32(step & 0xFFFFFFFF),
-                                   U32(step >> 32), seed & 0xFFFFFFFF, seed >> 32)
+    site = np.arange(ny * nx, dtype=np.uint64).reshape(ny, nx)
+    a, b = _words(site, ncomp, instance, step, seed)
     scale = np.asarray(scale, F32)
     re = np.empty((ncomp, ny, nx), F32)
     im = np.empty((ncomp, ny, nx), F32)
-    re[0], im[0] = box_muller_f32(w0, w1, scale[0])
+    re[0], im[0] = box_muller_f32(a[0], a[1], scale[0])
     if ncomp == 2:
-        re[1], im[1] = box_muller_f32(w2, w3, scale[1])
+        re[1], im[1] = box_muller_f32(b[0], b[1], scale[1])
     return re, im
 
 
@@ -197,15 +212,14 @@ def noise_at_scaled(seed, step, instance, sites, ncomp, scale):
     shape (ncomp,) + sites.shape."""
     seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     step = int(step) & 0xFFFFFFFFFFFFFFFF
-    sites = np.asarray(sites).astype(np.uint64).astype(U32)
-    w0, w1, w2, w3 = philox4x32_10(sites, U32(instance), U32(step & 0xFFFFFFFF),
-                                   U32(step >> 32), seed & 0xFFFFFFFF, seed >> 32)
+    sites = np.asarray(sites).astype(np.uint64)
+    a, b = _words(sites, ncomp, instance, step, seed)
     scale = np.asarray(scale, F32).reshape((ncomp,) + sites.shape)
     re = np.empty((ncomp,) + sites.shape, F32)
     im = np.empty((ncomp,) + sites.shape, F32)
-    re[0], im[0] = box_muller_f32(w0, w1, scale[0])
+    re[0], im[0] = box_muller_f32(a[0], a[1], scale[0])
     if ncomp == 2:
-        re[1], im[1] = box_muller_f32(w2, w3, scale[1])
+        re[1], im[1] = box_muller_f32(b[0], b[1], scale[1])
     return re, im
 
 
@@ -214,13 +228,12 @@ def noise_at(seed, step, instance, sites, ncomp, var):
     re, im of shape (ncomp,) + sites.shape."""
     seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     step = int(step) & 0xFFFFFFFFFFFFFFFF
-    sites = np.asarray(sites).astype(np.uint64).astype(U32)
-    w0, w1, w2, w3 = philox4x32_10(sites, U32(instance), U32(step & 0xFFFFFFFF),
-                                   U32(step >> 32), seed & 0xFFFFFFFF, seed >> 32)
+    sites = np.asarray(sites).astype(np.uint64)
+    a, b = _words(sites, ncomp, instance, step, seed)
     sc = noise_scale(var)
     re = np.empty((ncomp,) + sites.shape, F32)
     im = np.empty((ncomp,) + sites.shape, F32)
-    re[0], im[0] = box_muller_f32(w0, w1, sc)
+    re[0], im[0] = box_muller_f32(a[0], a[1], sc)
     if ncomp == 2:
-        re[1], im[1] = box_muller_f32(w2, w3, sc)
+        re[1], im[1] = box_muller_f32(b[0], b[1], sc)
     return re, im

@@ -2,7 +2,10 @@
 //
 // Philox4x32-10 as published by Salmon, Moraes, Dror and Shaw, "Parallel
 // random numbers: as easy as 1, 2, 3" (SC'11), keyed by
-// key = (seed lo, seed hi), counter = (site, instance, step lo, step hi).
+// key = (seed lo, seed hi), counter = (c, instance, step lo, step hi): for two
+// components c = site and words (w0, w1) give xi_+, (w2, w3) xi_-; for one
+// component c = site >> 1 and words (w0, w1) give the even, (w2, w3) the odd
+// site of the pair, so one call serves two sites.
 // The Box-Muller transform uses this project's own ln and cos/sin built
 // from textbook series and only separately rounded float32 +, -, *, / and
 // sqrt (explicit __f*_rn intrinsics, never contracted into FMA), so a CPU
@@ -132,22 +135,41 @@ __device__ __forceinline__ float2 nz_box_muller(uint32_t wa, uint32_t wb,
   return make_float2(__fmul_rn(scale, z1), __fmul_rn(scale, z2));
 }
 
-// Noise of site `site` at step `step`: xi_+ (and xi_- for spinors), each
-// component with its own per-quadrature standard deviation.
+__device__ __forceinline__ U4 nz_words(unsigned long long seed, unsigned int instance,
+                                       long long step, uint32_t ctr) {
+  U4 c;
+  c.x = ctr;
+  c.y = instance;
+  c.z = (uint32_t)((unsigned long long)step & 0xFFFFFFFFull);
+  c.w = (uint32_t)((unsigned long long)step >> 32);
+  return philox4x32_10(c, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
+}
+
+// Noise of site `site` at step `step`: xi_+ and, for two components, xi_-,
+// each component with its own per-quadrature standard deviation.
 __device__ __forceinline__ void nz_site2(unsigned long long seed,
                                          unsigned int instance,
                                          long long step, uint32_t site,
                                          float scale0, float scale1,
                                          float2& xi0, float2& xi1, bool two) {
-  U4 c;
-  c.x = site;
-  c.y = instance;
-  c.z = (uint32_t)((unsigned long long)step & 0xFFFFFFFFull);
-  c.w = (uint32_t)((unsigned long long)step >> 32);
-  U4 w = philox4x32_10(c, (uint32_t)(seed & 0xFFFFFFFFull),
-                       (uint32_t)(seed >> 32));
-  xi0 = nz_box_muller(w.x, w.y, scale0);
-  if (two) xi1 = nz_box_muller(w.z, w.w, scale1);
+  if (two) {
+    const U4 w = nz_words(seed, instance, step, site);
+    xi0 = nz_box_muller(w.x, w.y, scale0);
+    xi1 = nz_box_muller(w.z, w.w, scale1);
+  } else {
+    const U4 w = nz_words(seed, instance, step, site >> 1);
+    xi0 = (site & 1u) ? nz_box_muller(w.z, w.w, scale0) : nz_box_muller(w.x, w.y, scale0);
+  }
+}
+
+// One-component noise of the even site 2p and the odd site 2p + 1 from one
+// Philox call.
+__device__ __forceinline__ void nz_pair(unsigned long long seed, unsigned int instance,
+                                        long long step, uint32_t pair, float scale_even,
+                                        float scale_odd, float2& xi_even, float2& xi_odd) {
+  const U4 w = nz_words(seed, instance, step, pair);
+  xi_even = nz_box_muller(w.x, w.y, scale_even);
+  xi_odd = nz_box_muller(w.z, w.w, scale_odd);
 }
 
 __device__ __forceinline__ void nz_site(unsigned long long seed,

@@ -437,21 +437,36 @@ rk4_f32_tma(const TileArgs ta) {
       on[j] = __ffma2_rn(d62, na[j], n0[j]);
     }
     if (nz.on) {  // grid-uniform branch: the generator is not issued when off
+      // The micro-tile's columns gx0 (even) and gx0 + 1 hold the sites 2p and
+      // 2p + 1 of one Philox pair when the row length is even: one call for
+      // both; otherwise one call per site.
+      const bool paired = (g.nx & 1) == 0;
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
         const int gy = gy0 + j;
+        const uint32_t row = (uint32_t)(((gy % g.ny + g.ny) % g.ny) * g.nx);
+        uint32_t site[2];
+        float sc[2];
+        float2 xi[2];
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           const int gx = gx0 + i;
-          const uint32_t site = (uint32_t)(((gy % g.ny + g.ny) % g.ny) * g.nx +
-                                           (gx % g.nx + g.nx) % g.nx);
-          float2 xi, unused;
-          const float sc = nz.twa ? nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var,
-                                                    RES ? (i ? n0[j].y : n0[j].x) : 0.f)
-                                  : nz.scale;
-          nz_site(nz.seed, nz.instance, step, site, sc, xi, unused, false);
-          o[j][i].x = o[j][i].x + xi.x;
-          o[j][i].y = o[j][i].y + xi.y;
+          site[i] = row + (uint32_t)((gx % g.nx + g.nx) % g.nx);
+          sc[i] = nz.twa ? nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var,
+                                           RES ? (i ? n0[j].y : n0[j].x) : 0.f)
+                         : nz.scale;
+        }
+        if (paired) {
+          nz_pair(nz.seed, nz.instance, step, site[0] >> 1, sc[0], sc[1], xi[0], xi[1]);
+        } else {
+          float2 unused;
+          nz_site(nz.seed, nz.instance, step, site[0], sc[0], xi[0], unused, false);
+          nz_site(nz.seed, nz.instance, step, site[1], sc[1], xi[1], unused, false);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          o[j][i].x = o[j][i].x + xi[i].x;
+          o[j][i].y = o[j][i].y + xi[i].y;
         }
       }
     }
