@@ -146,3 +146,23 @@ def test_noise_enters_after_deterministic_step():
     re, im = noise.noise_field(77, 41, 0, 2, 6, 8, 2e-3)
     assert np.array_equal(psi.real, re.astype(np.float64))
     assert np.array_equal(psi.imag, im.astype(np.float64))
+
+
+def test_one_component_pairs_share_a_philox_call():
+    """One-component fields take the counter site >> 1: the even site 2p
+    gets the words that give xi_+ of site p in the two-component stream and
+    the odd site 2p + 1 those of xi_-, so that one Philox call serves two
+    sites (checked on a field whose rows have odd length, so pairs also
+    straddle rows)."""
+    nx, ny = 7, 6
+    re1, im1 = noise.noise_field(12, 345, 2, 1, ny, nx, 1e-3)
+    half = nx * ny // 2
+    re2, im2 = noise.noise_field(12, 345, 2, 2, 1, half, 1e-3)
+    f1 = (re1 + 1j * im1).reshape(-1)
+    f2 = (re2 + 1j * im2).reshape(2, -1)
+    assert np.array_equal(f1[0::2], f2[0])
+    assert np.array_equal(f1[1::2], f2[1])
+    # the same rule for sampled sites
+    sites = np.array([0, 1, 5, 6, 40, 41])
+    r, i = noise.noise_at(12, 345, 2, sites, 1, 1e-3)
+    assert np.array_equal(r[0] + 1j * i[0], f1[sites])
