@@ -77,3 +77,51 @@ def test_reservoir_1024_invariants_and_time():
     for _ in range(2000):
         acc += cfg["params"]["dt"]
     assert step == 2000 and t == acc
+
+
+def test_driven_9000_sampled_step():
+    """The coherently driven 9000^2 lattice (the TMA-fed drive mode) at full
+    size: one step after 20, sampled against the oracle's windowed step with
+    the same drive amplitude and the FP64 time of the device clock."""
+    m = phx()
+    cfg = synth.driven_lattice(9000)
+    d = cfg["params"]
+    h = make_handle(d, 32, cfg["psi0"], None, None, cfg["V"])
+    m.phx_set_drive(h, np.ascontiguousarray(cfg["E"][0], np.complex64))
+    m.phx_step_n(h, 20)
+    psi_s, _ = get_state(h, 32)
+    step, t = m.phx_time(h)
+    m.phx_step_n(h, 1)
+    psi_1, _ = get_state(h, 32)
+    assert 1 <= m.phx_tile(h) <= 7
+    sites = sample_sites(9000, 9000, np.random.default_rng(4))
+    sp, _ = gp.step_at_sites(psi_s.astype(np.complex128), None, None, cfg["V"], gp.Params(**d),
+                             sites, step, E=cfg["E"], t=t)
+    jj = np.array([s[0] for s in sites])
+    ii = np.array([s[1] for s in sites])
+    assert rel_l2(psi_1[0, jj, ii], sp[0]) <= TOL[32], rel_l2(psi_1[0, jj, ii], sp[0])
+
+
+def test_twa_ensemble_member_matches_oracle():
+    """The truncated-Wigner ensemble in the benchmark's configuration (150
+    members of 256^2 in one persistent launch per step): members 0 and 149
+    after one 5 ps sample against the oracle run of the same member."""
+    m = phx()
+    members = synth.twa_ensemble()
+    b = m.phx_batch_create([m.params_from_dict(x["params"], precision=32) for x in members])
+    for i, x in enumerate(members):
+        m.phx_batch_set_pump(b, i, np.ascontiguousarray(x["P"][0], np.float32))
+        m.phx_batch_set_state(b, i, np.ascontiguousarray(x["psi0"], np.complex64),
+                              np.ascontiguousarray(x["n0"], np.float32))
+    steps = int(round(5.0 / members[0]["params"]["dt"]))
+    m.phx_batch_step_n(b, steps)
+    for i in (0, 149):
+        x = members[i]
+        psi = np.empty((1, 256, 256), np.complex64)
+        n = np.empty((1, 256, 256), np.float32)
+        m.phx_batch_get_state(b, i, psi, n)
+        psi0 = x["psi0"].astype(np.complex64).astype(np.complex128)
+        o_psi, o_n = gp.run(psi0, x["n0"], x["P"], None, gp.Params(**x["params"]), steps)
+        assert rel_l2(psi, o_psi) <= 1e-4, (i, rel_l2(psi, o_psi))
+        assert rel_l2(n, o_n) <= 1e-4, (i, rel_l2(n, o_n))
+    m.phx_batch_destroy(b)
