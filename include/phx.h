@@ -122,7 +122,7 @@ phx_status phx_stability_dt(const phx_params* p, double* dt_max);
 /* Validate p, allocate the device state on the current CUDA device and
  * zero it (psi = 0, n = 0, P = 0, V absent, step 0, t = 0).
  * EINVAL: bad sizes, BC, precision, spinor-only terms on a scalar problem,
- * dt <= 0 or dt > phx_stability_dt.  ENODEV: no sm_10x device.
+ * dt <= 0 or dt > phx_stability_dt.  ENODEV: no sm_103 (GB300) device.
  * ENOMEM / ECUDA on allocation failure.  *out is NULL on error. */
 phx_status phx_create(const phx_params* p, phx_handle** out);
 
@@ -192,6 +192,7 @@ phx_status phx_step_imag(phx_handle* h, int64_t nsteps);
  * mask M(k) = exp(-((k_x^2 + k_y^2) / k_cut^2)^order), k = 2 pi m / L with m the
  * FFT index, and transformed back (cuFFT, loaded at the first call).  The
  * paper does not give the mask; this super-Gaussian is this library's.
+ * It follows phx_step_n's steps (not phx_step_ssf / phx_step_imag).
  * every = 0 turns smoothing off (k_cut, order ignored).  EINVAL: every < 0,
  * k_cut <= 0 or not finite, order outside 1..16.  ECUDA: cuFFT missing or its
  * plans failed. */
