@@ -65,7 +65,7 @@ typedef enum phx_status {
   PHX_ENONFINITE = 4,  /* a reduction found NaN or Inf in the state */
   PHX_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
   PHX_ESTATE = 6,      /* call not valid in the handle's current state */
-  PHX_ENODEV = 7       /* no CUDA device of compute capability 10.x */
+  PHX_ENODEV = 7       /* no CUDA device of compute capability 10.3 (GB300) */
 } phx_status;
 
 enum { PHX_BC_PERIODIC = 0, PHX_BC_ZERO = 1 };
