@@ -264,39 +264,59 @@ def kfilter(psi, p):
 
 
 def ssf_local(psi, V, p, tau):
-    """Exact solution over time tau of the local part of Eq. (PULSE_psi) for a
-    scalar field without reservoir, dpsi/dt = (-(i/hbar)(V + g|psi|^2) -
-    gamma_c/2) psi: |psi|^2 decays as e^{-gamma_c t}, so
-    psi(tau) = psi e^{-gamma_c tau/2} exp(-(i/hbar)(V tau + g |psi|^2 F)),
+    """Exact solution over time tau of the local part of Eq. (PULSE_psi)
+    without reservoir, dpsi_c/dt = (-(i/hbar)(V + g|psi_c|^2 + g_x|psi_o|^2)
+    - gamma_c/2) psi_c: every |psi_c|^2 decays as e^{-gamma_c t}, so
+    psi_c(tau) = psi_c e^{-gamma_c tau/2} exp(-(i/hbar)(V tau + (g|psi_c|^2 + g_x|psi_o|^2) F)),
     F = (1 - e^{-gamma_c tau})/gamma_c (F = tau without loss)."""
     a = np.abs(psi) ** 2
     if p.gamma_c != 0.0:
         F = -np.expm1(-p.gamma_c * tau) / p.gamma_c
     else:
         F = tau
-    phase = p.g * a * F
-    if V is not None:
-        phase = phase + V * tau
-    return psi * np.exp(-0.5 * p.gamma_c * tau) * np.exp(-1j / HBAR * phase)
+    out = np.empty_like(psi)
+    for c in range(psi.shape[0]):
+        dens = p.g * a[c]
+        if psi.shape[0] == 2:
+            dens = dens + p.g_x * a[1 - c]
+        phase = dens * F
+        if V is not None:
+            phase = phase + V * tau
+        out[c] = psi[c] * np.exp(-0.5 * p.gamma_c * tau) * np.exp(-1j / HBAR * phase)
+    return out
 
 
 def ssf_kinetic(psi, p, tau):
-    """Exact kinetic propagation exp(-(i/hbar) kappa k^2 tau) in Fourier
-    space (spectral kinetic energy, k = 2 pi m / L, periodic)."""
+    """Exact propagation by the linear part in Fourier space (spectral,
+    k = 2 pi m / L, periodic): exp(-(i/hbar) kappa k^2 tau) per component; for
+    two components with TE-TM splitting the 2x2 block per k,
+    H_k = [[kappa k^2, a], [a*, kappa k^2]], a = -Delta_LT (k_x - i k_y)^2
+    (J_+ = Delta_LT (d_x - i d_y)^2 on psi_-), whose exponential is
+    e^{-i kappa k^2 tau/hbar} (cos th - i sin th [[0, u], [u*, 0]]),
+    th = Delta_LT k^2 tau / hbar, u = a / |a|."""
     kx = 2.0 * np.pi * np.fft.fftfreq(p.nx, p.dx)
     ky = 2.0 * np.pi * np.fft.fftfreq(p.ny, p.dy)
     k2 = ky[:, None] ** 2 + kx[None, :] ** 2
     U = np.exp(-1j / HBAR * p.kappa * k2 * tau)
-    return np.stack([np.fft.ifft2(U * np.fft.fft2(psi[c])) for c in range(psi.shape[0])])
+    f = [np.fft.fft2(psi[c]) for c in range(psi.shape[0])]
+    if psi.shape[0] == 2 and p.delta_lt != 0.0:
+        kc = kx[None, :] - 1j * ky[:, None]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            u = np.where(k2 > 0, -(kc ** 2) / k2, 0.0)
+        th = p.delta_lt * k2 * tau / HBAR
+        c, s = np.cos(th), np.sin(th)
+        f = [c * f[0] - 1j * s * u * f[1], c * f[1] - 1j * s * np.conj(u) * f[0]]
+    return np.stack([np.fft.ifft2(U * fc) for fc in f])
 
 
 def run_ssf(psi, V, p, nsteps, step0=0):
     """The split-step Fourier method (conclusions: the conventional
     alternative to RK4 the paper's code also offers; no details given).
-    Reading: Strang splitting of a scalar field without reservoir,
-    psi <- L(dt/2) K(dt) L(dt/2) psi per step with the exact local (ssf_local)
-    and kinetic (ssf_kinetic) propagators, then the same per-step noise as
-    run().  Periodic boundaries only."""
+    Reading: Strang splitting of a field without reservoir (scalar, or two
+    components with cross-Kerr and TE-TM coupling), psi <- L(dt/2) K(dt)
+    L(dt/2) psi per step with the exact local (ssf_local) and linear
+    (ssf_kinetic) propagators, then the same per-step noise as run().
+    Periodic boundaries only."""
     psi = np.array(psi, dtype=np.complex128)
     V = None if V is None else np.asarray(V, dtype=np.float64)
     for k in range(nsteps):

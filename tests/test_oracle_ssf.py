@@ -81,3 +81,69 @@ def test_conservative_steps_keep_the_norm():
     V = rng.uniform(-1, 1, (14, 20))
     out = gp.run_ssf(psi, V, p, 40)
     assert abs(np.linalg.norm(out) / np.linalg.norm(psi) - 1) < 1e-13
+
+
+def spinor_plane(p, mx, my, sign):
+    """Eigen-spinor (1, sign u*) e^{i k.r} of the spectral TE-TM block."""
+    kx, ky = 2 * np.pi * mx / p.lx, 2 * np.pi * my / p.ly
+    x = np.arange(p.nx) * p.dx
+    y = np.arange(p.ny) * p.dy
+    w = np.exp(1j * (kx * x[None, :] + ky * y[:, None]))
+    k2 = kx * kx + ky * ky
+    u = -((kx - 1j * ky) ** 2) / k2
+    return np.stack([w, sign * np.conj(u) * w]), k2
+
+
+def test_tetm_eigen_spinors_rotate_at_their_energies():
+    """Free spinor field with TE-TM splitting: (1, +-u*) e^{ik.r} acquires
+    exp(-i (kappa +- Delta_LT) k^2 t / hbar) exactly -- the two TE and TM
+    branches of the splitting; a wrong sign or conjugation of J mixes them."""
+    p = gp.Params(nx=16, ny=12, lx=8.0, ly=6.0, spinor=True, kappa=0.67, delta_lt=0.2, dt=0.21)
+    for mx, my in [(2, 1), (-3, 2), (1, -4)]:
+        for sign in (1, -1):
+            v, k2 = spinor_plane(p, mx, my, sign)
+            out = gp.run_ssf(v, None, p, 5)
+            want = v * np.exp(-1j * (0.67 + sign * 0.2) * k2 * 5 * 0.21 / HB)
+            assert np.abs(out - want).max() < 1e-12, (mx, my, sign)
+
+
+def test_spinor_local_step_is_exact():
+    """Uniform spinor, g, g_x and loss: each component keeps its density
+    ratio and rotates by (g|psi_c|^2 + g_x|psi_o|^2)(1 - e^{-gamma t})/(gamma hbar)."""
+    g, gx, gam, dt, n = 0.4, 0.15, 0.3, 0.2, 9
+    p = gp.Params(nx=4, ny=4, lx=2.0, ly=2.0, spinor=True, g=g, g_x=gx, gamma_c=gam, dt=dt)
+    a, b = 1.1 + 0.2j, -0.5 + 0.7j
+    psi = np.stack([np.full((4, 4), a), np.full((4, 4), b)])
+    out = gp.run_ssf(psi, None, p, n)
+    t = n * dt
+    F = (1 - np.exp(-gam * t)) / gam
+    for c, (z, o) in enumerate(((a, b), (b, a))):
+        want = z * np.exp(-gam * t / 2) * np.exp(-1j / HB * (g * abs(z) ** 2 + gx * abs(o) ** 2) * F)
+        assert np.abs(out[c] - want).max() < 1e-13
+
+
+def test_spinor_split_step_agrees_with_the_rk4_path():
+    """A smooth spinor packet with TE-TM splitting, cross-Kerr and loss: the
+    split-step (spectral) and the RK4 (finite-difference) paths agree to
+    their discretisation errors, which ties the spectral J to the stencil's
+    sign conventions."""
+    n, L = 64, 16.0
+    p = gp.Params(nx=n, ny=n, lx=L, ly=L, spinor=True, kappa=0.67, g=0.05, g_x=0.02,
+                  gamma_c=0.1, delta_lt=0.5)
+    p = p.with_(dt=0.2 * gp.stability_dt_max(p))
+    x = (np.arange(n) - n // 2) * p.dx
+    env = np.exp(-(x[None, :] ** 2 + x[:, None] ** 2) / 8.0)
+    psi = np.stack([env * np.exp(0.6j * x[None, :]), 0.5 * env * np.exp(-0.4j * x[:, None])])
+    steps = int(1.0 / p.dt)  # 1 ps: the TE-TM coupling turns the state by O(1)
+    a = gp.run_ssf(psi, None, p, steps)
+    b, _ = gp.run(psi, None, None, None, p, steps)
+    nb = np.linalg.norm(b)
+    assert np.linalg.norm(a - b) / nb < 0.02
+    # the coupling matters at this scale (with it switched off they differ by O(1);
+    # with its sign flipped, by ~0.9)
+    a0 = gp.run_ssf(psi, None, p.with_(delta_lt=0.0), steps)
+    assert np.linalg.norm(a0 - b) / nb > 0.3
+    # and the spinor split-step keeps the norm without loss
+    q = p.with_(gamma_c=0.0)
+    c = gp.run_ssf(psi, None, q, 40)
+    assert abs(np.linalg.norm(c) / np.linalg.norm(psi) - 1) < 1e-12
