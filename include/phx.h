@@ -166,14 +166,16 @@ phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
 /* nsteps steps of the split-step Fourier method instead of RK4 (the
  * conventional alternative the paper's conclusions name, without details):
  * Strang splitting psi <- L(dt/2) K(dt) L(dt/2) psi with the exact local
- * propagator L(tau) psi = psi e^{-gamma_c tau/2} exp(-(i/hbar)(V tau + g|psi|^2 F)),
- * F = (1 - e^{-gamma_c tau})/gamma_c (tau without loss), and the exact
- * spectral kinetic propagator K(tau) = exp(-(i/hbar) kappa k^2 tau), k = 2 pi m / L
- * (cuFFT, loaded at the first call); then the step's noise as in phx_step_n.
- * Same dt, clock and state as phx_step_n (the two may alternate).  ESTATE
- * unless the handle is a scalar field without reservoir, periodic in x and
- * y, without drive and without truncated-Wigner noise; ECUDA if cuFFT is
- * missing. */
+ * propagator L(tau) psi_c = psi_c e^{-gamma_c tau/2}
+ * exp(-(i/hbar)(V tau + (g|psi_c|^2 + g_x|psi_o|^2) F)), F = (1 - e^{-gamma_c tau})/gamma_c
+ * (tau without loss), and the exact spectral linear propagator
+ * K(tau) = exp(-(i/hbar) kappa k^2 tau), k = 2 pi m / L, times, for two
+ * components, the exponential of the TE-TM block [[0, a], [a*, 0]],
+ * a = -Delta_LT (k_x - i k_y)^2 (cuFFT, loaded at the first call); then the
+ * step's noise as in phx_step_n.  Same dt, clock and state as phx_step_n
+ * (the two may alternate).  ESTATE unless the handle has no reservoir, is
+ * periodic in x and y, and has neither a drive nor truncated-Wigner noise;
+ * ECUDA if cuFFT is missing. */
 phx_status phx_step_ssf(phx_handle* h, int64_t nsteps);
 
 /* nsteps imaginary-time steps (t -> -i tau in the conservative part of

@@ -1,12 +1,16 @@
 // Split-step Fourier integrator (the conventional alternative to RK4 the
 // paper's conclusions name; no details given): Strang splitting
 //   psi <- L(dt/2) K(dt) L(dt/2) psi
-// of a scalar field without reservoir, with the exact local propagator
-//   L(tau) psi = psi e^{-gamma_c tau/2} exp(-(i/hbar)(V tau + g |psi|^2 F)),
+// of a field without reservoir (scalar, or two components), with the exact
+// local propagator
+//   L(tau) psi_c = psi_c e^{-gamma_c tau/2} exp(-(i/hbar)(V tau + (g|psi_c|^2 + g_x|psi_o|^2) F)),
 //   F = (1 - e^{-gamma_c tau}) / gamma_c   (F = tau without loss),
-// which holds because |psi|^2 only decays under the local equation, and the
-// exact kinetic propagator K(tau) = exp(-(i/hbar) kappa k^2 tau) applied in
-// Fourier space (cuFFT, via the FFT pair of kfilter.cu).  The second local
+// which holds because every |psi_c|^2 only decays under the local equation,
+// and the exact linear propagator applied in Fourier space (cuFFT, via the
+// FFT pair of kfilter.cu): exp(-(i/hbar) kappa k^2 tau) per component, times
+// the exponential of the TE-TM block [[0, a], [a*, 0]], a = -Delta_LT (k_x - i k_y)^2,
+// i.e. cos(th) - i sin(th) [[0, u], [u*, 0]], th = Delta_LT k^2 tau / hbar,
+// u = a / |a|, for two components.  The second local
 // half step of each step also adds the step's noise (same Philox stream as
 // the RK4 path) and advances the FP64 device clock.
 #include "phx_noise.cuh"
@@ -18,8 +22,8 @@ namespace {
 
 __device__ __forceinline__ int fft_index_ssf(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
 
-template <typename R, typename C>
-__global__ void ssf_local_kernel(C* psi, Geometry g, const R* V, R gF, R tau_h, R damp,
+template <typename R, typename C, int NC>
+__global__ void ssf_local_kernel(C* psi, Geometry g, const R* V, R gF, R gxF, R tau_h, R damp,
                                  NoiseKey nz, DevClock* clock, int parity, int last,
                                  double dt64) {
   const long long sites = (long long)g.nx * g.ny;
@@ -32,38 +36,68 @@ __global__ void ssf_local_kernel(C* psi, Geometry g, const R* V, R gF, R tau_h, 
        t += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
     const long long off = (long long)(j + HALO) * g.pitch + i + HALO;
-    C v = psi[off];
-    // angle of exp(-(i/hbar)(V tau + g |psi|^2 F)): gF = g F / hbar, tau_h = tau / hbar
-    R ph = gF * (v.x * v.x + v.y * v.y);
-    if (V) ph += tau_h * V[off];
-    R sn, cs;
-    sincos(ph, &sn, &cs);
-    C o;
-    o.x = damp * (v.x * cs + v.y * sn);
-    o.y = damp * (v.y * cs - v.x * sn);
-    if (last && nz.on) {
-      float2 xi, unused;
-      nz_site(nz.seed, nz.instance, step, (uint32_t)t, nz.scale, xi, unused, false);
-      o.x = o.x + R(xi.x);
-      o.y = o.y + R(xi.y);
+    C v[NC];
+    R a[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      v[c] = psi[c * g.plane + off];
+      a[c] = v[c].x * v[c].x + v[c].y * v[c].y;
     }
-    psi[off] = o;
+    float2 xi[2];
+    if (last && nz.on) nz_site(nz.seed, nz.instance, step, (uint32_t)t, nz.scale, xi[0], xi[1], NC == 2);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      // angle of exp(-(i/hbar)(V tau + (g|psi_c|^2 + g_x|psi_o|^2) F)):
+      // gF = g F / hbar, gxF = g_x F / hbar, tau_h = tau / hbar
+      R ph = gF * a[c];
+      if (NC == 2) ph += gxF * a[NC - 1 - c];
+      if (V) ph += tau_h * V[off];
+      R sn, cs;
+      sincos(ph, &sn, &cs);
+      C o;
+      o.x = damp * (v[c].x * cs + v[c].y * sn);
+      o.y = damp * (v[c].y * cs - v[c].x * sn);
+      if (last && nz.on) {
+        o.x = o.x + R(xi[c].x);
+        o.y = o.y + R(xi[c].y);
+      }
+      psi[c * g.plane + off] = o;
+    }
   }
 }
 
-template <typename R, typename C>
-__global__ void ssf_kinetic_kernel(C* d, int nx, int ny, R dkx, R dky, R c, R scale) {
+template <typename R, typename C, int NC>
+__global__ void ssf_kinetic_kernel(C* d, int nx, int ny, R dkx, R dky, R c, R cd, R scale) {
   const long long total = (long long)nx * ny;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(t / nx), i = (int)(t - (long long)j * nx);
     const R kx = dkx * R(fft_index_ssf(i, nx)), ky = dky * R(fft_index_ssf(j, ny));
+    const R k2 = ky * ky + kx * kx;
     R sn, cs;
-    sincos(c * (ky * ky + kx * kx), &sn, &cs);  // exp(-i c k^2) = cs - i sn
-    C v = d[t], o;
-    o.x = scale * (v.x * cs + v.y * sn);
-    o.y = scale * (v.y * cs - v.x * sn);
-    d[t] = o;
+    sincos(c * k2, &sn, &cs);  // exp(-i c k^2) = cs - i sn
+    C f[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) f[q] = d[q * total + t];
+    if (NC == 2 && cd != R(0) && k2 > R(0)) {
+      // cos(th) f - i sin(th) [[0, u], [u*, 0]] f,  u = -(k_x - i k_y)^2 / k^2
+      R st, ct;
+      sincos(cd * k2, &st, &ct);
+      const R ur = -(kx * kx - ky * ky) / k2, ui = R(2) * kx * ky / k2;
+      const C w0 = {ur * f[1].x - ui * f[1].y, ur * f[1].y + ui * f[1].x};  // u f_-
+      const C w1 = {ur * f[0].x + ui * f[0].y, ur * f[0].y - ui * f[0].x};  // u* f_+
+      const C g0 = {ct * f[0].x + st * w0.y, ct * f[0].y - st * w0.x};
+      const C g1 = {ct * f[1].x + st * w1.y, ct * f[1].y - st * w1.x};
+      f[0] = g0;
+      f[NC - 1] = g1;
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      C o;
+      o.x = scale * (f[q].x * cs + f[q].y * sn);
+      o.y = scale * (f[q].y * cs - f[q].x * sn);
+      d[q * total + t] = o;
+    }
   }
 }
 
@@ -161,25 +195,28 @@ int grid_for(long long n) {
   return (int)(b < 8192 ? (b < 1 ? 1 : b) : 8192);
 }
 
-template <typename R, typename C>
+template <typename R, typename C, int NC>
 const char* ssf_step_t(FftPair& fft, void* psi, const Geometry& g, const void* V,
                        const SsfCoeffs& k, const NoiseKey& nz, DevClock* clock, int parity,
                        cudaStream_t s) {
   C* p = static_cast<C*>(psi);
   const R* v = static_cast<const R*>(V);
   const int blocks = grid_for((long long)g.nx * g.ny);
-  ssf_local_kernel<R, C><<<blocks, 256, 0, s>>>(p, g, v, (R)k.gF_half, (R)k.tau_half_h,
-                                                (R)k.damp_half, nz, clock, parity, 0, k.dt);
+  ssf_local_kernel<R, C, NC><<<blocks, 256, 0, s>>>(p, g, v, (R)k.gF_half, (R)k.gxF_half,
+                                                    (R)k.tau_half_h, (R)k.damp_half, nz, clock,
+                                                    parity, 0, k.dt);
   count_launch();
   const char* msg = fft_transform(fft, psi, g, sizeof(R) == 8 ? 64 : 32, true, s);
   if (msg) return msg;
-  ssf_kinetic_kernel<R, C><<<blocks, 256, 0, s>>>(static_cast<C*>(fft.scratch), g.nx, g.ny,
-                                                  (R)k.dkx, (R)k.dky, (R)k.kin, (R)k.scale);
+  ssf_kinetic_kernel<R, C, NC><<<blocks, 256, 0, s>>>(static_cast<C*>(fft.scratch), g.nx, g.ny,
+                                                      (R)k.dkx, (R)k.dky, (R)k.kin, (R)k.tetm,
+                                                      (R)k.scale);
   count_launch();
   msg = fft_transform(fft, psi, g, sizeof(R) == 8 ? 64 : 32, false, s);
   if (msg) return msg;
-  ssf_local_kernel<R, C><<<blocks, 256, 0, s>>>(p, g, v, (R)k.gF_half, (R)k.tau_half_h,
-                                                (R)k.damp_half, nz, clock, parity, 1, k.dt);
+  ssf_local_kernel<R, C, NC><<<blocks, 256, 0, s>>>(p, g, v, (R)k.gF_half, (R)k.gxF_half,
+                                                    (R)k.tau_half_h, (R)k.damp_half, nz, clock,
+                                                    parity, 1, k.dt);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? nullptr : "split-step kernel launch failed";
 }
@@ -235,23 +272,27 @@ SsfCoeffs ssf_coeffs(const phx_params& p) {
   const double tau = 0.5 * p.dt;
   const double F = p.gamma_c != 0.0 ? -std::expm1(-p.gamma_c * tau) / p.gamma_c : tau;
   k.gF_half = p.g * F / HBAR;
+  k.gxF_half = p.g_x * F / HBAR;
   k.tau_half_h = tau / HBAR;
   k.damp_half = std::exp(-0.5 * p.gamma_c * tau);
   const double pi = 3.14159265358979323846;
   k.dkx = 2.0 * pi / p.lx;
   k.dky = 2.0 * pi / p.ly;
   k.kin = p.hbar2_over_2m * p.dt / HBAR;
+  k.tetm = p.delta_lt * p.dt / HBAR;
   k.scale = 1.0 / ((double)p.nx * p.ny);
   k.dt = p.dt;
   return k;
 }
 
-const char* ssf_step(FftPair& fft, void* psi, const Geometry& g, int precision, const void* V,
-                     const SsfCoeffs& k, const NoiseKey& nz, DevClock* clock, int parity,
-                     cudaStream_t s) {
+const char* ssf_step(FftPair& fft, void* psi, const Geometry& g, int precision, int ncomp,
+                     const void* V, const SsfCoeffs& k, const NoiseKey& nz, DevClock* clock,
+                     int parity, cudaStream_t s) {
   if (precision == 64)
-    return ssf_step_t<double, double2>(fft, psi, g, V, k, nz, clock, parity, s);
-  return ssf_step_t<float, float2>(fft, psi, g, V, k, nz, clock, parity, s);
+    return ncomp == 2 ? ssf_step_t<double, double2, 2>(fft, psi, g, V, k, nz, clock, parity, s)
+                      : ssf_step_t<double, double2, 1>(fft, psi, g, V, k, nz, clock, parity, s);
+  return ncomp == 2 ? ssf_step_t<float, float2, 2>(fft, psi, g, V, k, nz, clock, parity, s)
+                    : ssf_step_t<float, float2, 1>(fft, psi, g, V, k, nz, clock, parity, s);
 }
 
 }  // namespace phx

@@ -72,8 +72,7 @@ def test_ssf_conservative_keeps_norm_and_alternates_with_rk4(prec):
 
 def test_ssf_refuses_unsupported_states():
     m = phx()
-    for kw in (dict(reservoir=True, R=0.1, gamma_r=0.2), dict(spinor=True), dict(bc_x=1),
-               dict(wigner_nu=1.0)):
+    for kw in (dict(reservoir=True, R=0.1, gamma_r=0.2), dict(bc_x=1), dict(wigner_nu=1.0)):
         d = params(40, 36, **kw)
         h = m.phx_create(m.params_from_dict(d, precision=64))
         with pytest.raises(m.PhxError) as e:
@@ -85,3 +84,24 @@ def test_ssf_refuses_unsupported_states():
     with pytest.raises(m.PhxError) as e:
         m.phx_step_ssf(h, 1)
     assert e.value.status == 6
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("tetm", [0.0, 0.2])
+def test_ssf_spinor_parity(prec, tetm):
+    """Two components: cross-Kerr in the local step, the spectral TE-TM block
+    in the linear step, per-step noise on both components."""
+    m = phx()
+    real, cplx = (np.float64, np.complex128) if prec == 64 else (np.float32, np.complex64)
+    d = synth.base_params(97, 66, 29.1, 19.8, spinor=True, g=0.3, g_x=0.1, gamma_c=0.05,
+                          delta_lt=tetm, noise_var=1e-4, seed=43)
+    d["dt"] = min(0.45 * gp.stability_dt_max(gp.Params(**d)), 0.05)
+    psi0, _, _, V = synth.random_state(2, 66, 97, 9, amp=0.7, reservoir=False, smooth=True)
+    psi0, V = rounded(psi0, prec), rounded(V, prec)
+    h = m.phx_create(m.params_from_dict(d, precision=prec))
+    m.phx_set_potential(h, np.ascontiguousarray(V, real))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, cplx))
+    m.phx_step_ssf(h, 10)
+    g_psi, _ = get_state(h, prec)
+    o_psi = gp.run_ssf(psi0, V, gp.Params(**d), 10)
+    assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
