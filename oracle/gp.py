@@ -330,27 +330,48 @@ def run_ssf(psi, V, p, nsteps, step0=0):
 def run_imag(psi, V, p, nsteps):
     """Imaginary-time propagation (named in the conclusions; no details
     given).  Reading: t -> -i tau in the conservative part of Eq. (PULSE_psi)
-    for a scalar field without reservoir, split like run_ssf --
-    psi <- exp(-(V + g|psi|^2) dt/(2 hbar)) exp(-kappa k^2 dt/hbar) exp(-(V + g|psi|^2) dt/(2 hbar)) psi,
-    the density frozen within each local factor -- then rescaled to the norm
-    N = dV sum |psi|^2 it had at the start.  Loss, gain and noise take no part.
-    Converges to the ground state of the (spectral) Hamiltonian."""
+    without reservoir, split like run_ssf --
+    psi_c <- exp(-(V + g|psi_c|^2 + g_x|psi_o|^2) dt/(2 hbar)) psi_c (densities
+    frozen within the factor), the linear factor exp(-H_k dt/hbar) in Fourier
+    space (kappa k^2, and for two components the TE-TM block of ssf_kinetic:
+    e^{-kappa k^2 tau/hbar} (cosh th - sinh th [[0, u], [u*, 0]])), the local
+    factor again -- then rescaled to the norm N = dV sum |psi|^2 it had at the
+    start.  Loss, gain and noise take no part.  Converges to the ground state
+    of the (spectral) Hamiltonian."""
     psi = np.array(psi, dtype=np.complex128)
     V = None if V is None else np.asarray(V, dtype=np.float64)
     N0 = norm(psi, p)
+    nc = psi.shape[0]
 
     def local(u):
-        ph = p.g * np.abs(u) ** 2
-        if V is not None:
-            ph = ph + V
-        return u * np.exp(-0.5 * p.dt / HBAR * ph)
+        a = np.abs(u) ** 2
+        out = np.empty_like(u)
+        for c in range(nc):
+            ph = p.g * a[c]
+            if nc == 2:
+                ph = ph + p.g_x * a[1 - c]
+            if V is not None:
+                ph = ph + V
+            out[c] = u[c] * np.exp(-0.5 * p.dt / HBAR * ph)
+        return out
 
     kx = 2.0 * np.pi * np.fft.fftfreq(p.nx, p.dx)
     ky = 2.0 * np.pi * np.fft.fftfreq(p.ny, p.dy)
-    K = np.exp(-p.kappa * (ky[:, None] ** 2 + kx[None, :] ** 2) * p.dt / HBAR)
+    k2 = ky[:, None] ** 2 + kx[None, :] ** 2
+    K = np.exp(-p.kappa * k2 * p.dt / HBAR)
+    mix = nc == 2 and p.delta_lt != 0.0
+    if mix:
+        kc = kx[None, :] - 1j * ky[:, None]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            uu = np.where(k2 > 0, -(kc ** 2) / k2, 0.0)
+        th = p.delta_lt * k2 * p.dt / HBAR
+        ch, sh = np.cosh(th), np.sinh(th)
     for _ in range(nsteps):
         psi = local(psi)
-        psi = np.stack([np.fft.ifft2(K * np.fft.fft2(psi[c])) for c in range(psi.shape[0])])
+        f = [np.fft.fft2(psi[c]) for c in range(nc)]
+        if mix:
+            f = [ch * f[0] - sh * uu * f[1], ch * f[1] - sh * np.conj(uu) * f[0]]
+        psi = np.stack([np.fft.ifft2(K * fc) for fc in f])
         psi = local(psi)
         psi = psi * np.sqrt(N0 / norm(psi, p))
     return psi

@@ -54,3 +54,24 @@ def test_two_plane_waves_decay_by_their_kinetic_energy():
     tau = 5 * 0.3
     want = 0.5 * np.exp(-0.67 * ((k2[0] ** 2 + k2[1] ** 2) - (k1[0] ** 2 + k1[1] ** 2)) * tau / HB)
     assert abs(b / a - want) < 1e-12
+
+
+def test_tetm_branches_decay_by_their_energies():
+    """Free spinor field with TE-TM splitting in imaginary time: the TM-like
+    eigen-spinor (1, -u*) e^{ik.r} (energy (kappa - Delta) k^2) gains on the
+    TE-like (1, u*) e^{ik.r} by exactly exp(2 Delta k^2 tau / hbar)."""
+    p = gp.Params(nx=16, ny=12, lx=8.0, ly=6.0, spinor=True, kappa=0.67, delta_lt=0.2, dt=0.1)
+    mx, my = 2, -1
+    kx, ky = 2 * np.pi * mx / p.lx, 2 * np.pi * my / p.ly
+    x = np.arange(p.nx) * p.dx
+    y = np.arange(p.ny) * p.dy
+    w = np.exp(1j * (kx * x[None, :] + ky * y[:, None]))
+    k2 = kx * kx + ky * ky
+    u = -((kx - 1j * ky) ** 2) / k2
+    vp = np.stack([w, np.conj(u) * w])
+    vm = np.stack([w, -np.conj(u) * w])
+    out = gp.run_imag(vp + 0.3 * vm, None, p, 6)
+    cp = np.vdot(vp, out) / np.vdot(vp, vp)
+    cm = np.vdot(vm, out) / np.vdot(vm, vm)
+    want = 0.3 * np.exp(2 * 0.2 * k2 * 6 * 0.1 / HB)
+    assert abs(cm / cp - want) < 1e-10 * want
