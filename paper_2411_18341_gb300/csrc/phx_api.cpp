@@ -700,20 +700,21 @@ phx_status phx_step_ssf(phx_handle* h, int64_t nsteps) {
 phx_status phx_step_imag(phx_handle* h, int64_t nsteps) {
   if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(h, PHX_EINVAL, "nsteps must be >= 0");
-  if (h->m.ncomp != 1 || h->m.reservoir)
-    return fail(h, PHX_ESTATE, "imaginary time needs a scalar field without reservoir");
+  if (h->m.reservoir) return fail(h, PHX_ESTATE, "imaginary time needs a field without reservoir");
   if (h->p.bc_x != PHX_BC_PERIODIC || h->p.bc_y != PHX_BC_PERIODIC)
     return fail(h, PHX_ESTATE, "imaginary time needs periodic boundaries");
   if (nsteps == 0) return PHX_OK;
   DeviceGuard dg(h->device);
-  const char* msg = fft_pair_setup(h->ssf_fft, h->geo, 1, h->m.precision);
+  if (h->ssf_fft.have_plans && h->ssf_ncomp != h->m.ncomp) fft_pair_release(h->ssf_fft);
+  const char* msg = fft_pair_setup(h->ssf_fft, h->geo, h->m.ncomp, h->m.precision);
   if (msg) return fail(h, PHX_ECUDA, msg);
-  h->ssf_ncomp = 1;
+  h->ssf_ncomp = h->m.ncomp;
   if (!h->imag_red) PHX_CK(h, cudaMalloc(&h->imag_red, imag_scratch_doubles() * sizeof(double)));
   msg = imag_steps(h->ssf_fft, h->imag_red, h->psi[h->cur], h->geo, h->m.precision,
                    h->has_V ? h->V : nullptr, h->p, nsteps, h->stream);
   if (msg) return fail(h, PHX_ECUDA, msg);
-  PHX_CK(h, launch_fill_ghosts(h->psi[h->cur], (int)(2 * h->esize), 1, h->geo, h->stream));
+  PHX_CK(h, launch_fill_ghosts(h->psi[h->cur], (int)(2 * h->esize), h->m.ncomp, h->geo,
+                               h->stream));
   return PHX_OK;
 }
 

@@ -104,35 +104,63 @@ __global__ void ssf_kinetic_kernel(C* d, int nx, int ny, R dkx, R dky, R c, R cd
 // Imaginary time (t -> -i tau, conservative part): real factors
 // exp(-(g|psi|^2 + V) tau / hbar) locally and exp(-kappa k^2 tau / hbar) in
 // Fourier space.
-template <typename R, typename C>
-__global__ void imag_local_kernel(C* psi, Geometry g, const R* V, R cg, R cv) {
+template <typename R, typename C, int NC>
+__global__ void imag_local_kernel(C* psi, Geometry g, const R* V, R cg, R cgx, R cv) {
   const long long sites = (long long)g.nx * g.ny;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < sites;
        t += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
     const long long off = (long long)(j + HALO) * g.pitch + i + HALO;
-    C v = psi[off];
-    R e = cg * (v.x * v.x + v.y * v.y);
-    if (V) e += cv * V[off];
-    const R f = exp(-e);
-    v.x *= f;
-    v.y *= f;
-    psi[off] = v;
+    C v[NC];
+    R a[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      v[c] = psi[c * g.plane + off];
+      a[c] = v[c].x * v[c].x + v[c].y * v[c].y;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      R e = cg * a[c];
+      if (NC == 2) e += cgx * a[NC - 1 - c];
+      if (V) e += cv * V[off];
+      const R f = exp(-e);
+      v[c].x *= f;
+      v[c].y *= f;
+      psi[c * g.plane + off] = v[c];
+    }
   }
 }
 
-template <typename R, typename C>
-__global__ void imag_kinetic_kernel(C* d, int nx, int ny, R dkx, R dky, R c, R scale) {
+// exp(-H_k tau / hbar): e^{-c k^2} per component and, for two components,
+// cosh(th) - sinh(th) [[0, u], [u*, 0]], th = cd k^2, u = -(k_x - i k_y)^2 / k^2.
+template <typename R, typename C, int NC>
+__global__ void imag_kinetic_kernel(C* d, int nx, int ny, R dkx, R dky, R c, R cd, R scale) {
   const long long total = (long long)nx * ny;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(t / nx), i = (int)(t - (long long)j * nx);
     const R kx = dkx * R(fft_index_ssf(i, nx)), ky = dky * R(fft_index_ssf(j, ny));
-    const R f = scale * exp(-c * (ky * ky + kx * kx));
-    C v = d[t];
-    v.x *= f;
-    v.y *= f;
-    d[t] = v;
+    const R k2 = ky * ky + kx * kx;
+    const R f = scale * exp(-c * k2);
+    C v[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) v[q] = d[q * total + t];
+    if (NC == 2 && cd != R(0) && k2 > R(0)) {
+      const R ch = cosh(cd * k2), sh = sinh(cd * k2);
+      const R ur = -(kx * kx - ky * ky) / k2, ui = R(2) * kx * ky / k2;
+      const C w0 = {ur * v[1].x - ui * v[1].y, ur * v[1].y + ui * v[1].x};  // u f_-
+      const C w1 = {ur * v[0].x + ui * v[0].y, ur * v[0].y - ui * v[0].x};  // u* f_+
+      const C g0 = {ch * v[0].x - sh * w0.x, ch * v[0].y - sh * w0.y};
+      const C g1 = {ch * v[1].x - sh * w1.x, ch * v[1].y - sh * w1.y};
+      v[0] = g0;
+      v[NC - 1] = g1;
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      v[q].x *= f;
+      v[q].y *= f;
+      d[q * total + t] = v[q];
+    }
   }
 }
 
@@ -140,7 +168,7 @@ constexpr int RED_BLOCKS = 512, RED_THREADS = 256;
 
 // Block partials of sum |psi|^2 (FP64, fixed grid and order: deterministic).
 template <typename C>
-__global__ void __launch_bounds__(RED_THREADS) sumsq_kernel(const C* psi, Geometry g,
+__global__ void __launch_bounds__(RED_THREADS) sumsq_kernel(const C* psi, Geometry g, int ncomp,
                                                              double* partials) {
   __shared__ double sh[RED_THREADS / 32];
   const long long sites = (long long)g.nx * g.ny;
@@ -148,8 +176,10 @@ __global__ void __launch_bounds__(RED_THREADS) sumsq_kernel(const C* psi, Geomet
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < sites;
        t += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
-    const C v = psi[(long long)(j + HALO) * g.pitch + i + HALO];
-    acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    for (int c = 0; c < ncomp; ++c) {
+      const C v = psi[c * g.plane + (long long)(j + HALO) * g.pitch + i + HALO];
+      acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -174,7 +204,8 @@ __global__ void store_target_kernel(const double* partials, double* target) {
 
 // psi *= sqrt(target / sum): the norm back to its value at the start.
 template <typename R, typename C>
-__global__ void rescale_kernel(C* psi, Geometry g, const double* partials, const double* target) {
+__global__ void rescale_kernel(C* psi, Geometry g, int ncomp, const double* partials,
+                               const double* target) {
   __shared__ R f;
   if (threadIdx.x == 0) f = (R)sqrt(*target / sum_partials(partials));
   __syncthreads();
@@ -183,10 +214,12 @@ __global__ void rescale_kernel(C* psi, Geometry g, const double* partials, const
        t += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
     const long long off = (long long)(j + HALO) * g.pitch + i + HALO;
-    C v = psi[off];
-    v.x *= f;
-    v.y *= f;
-    psi[off] = v;
+    for (int c = 0; c < ncomp; ++c) {
+      C v = psi[c * g.plane + off];
+      v.x *= f;
+      v.y *= f;
+      psi[c * g.plane + off] = v;
+    }
   }
 }
 
@@ -221,7 +254,7 @@ const char* ssf_step_t(FftPair& fft, void* psi, const Geometry& g, const void* V
   return cudaGetLastError() == cudaSuccess ? nullptr : "split-step kernel launch failed";
 }
 
-template <typename R, typename C>
+template <typename R, typename C, int NC>
 const char* imag_steps_t(FftPair& fft, double* red, void* psi, const Geometry& g, const void* V,
                          const phx_params& p, long long nsteps, cudaStream_t s) {
   C* ps = static_cast<C*>(psi);
@@ -229,28 +262,29 @@ const char* imag_steps_t(FftPair& fft, double* red, void* psi, const Geometry& g
   const int blocks = grid_for((long long)g.nx * g.ny);
   const int prec = sizeof(R) == 8 ? 64 : 32;
   const double pi = 3.14159265358979323846;
-  const R cg = (R)(p.g * 0.5 * p.dt / HBAR), cv = (R)(0.5 * p.dt / HBAR);
-  const R ck = (R)(p.hbar2_over_2m * p.dt / HBAR);
+  const R cg = (R)(p.g * 0.5 * p.dt / HBAR), cgx = (R)(p.g_x * 0.5 * p.dt / HBAR);
+  const R cv = (R)(0.5 * p.dt / HBAR);
+  const R ck = (R)(p.hbar2_over_2m * p.dt / HBAR), cd = (R)(p.delta_lt * p.dt / HBAR);
   const R dkx = (R)(2.0 * pi / p.lx), dky = (R)(2.0 * pi / p.ly);
   const R scale = (R)(1.0 / ((double)p.nx * p.ny));
   double* partials = red;
   double* target = red + RED_BLOCKS;
-  sumsq_kernel<C><<<RED_BLOCKS, RED_THREADS, 0, s>>>(ps, g, partials);
+  sumsq_kernel<C><<<RED_BLOCKS, RED_THREADS, 0, s>>>(ps, g, NC, partials);
   store_target_kernel<<<1, 32, 0, s>>>(partials, target);
   count_launch(2);
   for (long long k = 0; k < nsteps; ++k) {
-    imag_local_kernel<R, C><<<blocks, 256, 0, s>>>(ps, g, v, cg, cv);
+    imag_local_kernel<R, C, NC><<<blocks, 256, 0, s>>>(ps, g, v, cg, cgx, cv);
     count_launch();
     const char* msg = fft_transform(fft, psi, g, prec, true, s);
     if (msg) return msg;
-    imag_kinetic_kernel<R, C><<<blocks, 256, 0, s>>>(static_cast<C*>(fft.scratch), g.nx, g.ny,
-                                                     dkx, dky, ck, scale);
+    imag_kinetic_kernel<R, C, NC><<<blocks, 256, 0, s>>>(static_cast<C*>(fft.scratch), g.nx,
+                                                         g.ny, dkx, dky, ck, cd, scale);
     count_launch();
     msg = fft_transform(fft, psi, g, prec, false, s);
     if (msg) return msg;
-    imag_local_kernel<R, C><<<blocks, 256, 0, s>>>(ps, g, v, cg, cv);
-    sumsq_kernel<C><<<RED_BLOCKS, RED_THREADS, 0, s>>>(ps, g, partials);
-    rescale_kernel<R, C><<<blocks, 256, 0, s>>>(ps, g, partials, target);
+    imag_local_kernel<R, C, NC><<<blocks, 256, 0, s>>>(ps, g, v, cg, cgx, cv);
+    sumsq_kernel<C><<<RED_BLOCKS, RED_THREADS, 0, s>>>(ps, g, NC, partials);
+    rescale_kernel<R, C><<<blocks, 256, 0, s>>>(ps, g, NC, partials, target);
     count_launch(3);
   }
   return cudaGetLastError() == cudaSuccess ? nullptr : "imaginary-time kernel launch failed";
@@ -262,9 +296,12 @@ size_t imag_scratch_doubles() { return RED_BLOCKS + 1; }
 
 const char* imag_steps(FftPair& fft, double* red, void* psi, const Geometry& g, int precision,
                        const void* V, const phx_params& p, long long nsteps, cudaStream_t s) {
+  const bool two = p.spinor != 0;
   if (precision == 64)
-    return imag_steps_t<double, double2>(fft, red, psi, g, V, p, nsteps, s);
-  return imag_steps_t<float, float2>(fft, red, psi, g, V, p, nsteps, s);
+    return two ? imag_steps_t<double, double2, 2>(fft, red, psi, g, V, p, nsteps, s)
+               : imag_steps_t<double, double2, 1>(fft, red, psi, g, V, p, nsteps, s);
+  return two ? imag_steps_t<float, float2, 2>(fft, red, psi, g, V, p, nsteps, s)
+             : imag_steps_t<float, float2, 1>(fft, red, psi, g, V, p, nsteps, s);
 }
 
 SsfCoeffs ssf_coeffs(const phx_params& p) {

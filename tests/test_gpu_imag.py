@@ -59,9 +59,26 @@ def test_harmonic_ground_state_on_gpu():
 
 def test_imag_refuses_unsupported_states():
     m = phx()
-    for kw in (dict(reservoir=True, R=0.1, gamma_r=0.2), dict(spinor=True), dict(bc_y=1)):
+    for kw in (dict(reservoir=True, R=0.1, gamma_r=0.2), dict(bc_y=1)):
         d = synth.base_params(40, 36, 12.0, 10.8, dt=0.01, **kw)
         h = m.phx_create(m.params_from_dict(d, precision=64))
         with pytest.raises(m.PhxError) as e:
             m.phx_step_imag(h, 1)
         assert e.value.status == 6, kw
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_imag_spinor_parity(prec):
+    """Two components with cross-Kerr and TE-TM in imaginary time."""
+    m = phx()
+    real, cplx = (np.float64, np.complex128) if prec == 64 else (np.float32, np.complex64)
+    d = synth.base_params(97, 66, 29.1, 19.8, spinor=True, g=0.3, g_x=0.1, delta_lt=0.2, dt=0.02)
+    psi0, _, _, V = synth.random_state(2, 66, 97, 13, amp=0.7, reservoir=False, smooth=True)
+    psi0, V = rounded(psi0, prec), rounded(V, prec)
+    h = m.phx_create(m.params_from_dict(d, precision=prec))
+    m.phx_set_potential(h, np.ascontiguousarray(V, real))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, cplx))
+    m.phx_step_imag(h, 25)
+    g_psi, _ = get_state(h, prec)
+    o_psi = gp.run_imag(psi0, V, gp.Params(**d), 25)
+    assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
