@@ -327,6 +327,56 @@ def run_ssf(psi, V, p, nsteps, step0=0):
     return psi
 
 
+def ssf_local_reservoir(psi, n, P, V, p, tau):
+    """Local part of Eqs. (PULSE_psi)/(PULSE_res) with the reservoir (no
+    spatial coupling): per site and component
+    dpsi_c/dt = (-(i/hbar)(V + g|psi_c|^2 + g_x|psi_o|^2 + g_r n_c) + (R n_c - gamma_c)/2) psi_c,
+    dn_c/dt = P_c - (gamma_r + R|psi_c|^2) n_c,
+    advanced by one classical RK4 step of length tau (the system has no
+    closed form; reading of the split-step method for the reservoir model)."""
+    nc = psi.shape[0]
+
+    def f(u, m):
+        a = np.abs(u) ** 2
+        fu = np.empty_like(u)
+        fm = np.empty_like(m)
+        for c in range(nc):
+            loc = p.g * a[c] + p.g_r * m[c]
+            if nc == 2:
+                loc = loc + p.g_x * a[1 - c]
+            if V is not None:
+                loc = loc + V
+            fu[c] = -1j / HBAR * loc * u[c] + 0.5 * (p.R * m[c] - p.gamma_c) * u[c]
+            fm[c] = P[c] - (p.gamma_r + p.R * a[c]) * m[c]
+        return fu, fm
+
+    k1 = f(psi, n)
+    k2 = f(psi + 0.5 * tau * k1[0], n + 0.5 * tau * k1[1])
+    k3 = f(psi + 0.5 * tau * k2[0], n + 0.5 * tau * k2[1])
+    k4 = f(psi + tau * k3[0], n + tau * k3[1])
+    return (psi + tau * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]) / 6,
+            n + tau * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]) / 6)
+
+
+def run_ssf_reservoir(psi, n, P, V, p, nsteps, step0=0):
+    """Split-step Fourier for the reservoir model (reading): Strang splitting
+    (psi, n) <- L(dt/2) K(dt) L(dt/2) with the local RK4 step of
+    ssf_local_reservoir and the exact spectral linear propagator of
+    ssf_kinetic acting on psi (n has no linear spatial part), then the
+    per-step noise of run().  Returns (psi, n)."""
+    psi = np.array(psi, dtype=np.complex128)
+    n = np.array(n, dtype=np.float64)
+    P = np.broadcast_to(np.asarray(P, dtype=np.float64), n.shape)
+    V = None if V is None else np.asarray(V, dtype=np.float64)
+    for k in range(nsteps):
+        n_start = n
+        psi, n = ssf_local_reservoir(psi, n, P, V, p, 0.5 * p.dt)
+        psi = ssf_kinetic(psi, p, p.dt)
+        psi, n = ssf_local_reservoir(psi, n, P, V, p, 0.5 * p.dt)
+        psi = add_noise(psi, step0 + k, p, n_start=n_start)
+    return psi, n
+
+
 def run_imag(psi, V, p, nsteps):
     """Imaginary-time propagation (named in the conclusions; no details
     given).  Reading: t -> -i tau in the conservative part of Eq. (PULSE_psi)

@@ -147,3 +147,64 @@ def test_spinor_split_step_agrees_with_the_rk4_path():
     q = p.with_(gamma_c=0.0)
     c = gp.run_ssf(psi, None, q, 40)
     assert abs(np.linalg.norm(c) / np.linalg.norm(psi) - 1) < 1e-12
+
+
+def test_reservoir_split_step_relaxes_to_the_uniform_condensate():
+    """Uniform pump above threshold: the reservoir split-step relaxes to
+    n = gamma_c / R and |psi|^2 = (P/n - gamma_r)/R (the closed-form stationary
+    state of Eqs. PULSE_psi/res), like the RK4 path."""
+    p = gp.Params(nx=4, ny=4, lx=2.0, ly=2.0, reservoir=True, g=6e-3, g_r=1.2e-2,
+                  R=0.01, gamma_c=0.15, gamma_r=0.225, dt=0.05)
+    Pv = 2.0 * gp.pump_threshold(p)
+    P = np.full((1, 4, 4), Pv)
+    psi, n = gp.run_ssf_reservoir(np.full((1, 4, 4), 1.5 + 0j), np.zeros((1, 4, 4)), P, None,
+                                  p, 12000)
+    n_s = p.gamma_c / p.R
+    assert np.allclose(n, n_s, rtol=1e-6)
+    assert np.allclose(np.abs(psi) ** 2, (Pv / n_s - p.gamma_r) / p.R, rtol=1e-6)
+
+
+def spectral_rk4_reservoir(psi, n, P, V, p, T, dt):
+    """Independent reference: RK4 with small dt, spectral Laplacian."""
+    kx = 2 * np.pi * np.fft.fftfreq(p.nx, p.dx)
+    ky = 2 * np.pi * np.fft.fftfreq(p.ny, p.dy)
+    k2 = ky[:, None] ** 2 + kx[None, :] ** 2
+
+    def f(u, m):
+        kin = np.fft.ifft2(k2 * np.fft.fft2(u))
+        fu = -1j / HB * (p.kappa * kin + (V + p.g * np.abs(u) ** 2 + p.g_r * m) * u) \
+            + 0.5 * (p.R * m - p.gamma_c) * u
+        fm = P - (p.gamma_r + p.R * np.abs(u) ** 2) * m
+        return fu, fm
+
+    u, m = psi.copy(), n.copy()
+    for _ in range(int(round(T / dt))):
+        a = f(u, m)
+        b = f(u + 0.5 * dt * a[0], m + 0.5 * dt * a[1])
+        c = f(u + 0.5 * dt * b[0], m + 0.5 * dt * b[1])
+        d = f(u + dt * c[0], m + dt * c[1])
+        u = u + dt * (a[0] + 2 * b[0] + 2 * c[0] + d[0]) / 6
+        m = m + dt * (a[1] + 2 * b[1] + 2 * c[1] + d[1]) / 6
+    return u, m
+
+
+def test_reservoir_split_step_is_second_order():
+    nx, ny, L = 32, 24, 8.0
+    p = gp.Params(nx=nx, ny=ny, lx=L, ly=L * ny / nx, reservoir=True, kappa=0.67, g=0.3,
+                  g_r=0.5, R=0.3, gamma_c=0.2, gamma_r=0.4)
+    x = np.arange(nx) * p.dx
+    y = np.arange(ny) * p.dy
+    psi = (np.exp(-((x[None, :] - 4) ** 2 + (y[:, None] - 3) ** 2) / 2.0)
+           * np.exp(1j * 2 * np.pi * x[None, :] / L)).astype(complex)
+    n = 0.5 + 0.3 * np.cos(2 * np.pi * y[:, None] / p.ly) * np.ones((ny, nx))
+    P = 0.8 + 0.4 * np.sin(2 * np.pi * x[None, :] / L) * np.ones((ny, nx))
+    V = 0.5 * np.cos(2 * np.pi * x[None, :] / L) * np.cos(2 * np.pi * y[:, None] / p.ly)
+    T = 0.8
+    ref_u, ref_m = spectral_rk4_reservoir(psi, n, P, V, p, T, 0.0005)
+    errs = []
+    for dt in (0.04, 0.02, 0.01):
+        u, m = gp.run_ssf_reservoir(psi[None], n[None], P[None], V, p.with_(dt=dt),
+                                    int(round(T / dt)))
+        errs.append(np.linalg.norm(u[0] - ref_u) / np.linalg.norm(ref_u)
+                    + np.linalg.norm(m[0] - ref_m) / np.linalg.norm(ref_m))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
