@@ -172,10 +172,12 @@ phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
  * K(tau) = exp(-(i/hbar) kappa k^2 tau), k = 2 pi m / L, times, for two
  * components, the exponential of the TE-TM block [[0, a], [a*, 0]],
  * a = -Delta_LT (k_x - i k_y)^2 (cuFFT, loaded at the first call); then the
- * step's noise as in phx_step_n.  Same dt, clock and state as phx_step_n
- * (the two may alternate).  ESTATE unless the handle has no reservoir, is
- * periodic in x and y, and has neither a drive nor truncated-Wigner noise;
- * ECUDA if cuFFT is missing. */
+ * step's noise as in phx_step_n.  With a reservoir, each local half step
+ * integrates psi and n together by one RK4 step of dt/2 (the local system
+ * has no closed form) and the linear step acts on psi only.  Same dt, clock
+ * and state as phx_step_n (the two may alternate).  ESTATE unless the
+ * handle is periodic in x and y and has neither a drive nor truncated-Wigner
+ * noise; ECUDA if cuFFT is missing. */
 phx_status phx_step_ssf(phx_handle* h, int64_t nsteps);
 
 /* nsteps imaginary-time steps (t -> -i tau in the conservative part of

@@ -672,7 +672,6 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
 phx_status phx_step_ssf(phx_handle* h, int64_t nsteps) {
   if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(h, PHX_EINVAL, "nsteps must be >= 0");
-  if (h->m.reservoir) return fail(h, PHX_ESTATE, "split-step needs a field without reservoir");
   if (h->p.bc_x != PHX_BC_PERIODIC || h->p.bc_y != PHX_BC_PERIODIC)
     return fail(h, PHX_ESTATE, "split-step needs periodic boundaries");
   if (h->has_E || h->p.wigner_nu > 0.0)
@@ -686,14 +685,21 @@ phx_status phx_step_ssf(phx_handle* h, int64_t nsteps) {
   const SsfCoeffs k = ssf_coeffs(h->p);
   const NoiseKey nz = make_noise_key(h->p);
   for (int64_t s = 0; s < nsteps; ++s) {
-    msg = ssf_step(h->ssf_fft, h->psi[h->cur], h->geo, h->m.precision, h->m.ncomp,
-                   h->has_V ? h->V : nullptr, k, nz, h->clock, h->parity, h->stream);
+    if (h->m.reservoir)
+      msg = ssf_step_reservoir(h->ssf_fft, h->psi[h->cur], h->n[h->cur], h->P, h->P_stride,
+                               h->geo, h->m.precision, h->m.ncomp, h->has_V ? h->V : nullptr,
+                               h->p, k, nz, h->clock, h->parity, h->stream);
+    else
+      msg = ssf_step(h->ssf_fft, h->psi[h->cur], h->geo, h->m.precision, h->m.ncomp,
+                     h->has_V ? h->V : nullptr, k, nz, h->clock, h->parity, h->stream);
     if (msg) return fail(h, PHX_ECUDA, msg);
     h->parity ^= 1;
     h->host_step += 1;
   }
   PHX_CK(h, launch_fill_ghosts(h->psi[h->cur], (int)(2 * h->esize), h->m.ncomp, h->geo,
                                h->stream));
+  if (h->m.reservoir)
+    PHX_CK(h, launch_fill_ghosts(h->n[h->cur], (int)h->esize, h->m.ncomp, h->geo, h->stream));
   return PHX_OK;
 }
 

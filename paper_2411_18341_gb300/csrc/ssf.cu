@@ -223,6 +223,102 @@ __global__ void rescale_kernel(C* psi, Geometry g, int ncomp, const double* part
   }
 }
 
+// Local part with the reservoir (no closed form): one classical RK4 step of
+// length tau of, per site and component,
+//   dpsi_c/dt = (-(i/hbar)(V + g|psi_c|^2 + g_x|psi_o|^2 + g_r n_c) + (R n_c - gamma_c)/2) psi_c,
+//   dn_c/dt = P_c - (gamma_r + R|psi_c|^2) n_c,
+// in place; with `last` also the step's noise and the clock update.
+struct LocalRes {
+  double g, gx, gr, ih;    // g/hbar, g_x/hbar, g_r/hbar, 1/hbar (multiplies V)
+  double hR, hgc, R, gam;  // R/2, gamma_c/2, R, gamma_r
+  double tau;
+};
+
+template <typename R, typename C, int NC>
+__global__ void ssf_local_res_kernel(C* psi, R* n, const R* P, long long P_stride, Geometry g,
+                                     const R* V, LocalRes q, NoiseKey nz, DevClock* clock,
+                                     int parity, int last, double dt64) {
+  const long long sites = (long long)g.nx * g.ny;
+  const long long step = clock->step[parity];
+  if (last && blockIdx.x == 0 && threadIdx.x == 0) {
+    clock->step[parity ^ 1] = step + 1;
+    clock->t[parity ^ 1] = clock->t[parity] + dt64;
+  }
+  const R cg = (R)q.g, cgx = (R)q.gx, cgr = (R)q.gr, cih = (R)q.ih;
+  const R hR = (R)q.hR, hgc = (R)q.hgc, cR = (R)q.R, cgam = (R)q.gam, tau = (R)q.tau;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < sites;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
+    const long long off = (long long)(j + HALO) * g.pitch + i + HALO;
+    const R vloc = V ? cih * V[off] : R(0);
+    C u0[NC];
+    R m0[NC], Pc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      u0[c] = psi[c * g.plane + off];
+      m0[c] = n[c * g.plane + off];
+      Pc[c] = P[c * P_stride + off];
+    }
+    C u[NC], au[NC];
+    R m[NC], am[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      u[c] = u0[c];
+      m[c] = m0[c];
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const R w = (s == 0 || s == 3) ? R(1) : R(2);
+      const R cs = (s == 2) ? tau : R(0.5) * tau;
+      R a[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) a[c] = u[c].x * u[c].x + u[c].y * u[c].y;
+      C ku[NC];
+      R km[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        R loc = cg * a[c] + cgr * m[c] + vloc;
+        if (NC == 2) loc += cgx * a[NC - 1 - c];
+        const R G = hR * m[c] - hgc;
+        ku[c].x = loc * u[c].y + G * u[c].x;
+        ku[c].y = -loc * u[c].x + G * u[c].y;
+        km[c] = Pc[c] - (cgam + cR * a[c]) * m[c];
+        if (s == 0) {
+          au[c] = ku[c];
+          am[c] = km[c];
+        } else {
+          au[c].x += w * ku[c].x;
+          au[c].y += w * ku[c].y;
+          am[c] += w * km[c];
+        }
+      }
+      if (s < 3) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          u[c].x = u0[c].x + cs * ku[c].x;
+          u[c].y = u0[c].y + cs * ku[c].y;
+          m[c] = m0[c] + cs * km[c];
+        }
+      }
+    }
+    float2 xi[2];
+    if (last && nz.on) nz_site(nz.seed, nz.instance, step, (uint32_t)t, nz.scale, xi[0], xi[1], NC == 2);
+    const R t6 = tau / R(6);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      C o;
+      o.x = u0[c].x + t6 * au[c].x;
+      o.y = u0[c].y + t6 * au[c].y;
+      if (last && nz.on) {
+        o.x = o.x + R(xi[c].x);
+        o.y = o.y + R(xi[c].y);
+      }
+      psi[c * g.plane + off] = o;
+      n[c * g.plane + off] = m0[c] + t6 * am[c];
+    }
+  }
+}
+
 int grid_for(long long n) {
   const long long b = (n + 255) / 256;
   return (int)(b < 8192 ? (b < 1 ? 1 : b) : 8192);
@@ -290,7 +386,59 @@ const char* imag_steps_t(FftPair& fft, double* red, void* psi, const Geometry& g
   return cudaGetLastError() == cudaSuccess ? nullptr : "imaginary-time kernel launch failed";
 }
 
+template <typename R, typename C, int NC>
+const char* ssf_res_step_t(FftPair& fft, void* psi, void* n, const void* P, long long P_stride,
+                           const Geometry& g, const void* V, const SsfCoeffs& k,
+                           const LocalRes& q, const NoiseKey& nz, DevClock* clock, int parity,
+                           cudaStream_t s) {
+  C* p = static_cast<C*>(psi);
+  R* nn = static_cast<R*>(n);
+  const R* pp = static_cast<const R*>(P);
+  const R* v = static_cast<const R*>(V);
+  const int blocks = grid_for((long long)g.nx * g.ny);
+  ssf_local_res_kernel<R, C, NC><<<blocks, 256, 0, s>>>(p, nn, pp, P_stride, g, v, q, nz, clock,
+                                                        parity, 0, k.dt);
+  count_launch();
+  const char* msg = fft_transform(fft, psi, g, sizeof(R) == 8 ? 64 : 32, true, s);
+  if (msg) return msg;
+  ssf_kinetic_kernel<R, C, NC><<<blocks, 256, 0, s>>>(static_cast<C*>(fft.scratch), g.nx, g.ny,
+                                                      (R)k.dkx, (R)k.dky, (R)k.kin, (R)k.tetm,
+                                                      (R)k.scale);
+  count_launch();
+  msg = fft_transform(fft, psi, g, sizeof(R) == 8 ? 64 : 32, false, s);
+  if (msg) return msg;
+  ssf_local_res_kernel<R, C, NC><<<blocks, 256, 0, s>>>(p, nn, pp, P_stride, g, v, q, nz, clock,
+                                                        parity, 1, k.dt);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? nullptr : "split-step kernel launch failed";
+}
+
 }  // namespace
+
+const char* ssf_step_reservoir(FftPair& fft, void* psi, void* n, const void* P,
+                               long long P_stride, const Geometry& g, int precision, int ncomp,
+                               const void* V, const phx_params& p, const SsfCoeffs& k,
+                               const NoiseKey& nz, DevClock* clock, int parity, cudaStream_t s) {
+  LocalRes q;
+  q.g = p.g / HBAR;
+  q.gx = p.g_x / HBAR;
+  q.gr = p.g_r / HBAR;
+  q.ih = 1.0 / HBAR;
+  q.hR = 0.5 * p.R;
+  q.hgc = 0.5 * p.gamma_c;
+  q.R = p.R;
+  q.gam = p.gamma_r;
+  q.tau = 0.5 * p.dt;
+  if (precision == 64)
+    return ncomp == 2 ? ssf_res_step_t<double, double2, 2>(fft, psi, n, P, P_stride, g, V, k, q,
+                                                            nz, clock, parity, s)
+                      : ssf_res_step_t<double, double2, 1>(fft, psi, n, P, P_stride, g, V, k, q,
+                                                            nz, clock, parity, s);
+  return ncomp == 2 ? ssf_res_step_t<float, float2, 2>(fft, psi, n, P, P_stride, g, V, k, q, nz,
+                                                        clock, parity, s)
+                    : ssf_res_step_t<float, float2, 1>(fft, psi, n, P, P_stride, g, V, k, q, nz,
+                                                        clock, parity, s);
+}
 
 size_t imag_scratch_doubles() { return RED_BLOCKS + 1; }
 

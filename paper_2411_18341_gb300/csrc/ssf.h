@@ -30,6 +30,13 @@ const char* ssf_step(FftPair& fft, void* psi, const Geometry& g, int precision, 
                      const void* V, const SsfCoeffs& k, const NoiseKey& nz, DevClock* clock,
                      int parity, cudaStream_t s);
 
+// One step of the reservoir model: the local half steps integrate psi and n
+// together (one RK4 step of dt/2 each), the linear step acts on psi.
+const char* ssf_step_reservoir(FftPair& fft, void* psi, void* n, const void* P,
+                               long long P_stride, const Geometry& g, int precision, int ncomp,
+                               const void* V, const phx_params& p, const SsfCoeffs& k,
+                               const NoiseKey& nz, DevClock* clock, int parity, cudaStream_t s);
+
 // Imaginary-time split-step steps with the norm kept at its value at the
 // start (the ground state of the conservative scalar Hamiltonian); red is
 // device scratch of imag_scratch_doubles() doubles.  The clock does not move.

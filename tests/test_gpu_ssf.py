@@ -72,7 +72,7 @@ def test_ssf_conservative_keeps_norm_and_alternates_with_rk4(prec):
 
 def test_ssf_refuses_unsupported_states():
     m = phx()
-    for kw in (dict(reservoir=True, R=0.1, gamma_r=0.2), dict(bc_x=1), dict(wigner_nu=1.0)):
+    for kw in (dict(bc_x=1), dict(wigner_nu=1.0)):
         d = params(40, 36, **kw)
         h = m.phx_create(m.params_from_dict(d, precision=64))
         with pytest.raises(m.PhxError) as e:
@@ -105,3 +105,36 @@ def test_ssf_spinor_parity(prec, tetm):
     g_psi, _ = get_state(h, prec)
     o_psi = gp.run_ssf(psi0, V, gp.Params(**d), 10)
     assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("spinor", [False, True])
+def test_ssf_reservoir_parity(prec, spinor):
+    """Reservoir model: local half steps integrate psi and n together (one RK4
+    step each), the spectral linear step acts on psi; separate pump planes
+    for two components; noise."""
+    m = phx()
+    real, cplx = (np.float64, np.complex128) if prec == 64 else (np.float32, np.complex64)
+    kw = dict(spinor=True, g_x=0.1, delta_lt=0.2) if spinor else {}
+    d = synth.base_params(83, 58, 24.9, 17.4, g=0.3, g_r=0.5, R=0.3, gamma_c=0.15, gamma_r=0.4,
+                          reservoir=True, noise_var=1e-4, seed=47, **kw)
+    d["dt"] = min(0.45 * gp.stability_dt_max(gp.Params(**d)), 0.05)
+    nc = 2 if spinor else 1
+    psi0, n0, P, V = synth.random_state(nc, 58, 83, 15, amp=0.7, smooth=True)
+    psi0, n0, P, V = (rounded(x, prec) for x in (psi0, n0, P, V))
+    h = m.phx_create(m.params_from_dict(d, precision=prec))
+    m.phx_set_pump(h, *[np.ascontiguousarray(P[c], real) for c in range(nc)])
+    m.phx_set_potential(h, np.ascontiguousarray(V, real))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, cplx), np.ascontiguousarray(n0, real))
+    m.phx_set_time(h, 7, 0.0)
+    m.phx_step_ssf(h, 9)
+    g_psi, g_n = get_state(h, prec)
+    o_psi, o_n = gp.run_ssf_reservoir(psi0, n0, P, V, gp.Params(**d), 9, step0=7)
+    assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
+    assert rel_l2(g_n, o_n) <= TOL[prec], rel_l2(g_n, o_n)
+    # RK4 steps continue from the split-step state (ghost rings refilled)
+    m.phx_step_n(h, 3)
+    g_psi, g_n = get_state(h, prec)
+    o_psi, o_n = gp.run(o_psi, o_n, P, V, gp.Params(**d), 3, step0=16)
+    assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
+    assert rel_l2(g_n, o_n) <= TOL[prec], rel_l2(g_n, o_n)
