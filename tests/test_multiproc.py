@@ -73,3 +73,18 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2
     assert rec["value"] > 0 and rec["cpu_baseline"]["kind"] == "oracle"
     assert rec["e2e"]["h2d_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("workload", ["ensemble", "twa_ensemble"])
+def test_reference_arm_for_batched_workloads(workload):
+    """The reference arm (the oracle, timed on the host) runs on a bounded
+    sample of each batched workload and prints the contract's JSON line."""
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1",
+           "--workload", workload]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    rec = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert rec["impl"] == "reference" and rec["config"]["workload"] == workload
+    assert rec["value"] > 0 and rec["unit"] == "site-updates/s" and rec["higher_is_better"]
+    assert rec["cpu_baseline"]["cores"] == 1 and rec["e2e"]["d2h_bytes_per_step"] == 0
