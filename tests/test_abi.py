@@ -134,3 +134,48 @@ def test_buffer_sizes_are_the_padded_layout(phx):
     with pytest.raises(phx.PhxError) as e:
         phx.phx_buffer_sizes(phx.phx_params_init(nx=0))
     assert e.value.status == 1
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "phx.h"
+int main(void) {
+  phx_params p;
+  double dt = 0.0;
+  size_t sizes[5];
+  if (phx_params_init(&p) != PHX_OK) return 1;
+  p.nx = 128; p.ny = 96; p.lx = 40.0; p.ly = 30.0;
+  if (phx_stability_dt(&p, &dt) != PHX_OK) return 2;
+  p.dt = 0.5 * dt;
+  if (phx_buffer_sizes(&p, sizes) != PHX_OK) return 3;
+  p.nx = 0;
+  if (phx_stability_dt(&p, &dt) != PHX_EINVAL) return 4;
+  printf("%.17g %lu\n", 2.0 * p.dt, (unsigned long)sizes[0]);
+  return 0;
+}
+"""
+
+
+def test_plain_c_client_compiles_links_and_runs(phx, tmp_path):
+    """The boundary is a C ABI: a strict C99 program (-pedantic -Werror)
+    includes the header, links the shared library and calls its host-only
+    entry points, which agree with the oracle."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    lib_dir = os.path.dirname(phx.LIB_PATH)
+    exe = tmp_path / "client"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-L", lib_dir, "-lphx",
+                        "-Wl,-rpath," + lib_dir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.returncode
+    dt, size0 = out.stdout.split()
+    want = gp.stability_dt_max(gp.Params(nx=128, ny=96, lx=40.0, ly=30.0))
+    assert abs(float(dt) - want) <= 1e-12 * want
+    pitch = -(-(128 + 8) // 32) * 32
+    assert int(size0) == pitch * (96 + 8) * 8
