@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--rk4-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--integrator", default="rk4", choices=["rk4", "ssf"],
+                    help="time stepper of the single-handle workloads: fused RK4 or split-step Fourier")
     ap.add_argument("--tile", type=int, default=0,
                     help="step-kernel configuration (0 = autotune, 1..7 TMA-fed, 9 generic)")
     return ap.parse_args()
@@ -529,11 +531,13 @@ def main():
         phx.phx_set_drive(h, E_d)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    step_fn = phx.phx_step_ssf if args.integrator == "ssf" else phx.phx_step_n
+
     def one_step(ev_k0=None, ev_k1=None):
         phx.phx_set_state(h, psi0_d, n0_d)
         if ev_k0 is not None:
             ev_k0.record(stream)
-        phx.phx_step_n(h, rk4_steps)
+        step_fn(h, rk4_steps)
         if ev_k1 is not None:
             ev_k1.record(stream)
         phx.phx_norm_energy(h)
@@ -587,7 +591,7 @@ def main():
         if E_h is not None:
             phx.phx_set_drive(h, E_h)
         phx.phx_set_state(h, psi_h, n_h)
-        phx.phx_step_n(h, rk4_steps)
+        step_fn(h, rk4_steps)
         phx.phx_norm_energy(h)
         phx.phx_residual(h)
         phx.phx_get_state(h, out_psi, out_n)
@@ -612,7 +616,7 @@ def main():
     kern_s = float(np.mean(kern_ms)) * 1e-3 / rk4_steps
     achieved = bps * sites / kern_s / 1e9
     traffic = recorded_traffic(wname, prec, phx.phx_tile(h))
-    if prec == 64 and kind in FLOPS_PER_SITE:
+    if prec == 64 and kind in FLOPS_PER_SITE and args.integrator == "rk4":
         # the FP64 stencil is bound by the FP64 pipe, not by HBM
         tf = FLOPS_PER_SITE[kind] * sites / kern_s / 1e12
         roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -624,13 +628,19 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                 "traffic": traffic,
-                "kernel": "rk4_f32_tma (fused, one launch per RK4 step)"
-                          if 1 <= phx.phx_tile(h) <= 7
-                          else "rk4_step_generic (fused, one launch per RK4 step)",
+                "kernel": ("split-step (local kernels + cuFFT round trip per step)"
+                           if args.integrator == "ssf" else
+                           "rk4_f32_tma (fused, one launch per RK4 step)"
+                           if 1 <= phx.phx_tile(h) <= 7
+                           else "rk4_step_generic (fused, one launch per RK4 step)"),
                 "algorithmic_bytes_per_site": bps,
                 "avg_launch_us": kern_s * 1e6,
                 "peak_source": pk_kind}
-        if d.get("noise_var", 0) > 0 or d.get("wigner_nu", 0) > 0:
+        if args.integrator == "ssf":
+            roof["note"] = ("split-step: the FFT round trip re-reads the state several times per "
+                            "step; traffic is not the fused kernel's")
+            roof["traffic"] = None
+        elif d.get("noise_var", 0) > 0 or d.get("wigner_nu", 0) > 0:
             roof["note"] = ("per-site Philox + Box-Muller noise every step: the kernel is bound by "
                             "instruction issue, not by HBM")
         elif sites * bps < 129e6:
@@ -643,10 +653,11 @@ def main():
         "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
         "config": {"workload": wname, "description": desc,
                    "grid": "%dx%d" % (nx, ny), "rk4_steps_per_step": rk4_steps,
-                   "per_step": "set_state + %d fused RK4 steps + FP64 norm/energy + "
-                               "FP64 residual" % rk4_steps,
+                   "per_step": "set_state + %d %s + FP64 norm/energy + FP64 residual" % (
+                       rk4_steps, "split-step Fourier steps" if args.integrator == "ssf"
+                       else "fused RK4 steps"),
                    "l2": l2_note,
-                   "tile": phx.phx_tile(h),
+                   "tile": phx.phx_tile(h), "integrator": args.integrator,
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": world * sites * rk4_steps / e2e_s, "unit": "site-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
