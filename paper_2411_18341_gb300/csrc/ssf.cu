@@ -228,15 +228,18 @@ __global__ void rescale_kernel(C* psi, Geometry g, int ncomp, const double* part
 //   dpsi_c/dt = (-(i/hbar)(V + g|psi_c|^2 + g_x|psi_o|^2 + g_r n_c) + (R n_c - gamma_c)/2) psi_c,
 //   dn_c/dt = P_c - (gamma_r + R|psi_c|^2) n_c,
 // in place; with `last` also the step's noise and the clock update.
+// Coefficients arrive in the stencil precision (a double-to-float conversion
+// per thread would run on the narrow FP64 pipe).
+template <typename R>
 struct LocalRes {
-  double g, gx, gr, ih;    // g/hbar, g_x/hbar, g_r/hbar, 1/hbar (multiplies V)
-  double hR, hgc, R, gam;  // R/2, gamma_c/2, R, gamma_r
-  double tau;
+  R g, gx, gr, ih;    // g/hbar, g_x/hbar, g_r/hbar, 1/hbar (multiplies V)
+  R hR, hgc, Rg, gam; // R/2, gamma_c/2, R, gamma_r
+  R tau;
 };
 
 template <typename R, typename C, int NC>
 __global__ void ssf_local_res_kernel(C* psi, R* n, const R* P, long long P_stride, Geometry g,
-                                     const R* V, LocalRes q, NoiseKey nz, DevClock* clock,
+                                     const R* V, LocalRes<R> q, NoiseKey nz, DevClock* clock,
                                      int parity, int last, double dt64) {
   const long long sites = (long long)g.nx * g.ny;
   const long long step = clock->step[parity];
@@ -244,8 +247,8 @@ __global__ void ssf_local_res_kernel(C* psi, R* n, const R* P, long long P_strid
     clock->step[parity ^ 1] = step + 1;
     clock->t[parity ^ 1] = clock->t[parity] + dt64;
   }
-  const R cg = (R)q.g, cgx = (R)q.gx, cgr = (R)q.gr, cih = (R)q.ih;
-  const R hR = (R)q.hR, hgc = (R)q.hgc, cR = (R)q.R, cgam = (R)q.gam, tau = (R)q.tau;
+  const R cg = q.g, cgx = q.gx, cgr = q.gr, cih = q.ih;
+  const R hR = q.hR, hgc = q.hgc, cR = q.Rg, cgam = q.gam, tau = q.tau;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < sites;
        t += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(t / g.nx), i = (int)(t - (long long)j * g.nx);
@@ -389,8 +392,18 @@ const char* imag_steps_t(FftPair& fft, double* red, void* psi, const Geometry& g
 template <typename R, typename C, int NC>
 const char* ssf_res_step_t(FftPair& fft, void* psi, void* n, const void* P, long long P_stride,
                            const Geometry& g, const void* V, const SsfCoeffs& k,
-                           const LocalRes& q, const NoiseKey& nz, DevClock* clock, int parity,
+                           const phx_params& pp_, const NoiseKey& nz, DevClock* clock, int parity,
                            cudaStream_t s) {
+  LocalRes<R> q;
+  q.g = (R)(pp_.g / HBAR);
+  q.gx = (R)(pp_.g_x / HBAR);
+  q.gr = (R)(pp_.g_r / HBAR);
+  q.ih = (R)(1.0 / HBAR);
+  q.hR = (R)(0.5 * pp_.R);
+  q.hgc = (R)(0.5 * pp_.gamma_c);
+  q.Rg = (R)pp_.R;
+  q.gam = (R)pp_.gamma_r;
+  q.tau = (R)(0.5 * pp_.dt);
   C* p = static_cast<C*>(psi);
   R* nn = static_cast<R*>(n);
   const R* pp = static_cast<const R*>(P);
@@ -419,24 +432,14 @@ const char* ssf_step_reservoir(FftPair& fft, void* psi, void* n, const void* P,
                                long long P_stride, const Geometry& g, int precision, int ncomp,
                                const void* V, const phx_params& p, const SsfCoeffs& k,
                                const NoiseKey& nz, DevClock* clock, int parity, cudaStream_t s) {
-  LocalRes q;
-  q.g = p.g / HBAR;
-  q.gx = p.g_x / HBAR;
-  q.gr = p.g_r / HBAR;
-  q.ih = 1.0 / HBAR;
-  q.hR = 0.5 * p.R;
-  q.hgc = 0.5 * p.gamma_c;
-  q.R = p.R;
-  q.gam = p.gamma_r;
-  q.tau = 0.5 * p.dt;
   if (precision == 64)
-    return ncomp == 2 ? ssf_res_step_t<double, double2, 2>(fft, psi, n, P, P_stride, g, V, k, q,
+    return ncomp == 2 ? ssf_res_step_t<double, double2, 2>(fft, psi, n, P, P_stride, g, V, k, p,
                                                             nz, clock, parity, s)
-                      : ssf_res_step_t<double, double2, 1>(fft, psi, n, P, P_stride, g, V, k, q,
+                      : ssf_res_step_t<double, double2, 1>(fft, psi, n, P, P_stride, g, V, k, p,
                                                             nz, clock, parity, s);
-  return ncomp == 2 ? ssf_res_step_t<float, float2, 2>(fft, psi, n, P, P_stride, g, V, k, q, nz,
+  return ncomp == 2 ? ssf_res_step_t<float, float2, 2>(fft, psi, n, P, P_stride, g, V, k, p, nz,
                                                         clock, parity, s)
-                    : ssf_res_step_t<float, float2, 1>(fft, psi, n, P, P_stride, g, V, k, q, nz,
+                    : ssf_res_step_t<float, float2, 1>(fft, psi, n, P, P_stride, g, V, k, p, nz,
                                                         clock, parity, s);
 }
 
