@@ -83,3 +83,21 @@ def test_time_origin_carries_over():
         t = t + p.dt
     b, _ = gp.run(b1, None, None, None, p, 10, step0=10, E=E, t0=t)
     assert np.array_equal(a, b)
+
+
+def test_windowed_step_with_drive_equals_full_grid_step():
+    """oracle.gp.step_at_sites (the full-size sampled parity) with a drive and
+    a time origin equals the full-grid step at every sampled site."""
+    import synth
+    p = gp.Params(nx=23, ny=19, lx=7.0, ly=6.0, g=0.2, gamma_c=0.1, drive_omega=1.7,
+                  noise_var=1e-3, seed=5)
+    p = p.with_(dt=0.4 * gp.stability_dt_max(p))
+    psi, _, _, V = synth.random_state(1, 19, 23, 11, reservoir=False)
+    rng = np.random.default_rng(6)
+    E = (rng.normal(size=(1, 19, 23)) + 1j * rng.normal(size=(1, 19, 23))) * 0.2
+    t0 = 2.35
+    full, _ = gp.run(psi, None, None, V, p, 1, step0=4, E=E, t0=t0)
+    sites = [(0, 0), (18, 22), (0, 22), (9, 11), (5, 0)]
+    sp, _ = gp.step_at_sites(psi, None, None, V, p, sites, step=4, E=E, t=t0)
+    for k, (j, i) in enumerate(sites):
+        assert abs(sp[0, k] - full[0, j, i]) < 1e-13
