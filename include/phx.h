@@ -186,8 +186,8 @@ phx_status phx_step_ssf(phx_handle* h, int64_t nsteps);
  * A = exp(-(V + g|psi_c|^2 + g_x|psi_o|^2) dt/(2 hbar)) (densities frozen within
  * the factor) and B = exp(-H_k dt/hbar) in Fourier space (kappa k^2 and, for
  * two components, the TE-TM block), then psi rescaled to the norm it had
- * when the call began.  Converges to the ground state; loss, gain and noise
- * take no part and the clock does not move.  ESTATE unless the handle has no
+ * when the call began.  Converges to the ground state; loss, gain, drive and
+ * noise take no part and the clock does not move.  ESTATE unless the handle has no
  * reservoir and is periodic in x and y; ECUDA if cuFFT is missing. */
 phx_status phx_step_imag(phx_handle* h, int64_t nsteps);
 
