@@ -38,9 +38,11 @@ constexpr int NA_MAX_DEVICES = 64;
 // this array.
 __device__ __align__(256) double g_na_scratch[2 * NA_MAX_BLOCKS + 2];
 
+// Device address of the scratch per device, looked up once per device (a
+// failed look-up is retried on the next call; the lock keeps threads that
+// call at the same time from racing on the slot).
 double* g_na_ptr[NA_MAX_DEVICES] = {nullptr};
-std::once_flag g_na_once[NA_MAX_DEVICES];
-cudaError_t g_na_err[NA_MAX_DEVICES];
+std::mutex g_na_mu;
 
 __device__ __forceinline__ double na_warp_sum(double v) {
 #pragma unroll
@@ -227,13 +229,22 @@ extern "C" phx_status phx_norm_energy_static(const phx_params* p, const void* ps
   if (e != cudaSuccess) return na_fail(PHX_ENODEV, cudaGetErrorString(e));
   if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(PHX_ENODEV, "device index too large");
   // Set-up, once per device, with that device current: the device address of
-  // the static scratch (its host-side name is only a stand-in).
-  std::call_once(g_na_once[dev], [dev]() {
-    g_na_err[dev] = cudaGetSymbolAddress((void**)&g_na_ptr[dev], g_na_scratch);
-  });
-  if (g_na_err[dev] != cudaSuccess || !g_na_ptr[dev])
-    return na_fail(PHX_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
-  double* scratch = g_na_ptr[dev];
+  // the static scratch (its host-side name is only a stand-in).  A look-up
+  // that failed leaves the slot empty and is tried again by the next call.
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+      double* ptr = nullptr;
+      e = cudaGetSymbolAddress((void**)&ptr, g_na_scratch);
+      if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();  // clear it: the next call starts clean
+        return na_fail(PHX_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
+      }
+      g_na_ptr[dev] = ptr;
+    }
+    scratch = g_na_ptr[dev];
+  }
 
   const double dx = p->lx / p->nx, dy = p->ly / p->ny;
   NaPhys a;
