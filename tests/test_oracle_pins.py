@@ -432,6 +432,32 @@ def test_derived_constants_file_matches_oracle():
     assert c["pump_threshold"] == pytest.approx(0.15 * 0.225 / 0.01)
 
 
+@pytest.mark.parametrize("factor,grows", [(0.9, False), (1.1, True), (0.97, False),
+                                           (1.03, True)])
+def test_pump_threshold_from_the_dynamics(factor, grows):
+    """gp.pump_threshold pinned by the equations' own dynamics rather than by
+    its formula: a uniform pump factor * P_thr on a periodic grid, the
+    reservoir started at its psi = 0 value P / gamma_r, a weak uniform psi.
+    Below the threshold the condensate amplitude decays, above it grows (the
+    amplitude stays far below saturation, so depletion plays no part); the
+    net rate is (R P / gamma_r - gamma_c) / 2 for |psi|^2, i.e. the sign
+    flips exactly at P = P_thr."""
+    p = gp.Params(nx=2, ny=2, lx=4.0, ly=4.0, **{k: v for k, v in synth.reservoir_physics().items()})
+    p = p.with_(dt=0.25)
+    Pv = factor * gp.pump_threshold(p)
+    psi0 = np.full((1, 2, 2), 1e-4 + 0j)
+    n0 = np.full((1, 2, 2), Pv / p.gamma_r)
+    P = np.full((1, 2, 2), Pv)
+    steps = 2400 if abs(factor - 1) > 0.05 else 4800   # 600 / 1200 ps
+    psi, n = gp.run(psi0, n0, P, None, p, steps)
+    ratio = float(np.mean(np.abs(psi) ** 2) / np.mean(np.abs(psi0) ** 2))
+    expected = np.exp((p.R * Pv / p.gamma_r - p.gamma_c) * steps * p.dt)
+    assert (ratio > 1.0) == grows, ratio
+    # and at the rate the linear analysis gives (RK4 error at dt = 0.25 ps
+    # is far below 1 %)
+    assert ratio == pytest.approx(expected, rel=1e-2)
+
+
 @pytest.mark.parametrize("bc,nu", [(gp.PERIODIC, 0.0), (gp.ZERO, 0.0), (gp.PERIODIC, 1.5)])
 def test_windowed_step_equals_full_grid_step(bc, nu):
     """oracle.gp.step_at_sites (used for sampled parity at full size) equals
