@@ -285,6 +285,10 @@ phx_status phx_batch_create(const phx_params* params, int32_t count, phx_batch**
   b->stream = static_cast<cudaStream_t>(params[0].stream);
   b->reservoir = params[0].reservoir != 0;
   b->p.assign(params, params + count);
+  // params[0].tile fixes the step-kernel configuration (a TMA-fed one);
+  // 0 (or any other value) leaves it to the autotuner
+  if (params[0].tile >= TILE_64x64 && params[0].tile <= TILE_64x32_M4_2)
+    b->tile_cfg = params[0].tile;
   b->h_inst.resize(count);
   b->has_V.assign(count, 0);
   b->V.assign(count, nullptr);

@@ -59,3 +59,11 @@ def rel_l2(a, b):
 
 
 TOL = {64: 1e-11, 32: 1e-4}
+
+
+# FP32 scalar step configurations of the TMA-fed persistent kernel
+TMA_SCALAR_TILES = [1, 2, 3, 4, 5, 6, 7]
+
+
+def tma_scalar(tile):
+    return tile in TMA_SCALAR_TILES

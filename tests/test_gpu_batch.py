@@ -29,9 +29,9 @@ def members(sizes, reservoir=True, seed0=40, bc=(0, 0)):
     return out
 
 
-def make_batch(ms):
+def make_batch(ms, tile=0):
     m = phx()
-    b = m.phx_batch_create([m.params_from_dict(d, precision=32) for d, *_ in ms])
+    b = m.phx_batch_create([m.params_from_dict(d, precision=32, tile=tile) for d, *_ in ms])
     for i, (d, psi0, n0, P) in enumerate(ms):
         if P is not None:
             m.phx_batch_set_pump(b, i, np.ascontiguousarray(P[0], np.float32))
@@ -63,6 +63,23 @@ def test_batch_members_match_oracle(steps, reservoir):
         assert rel_l2(g_psi, o_psi) <= 1e-4, (i, rel_l2(g_psi, o_psi))
         if reservoir:
             assert rel_l2(g_n, o_n) <= 1e-4
+
+
+@pytest.mark.parametrize("tile", [1, 3, 4, 6, 7])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 0)])
+def test_batch_fixed_tile_configs(tile, bc):
+    """Every member against the oracle with the step kernel configuration
+    fixed (the per-tile instance table of the persistent kernel), uneven
+    grids, graph and non-graph step counts."""
+    ms = members(SIZES, True, bc=bc)
+    b = make_batch(ms, tile=tile)
+    phx().phx_batch_step_n(b, 27)
+    assert phx().phx_batch_tile(b) == tile
+    for i, (d, psi0, n0, P) in enumerate(ms):
+        g_psi, g_n = member_state(b, i, d)
+        o_psi, o_n = gp.run(psi0, n0, P, None, gp.Params(**d), 27)
+        assert rel_l2(g_psi, o_psi) <= 1e-4, (i, rel_l2(g_psi, o_psi))
+        assert rel_l2(g_n, o_n) <= 1e-4
 
 
 def test_batch_equals_single_handles_and_zero_bc():

@@ -7,7 +7,7 @@ import pytest
 
 from oracle import gp
 import synth
-from gpu_util import phx, get_state, rel_l2, rounded, TOL
+from gpu_util import phx, get_state, rel_l2, rounded, TOL, TMA_SCALAR_TILES
 
 pytestmark = pytest.mark.gpu
 
@@ -113,7 +113,7 @@ def test_drive_changes_the_state_and_can_be_removed(prec):
     g2, _ = get_state(h, prec)
     assert rel_l2(g2, u_psi) <= TOL[prec]
     if prec == 32:
-        assert m.phx_tile(h) in range(1, 8)
+        assert m.phx_tile(h) in TMA_SCALAR_TILES
 
 
 @pytest.mark.parametrize("prec", [64, 32])
@@ -146,7 +146,7 @@ def test_drive_tma_scalar_kernel(tile, bc):
     E = smooth_field(1, 77, 131, 8, 0.4)
     h, (g_psi, _), (o_psi, _) = run_driven(d, 32, E, False, steps=11, tile=tile)
     assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
-    assert m.phx_tile(h) in range(1, 8)
+    assert m.phx_tile(h) in TMA_SCALAR_TILES
     if tile:
         assert m.phx_tile(h) == tile
 
@@ -158,4 +158,4 @@ def test_drive_tma_with_truncated_wigner_noise(tile):
     E = smooth_field(1, 66, 97, 9, 0.3)
     h, (g_psi, _), (o_psi, _) = run_driven(d, 32, E, False, steps=9, tile=tile)
     assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
-    assert phx().phx_tile(h) in range(1, 8)
+    assert phx().phx_tile(h) in TMA_SCALAR_TILES

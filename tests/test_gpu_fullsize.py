@@ -8,7 +8,7 @@ import pytest
 
 from oracle import gp
 import synth
-from gpu_util import phx, make_handle, get_state, rel_l2, TOL
+from gpu_util import phx, make_handle, get_state, rel_l2, TOL, TMA_SCALAR_TILES
 
 pytestmark = pytest.mark.gpu
 
@@ -93,7 +93,7 @@ def test_driven_9000_sampled_step():
     step, t = m.phx_time(h)
     m.phx_step_n(h, 1)
     psi_1, _ = get_state(h, 32)
-    assert 1 <= m.phx_tile(h) <= 7
+    assert m.phx_tile(h) in TMA_SCALAR_TILES
     sites = sample_sites(9000, 9000, np.random.default_rng(4))
     sp, _ = gp.step_at_sites(psi_s.astype(np.complex128), None, None, cfg["V"], gp.Params(**d),
                              sites, step, E=cfg["E"], t=t)

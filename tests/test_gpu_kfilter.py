@@ -7,7 +7,7 @@ import pytest
 
 from oracle import gp
 import synth
-from gpu_util import phx, get_state, rel_l2, rounded, TOL
+from gpu_util import phx, get_state, rel_l2, rounded, TOL, TMA_SCALAR_TILES
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +66,7 @@ def test_kfilter_with_tma_scalar_kernel(tile):
                                                     steps=9, tile=tile)
     assert rel_l2(g_psi, o_psi) <= 1e-4
     assert rel_l2(g_n, o_n) <= 1e-4
-    assert phx().phx_tile(h) in range(1, 8)
+    assert phx().phx_tile(h) in TMA_SCALAR_TILES
 
 
 def test_kfilter_off_and_invalid_arguments():
