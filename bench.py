@@ -1,9 +1,11 @@
 """Benchmark of the fused RK4 dNLSE step on GB300.
 
 One bench step = one full run of the driven-dissipative reservoir workload
-(1024x1024 grid, 100 um periodic box, ring pump of radius 20 um / width 3 um at
-1.5 P_thr, initial noise 1e-2, 10^4 RK4 steps at half the stability limit) plus
-the FP64 norm/energy and steady-state-residual reductions, through the C ABI.
+(default: 2048x2048 grid over a 200 um periodic box -- the 1024^2 workload's
+cell size and time step --, ring pump of radius 20 um / width 3 um at
+1.5 P_thr, initial noise 1e-2, 10^4 RK4 steps at half the stability limit)
+plus the FP64 norm/energy and steady-state-residual reductions, through the
+C ABI.
 
 Prints ONE JSON line (rank 0).  Metric: RK4 site-updates/s (whole job).
   value      device-timed (CUDA events on the solver's stream), inputs resident
@@ -12,6 +14,8 @@ Prints ONE JSON line (rank 0).  Metric: RK4 site-updates/s (whole job).
   roofline   dominant kernel (the fused RK4 step): algorithmic bytes / average
              launch time against the measured HBM copy bandwidth
   cpu_baseline  the FP64 numpy oracle timed on a bounded sample (rank 0, N=1)
+  precision_error  FP32 runs: relative L2 error of the final state against
+             the FP64 path run on the same inputs over the same steps
 
 --impl reference times the oracle itself on the same workload.
 Under torchrun (N > 1) every rank runs an independent replica (different
@@ -53,9 +57,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phx", choices=["phx", "reference"])
-    ap.add_argument("--workload", default="reservoir_1024",
-                    choices=["reservoir_1024", "reservoir", "spinor_2048", "conservative_64",
-                             "ensemble", "twa_ensemble", "driven_9000"])
+    ap.add_argument("--workload", default="reservoir_2048",
+                    choices=["reservoir_2048", "reservoir_1024", "reservoir", "spinor_2048",
+                             "conservative_64", "ensemble", "twa_ensemble", "driven_9000",
+                             "steady_256"])
     ap.add_argument("--grid", type=int, default=1024,
                     help="grid size of the 'reservoir' workload (100 um box, config-2 physics)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -65,6 +70,16 @@ def parse():
                     help="time stepper of the single-handle workloads: fused RK4 or split-step Fourier")
     ap.add_argument("--tile", type=int, default=0,
                     help="step-kernel configuration (0 = autotune, 1..7 TMA-fed, 9 generic)")
+    ap.add_argument("--no-steady", action="store_true",
+                    help="skip the reduced warm-vs-cold steady-state measurement")
+    # steady_256 (warm-start experiment) sizes
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=200)
+    ap.add_argument("--gen-steps", type=int, default=40000)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--cap", type=int, default=200000)
+    ap.add_argument("--time-limit", type=float, default=None)
+    ap.add_argument("--out", default=None)
     return ap.parse_args()
 
 
@@ -114,7 +129,12 @@ def workload_name(args):
 
 def workload(name, seed_offset=0, grid=1024):
     import synth
-    if name == "reservoir_1024" or (name == "reservoir" and grid == 1024):
+    if name == "reservoir_2048":
+        cfg = synth.reservoir_2048(seed=2 + seed_offset)
+        kind = "reservoir"
+        desc = ("driven-dissipative GP + reservoir, 2048x2048, 200 um periodic (cell 100/1024 um), "
+                "ring pump r=20 um w=3 um at 1.5 P_thr, psi0 noise 1e-2, dt = half RK4 limit")
+    elif name == "reservoir_1024" or (name == "reservoir" and grid == 1024):
         cfg = synth.reservoir_1024(seed=2 + seed_offset)
         kind = "reservoir"
         desc = ("driven-dissipative GP + reservoir, 1024x1024, 100 um periodic, ring "
@@ -146,6 +166,12 @@ STEP_KERNEL_SOURCES = ("phx_internal.h", "phx_noise.cuh", "rk4_generic.cuh", "rk
                        "rk4_tma_kernel.cuh", "rk4_tma.cu", "rk4_tma_cfg1.cu", "rk4_tma_cfg2.cu",
                        "rk4_tma_cfg3.cu", "rk4_tma_cfg4.cu", "rk4_tma_cfg5.cu", "rk4_tma_cfg6.cu",
                        "rk4_tma_cfg7.cu")
+
+
+def step_kernel_name(tile):
+    if 1 <= tile <= 7:
+        return "rk4_f32_tma (fused, one launch per RK4 step)"
+    return "rk4_step_generic (fused, one launch per RK4 step)"
 
 
 def kernel_hash():
@@ -261,6 +287,50 @@ def cpu_baseline(name, cfg, budget_s=15.0):
             "kind": "oracle",
             "sample": "%d RK4 steps of the %dx%d %s workload (numpy FP64, 1 thread), %.1f s"
                       % (steps, p.nx, p.ny, name, dt)}
+
+
+def _rel_l2(a, b):
+    import torch
+    a, b = a.reshape(-1), b.reshape(-1)
+    den = float(torch.linalg.vector_norm(b))
+    return float(torch.linalg.vector_norm(a - b)) / den if den > 0 else None
+
+
+def fp64_run(phx, d, cfg, nsteps, stream, dev, step_fn_name="phx_step_n"):
+    """The same workload run by the FP64 path (parity-pinned to the oracle at
+    1e-11) from the workload's FP64 inputs: the yardstick of the FP32 error."""
+    import torch
+    h = phx.phx_create(phx.params_from_dict(d, precision=64, stream=stream.cuda_stream))
+    f64, c128 = torch.float64, torch.complex128
+    if cfg.get("P") is not None:
+        phx.phx_set_pump(h, torch.tensor(np.asarray(cfg["P"])[0], dtype=f64, device=dev))
+    if cfg.get("V") is not None:
+        phx.phx_set_potential(h, torch.tensor(np.asarray(cfg["V"]), dtype=f64, device=dev))
+    if cfg.get("E") is not None:
+        phx.phx_set_drive(h, torch.tensor(np.asarray(cfg["E"])[0], dtype=c128, device=dev))
+    psi0 = torch.tensor(np.ascontiguousarray(cfg["psi0"]), dtype=c128, device=dev)
+    n0 = None if cfg.get("n0") is None else torch.tensor(cfg["n0"], dtype=f64, device=dev)
+    phx.phx_set_state(h, psi0, n0)
+    getattr(phx, step_fn_name)(h, nsteps)
+    psi = torch.empty_like(psi0)
+    n = None if n0 is None else torch.empty_like(n0)
+    phx.phx_get_state(h, psi, n)
+    torch.cuda.synchronize()
+    phx.phx_destroy(h)
+    return psi, n
+
+
+def precision_error(psi32, n32, psi64, n64, what):
+    """Relative L2 error of an FP32 result against the FP64 result of the
+    same inputs and steps (the FP32 run starts from the inputs rounded to
+    FP32; that rounding is part of its error)."""
+    dev = psi64.device
+    out = {"psi_rel_l2": _rel_l2(psi32.to(dev).to(psi64.dtype), psi64),
+           "against": "FP64 GPU path (pinned to the oracle at rel. L2 1e-11) on the same "
+                      "inputs and steps", "what": what}
+    if n32 is not None and n64 is not None:
+        out["n_rel_l2"] = _rel_l2(n32.to(dev).to(n64.dtype), n64)
+    return out
 
 
 def peaks():
@@ -429,6 +499,19 @@ def run_ensemble(args, world, rank, local, pg):
         phx.phx_batch_get_state(b, i, out_psi[i], out_n[i])
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    # FP32 error per result: two members (the smallest and the largest grid
+    # of the ensemble; member 0 of the truncated-Wigner ensemble) against
+    # the FP64 path over the same steps (noise bits identical in both)
+    picks = [0] if twa else [0, len(members) - 1]
+    prec_err = []
+    for i in picks:
+        m = members[i]
+        psi64, n64 = fp64_run(phx, m["params"], m, rk4_steps, stream, dev)
+        e = precision_error(out_psi[i][None], out_n[i][None], psi64, n64,
+                            "member %d (%dx%d) after %d steps" % (
+                                i, m["params"]["nx"], m["params"]["ny"], rk4_steps))
+        prec_err.append(e)
+        del psi64, n64
     pk, pk_kind = peaks()
     achieved = 28 * sites / kern_s / 1e9
     if twa:
@@ -458,13 +541,14 @@ def run_ensemble(args, world, rank, local, pg):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
                      "traffic": recorded_traffic(args.workload, 32, phx.phx_batch_tile(b)),
-                     "kernel": "rk4_f32_tma (persistent, all members per launch)",
+                     "kernel": step_kernel_name(phx.phx_batch_tile(b)) + ", all members per launch",
                      "algorithmic_bytes_per_site": 28, "avg_launch_us": kern_s * 1e6,
                      "peak_source": pk_kind,
                      **({"note": "per-site Philox + Box-Muller noise every step: the kernel is "
                                  "bound by instruction issue, not by HBM"} if twa else {})},
         "clocks": clk,
         "energy": energy(clk, ms * 1e-3, sites * rk4_steps),
+        "precision_error": prec_err,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if twa:
@@ -476,6 +560,176 @@ def run_ensemble(args, world, rank, local, pg):
     phx.phx_batch_destroy(b)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+WAISTS = (3.0, 4.5, 6.0, 9.0, 12.0, 15.0)   # um, spot waists whose threshold is measured
+
+
+def steady_experiment(n_train=2000, n_test=200, gen_steps=40000, epochs=40, cap=200000,
+                      tol=1e-6, tol32=1e-5, check_every=100, seed=0, time_limit=None,
+                      log=None):
+    """Learned warm start against cold start on the steady-state workload
+    (256x256, 128 um periodic, the reservoir workload's physics, dt at 0.7 of
+    the RK4 limit of the linear part: the strongest pumps' reservoir
+    blueshift g_r n of several meV shifts the spectrum, which 0.85 of the
+    limit leaves unstable, while RK4 still damps the zero-group-velocity
+    lattice modes of the 5-point stencil that a smaller dt would let grow
+    inside the spot): the finite-spot thresholds are measured with the
+    solver, pumps (sums of 1-4 Gaussians, waist 3-15 um, peak 1-3 times the
+    threshold of a spot of that waist) are drawn, the training pairs are
+    relaxed from noise by the batched solver, the network is trained only on
+    the pairs that reached r_psi < tol32, and held-out pumps are relaxed to
+    r_psi < tol from noise (cold) and from the prediction (warm) under the
+    same protocol.  Returns (report dict, network)."""
+    import torch
+    import synth
+    from paper_2411_18341_gb300 import warmstart as ws
+    log = log or (lambda s: None)
+    d = synth.base_params(256, 256, 128.0, 128.0, dt=0.0, **synth.reservoir_physics())
+    d["dt"] = ws.stable_dt(d, 0.7)
+    pthr = ws.pump_threshold(d)
+    prob = ws.Problem(d, pthr)
+    n = prob.n
+    t_all = time.time()
+    thr, _ = ws.spot_thresholds(prob, WAISTS)
+    fin = np.isfinite(thr)
+    top = float(np.max(thr[fin])) if fin.any() else 1.0
+    thr_used = np.where(fin, thr, top)
+    lw, lt = np.log(np.asarray(WAISTS)), np.log(thr_used)
+    spot = lambda w: pthr * float(np.exp(np.interp(np.log(w), lw, lt)))  # noqa: E731
+    rep = {"workload": "steady_256: 256x256, 128 um periodic, config-2 physics, dt %.6g ps "
+                       "(0.7 of the RK4 limit); pumps: sums of 1-4 Gaussians, waist 3-15 um, "
+                       "peak 1-3 x the solver-measured threshold of a spot of that waist"
+                       % d["dt"],
+           "spot_threshold_factors": {"%g" % w: float(t) for w, t in zip(WAISTS, thr)},
+           "n_train": n_train, "n_test": n_test, "gen_steps": gen_steps, "epochs": epochs,
+           "tol": tol, "tol32": tol32, "check_every": check_every, "cap": cap}
+    train_pumps = synth.random_gaussian_pumps(256, 128.0, n_train, seed=5000, threshold=spot)
+    test_pumps = synth.random_gaussian_pumps(256, 128.0, n_test, seed=5000 + n_train,
+                                             threshold=spot)
+
+    def noise_init(seed0):
+        def init(i0, i1):
+            z = np.stack([synth.complex_normal((n, n), 1e-2, seed0 + i) for i in range(i0, i1)])
+            return (torch.as_tensor(z.astype(np.complex64)).cuda(),
+                    torch.zeros(i1 - i0, n, n, device="cuda"))
+        return init
+
+    t0 = time.time()
+    feats, targs, gen = ws.generate(prob, train_pumps, noise_init(105000), steps=gen_steps,
+                                    tol32=tol32, log=log)
+    rep["generate_s"] = time.time() - t0
+    keep = np.where(gen["steps"] >= 0)[0]
+    rep["train_converged"] = int(len(keep))
+    rep["train_decayed"] = int(gen["decayed"].sum())
+    rep["train_diverged"] = int(gen["diverged"].sum())
+    sel = torch.as_tensor(keep, device="cuda")
+    feats, targs = feats.index_select(0, sel), targs.index_select(0, sel)
+    tf, tt, tgen = ws.generate(prob, test_pumps, noise_init(105000 + n_train), steps=gen_steps,
+                               tol32=tol32, log=log)
+    tkeep = torch.as_tensor(np.where(tgen["steps"] >= 0)[0], device="cuda")
+    rep["heldout_converged"] = int(len(tkeep))
+    net = ws.new_network(prob)
+    ws.phx_fno_set_params(net, ws.initial_weights(net, seed))
+    t0 = time.time()
+    hist = ws.train(net, feats, targs, epochs, log=log) if len(keep) >= 8 else []
+    torch.cuda.synchronize()
+    rep["train_s"] = time.time() - t0
+    rep["train_loss"] = hist
+    if len(tkeep):
+        rep["heldout_loss"] = ws.eval_loss(net, tf.index_select(0, tkeep),
+                                           tt.index_select(0, tkeep))
+    del feats, targs, tt
+    cold = noise_init(205000)
+    wpsi, wn = ws.predict_states(net, prob, tf)
+
+    def warm(i0, i1):
+        return wpsi[i0:i1].contiguous(), wn[i0:i1].contiguous()
+
+    t0 = time.time()
+    sc = ws.screen(prob, test_pumps, cold, tol32=tol32, cap=cap, check_every=check_every, log=log)
+    sw = ws.screen(prob, test_pumps, warm, tol32=tol32, cap=cap, check_every=check_every, log=log)
+    rep["screen_s"] = time.time() - t0
+    both = np.where((sc["steps"] >= 0) & (sw["steps"] >= 0))[0]
+    rep["screen"] = {
+        "cold_converged": int((sc["steps"] >= 0).sum()),
+        "warm_converged": int((sw["steps"] >= 0).sum()),
+        "cold_decayed": int(sc["decayed"].sum()), "warm_decayed": int(sw["decayed"].sum()),
+        "cold_diverged": int(sc["diverged"].sum()), "warm_diverged": int(sw["diverged"].sum()),
+        "both_converged": int(len(both)),
+        "cold_steps32_median": float(np.median(sc["steps"][both])) if len(both) else None,
+        "warm_steps32_median": float(np.median(sw["steps"][both])) if len(both) else None}
+    rows = []
+    for i in both:
+        if time_limit and time.time() - t_all > time_limit:
+            break
+        z = cold(int(i), int(i) + 1)
+        rc = ws.relax(prob, test_pumps[i], init=(z[0][0], z[1][0]), tol=tol, tol32=tol32,
+                      check_every=check_every, cap=cap, instance=int(i))
+        rw = ws.relax(prob, test_pumps[i], net=net, tol=tol, tol32=tol32,
+                      check_every=check_every, cap=cap, instance=int(i))
+        row = {"i": int(i), "cold_steps": rc["steps"], "warm_steps": rw["steps"],
+               "cold_ms": rc["ms"], "warm_ms": rw["ms"], "cold_r": rc["r"], "warm_r": rw["r"],
+               "cold_converged": rc["converged"], "warm_converged": rw["converged"]}
+        if rc["converged"] and rw["converged"]:
+            row["density_rel_diff"] = ws.density_match(rw["state"][0], rc["state"][0])
+        rows.append(row)
+    rep["relax"] = rows
+    ok = [r for r in rows if r["cold_converged"] and r["warm_converged"]]
+    if ok:
+        cs = np.array([r["cold_steps"] for r in ok])
+        wsp = np.array([r["warm_steps"] for r in ok])
+        cm = np.array([r["cold_ms"] for r in ok])
+        wm = np.array([r["warm_ms"] for r in ok])
+        dm = np.array([r.get("density_rel_diff", np.nan) for r in ok])
+        q = lambda a: [float(np.percentile(a, 25)), float(np.median(a)),  # noqa: E731
+                       float(np.percentile(a, 75))]
+        rep["summary"] = {"pairs": len(ok), "cold_steps_q": q(cs), "warm_steps_q": q(wsp),
+                          "cold_ms_q": q(cm), "warm_ms_q": q(wm),
+                          "warm_faster_fraction": float((wm < cm).mean()),
+                          "speedup_median_ms": float(np.median(cm / wm)),
+                          "same_state_fraction": float((dm < 1e-3).mean()),
+                          "density_rel_diff_median": float(np.nanmedian(dm))}
+    rep["total_s"] = time.time() - t_all
+    return rep, net
+
+
+def steady_key(rep):
+    """The warm-vs-cold summary carried in a bench line."""
+    s = rep.get("summary") or {}
+    return {"workload": rep["workload"], "n_train": rep["n_train"],
+            "train_converged": rep["train_converged"], "n_test": rep["n_test"],
+            "heldout_converged": rep["heldout_converged"], "epochs": rep["epochs"],
+            "pairs": s.get("pairs", 0),
+            "cold_ms_median": s.get("cold_ms_q", [None] * 3)[1],
+            "warm_ms_median": s.get("warm_ms_q", [None] * 3)[1],
+            "cold_steps_median": s.get("cold_steps_q", [None] * 3)[1],
+            "warm_steps_median": s.get("warm_steps_q", [None] * 3)[1],
+            "speedup_median_ms": s.get("speedup_median_ms"),
+            "warm_faster_fraction": s.get("warm_faster_fraction"),
+            "same_state_fraction": s.get("same_state_fraction"),
+            "tol": rep["tol"], "timing": "CUDA events, FNO inference inside the warm runs",
+            "seconds": rep["total_s"]}
+
+
+def run_steady(args, world, rank):
+    """--workload steady_256: the warm-start experiment as one JSON line."""
+    if rank != 0:
+        return
+    rep, _ = steady_experiment(args.train, args.test, args.gen_steps, args.epochs, args.cap,
+                               time_limit=args.time_limit,
+                               log=lambda s: print(s, file=sys.stderr, flush=True))
+    s = rep.get("summary") or {}
+    line = {"metric": "time to steady state r_psi < 1e-6 (GPU ms, median over held-out pumps)",
+            "value": s.get("warm_ms_q", [None] * 3)[1], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "steady_256"}, "steady_state": steady_key(rep),
+            "report": rep}
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(rep, f, indent=1)
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -494,6 +748,11 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
+    if args.workload == "steady_256":
+        run_steady(args, world, rank)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
     if args.workload in ("ensemble", "twa_ensemble"):
         run_ensemble(args, world, rank, local, pg)
         if pg is not None:
@@ -597,6 +856,14 @@ def main():
         phx.phx_get_state(h, out_psi, out_n)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(pg, (time.perf_counter() - t0) / e2e_steps)
+    if prec == 32:
+        psi64, n64 = fp64_run(phx, d, cfg, rk4_steps, stream, dev,
+                              "phx_step_ssf" if args.integrator == "ssf" else "phx_step_n")
+        prec_err = precision_error(out_psi, out_n, psi64, n64,
+                                   "final state after the bench step's %d steps" % rk4_steps)
+        del psi64, n64
+    else:
+        prec_err = {"note": "FP64 run: the FP64 path is the yardstick of the FP32 error"}
     esz = 4 if prec == 32 else 8
     h2d = sites * nc * 2 * esz + (0 if n_h is None else sites * nc * esz) + \
         (0 if P_h is None else sites * esz) + (0 if V_h is None else sites * esz) + \
@@ -629,10 +896,7 @@ def main():
                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                 "traffic": traffic,
                 "kernel": ("split-step (local kernels + cuFFT round trip per step)"
-                           if args.integrator == "ssf" else
-                           "rk4_f32_tma (fused, one launch per RK4 step)"
-                           if 1 <= phx.phx_tile(h) <= 7
-                           else "rk4_step_generic (fused, one launch per RK4 step)"),
+                           if args.integrator == "ssf" else step_kernel_name(phx.phx_tile(h))),
                 "algorithmic_bytes_per_site": bps,
                 "avg_launch_us": kern_s * 1e6,
                 "peak_source": pk_kind}
@@ -665,7 +929,15 @@ def main():
         "roofline": roof,
         "clocks": clk,
         "energy": energy(clk, ms * 1e-3, sites * rk4_steps),
+        "precision_error": prec_err,
     }
+    if rank == 0 and world == 1 and not args.no_steady and args.workload == "reservoir_2048":
+        # reduced warm-vs-cold time to steady state (the metric's second part)
+        rep, _ = steady_experiment(n_train=256, n_test=64, gen_steps=30000, epochs=12,
+                                   cap=60000, time_limit=100)
+        line["steady_state"] = dict(steady_key(rep), reduced=(
+            "256 training / 64 held-out pumps, 12 epochs, cap 6e4 steps; the full "
+            "experiment is --workload steady_256"))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if sites > 1 << 24:
             import synth

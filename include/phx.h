@@ -285,7 +285,8 @@ void phx_destroy(phx_handle* h);
  * steps: each step is ONE persistent kernel launch over the tiles of all
  * members (a per-tile instance table), replayed from a CUDA graph, with the
  * tile configuration picked by an autotuner on the first call (which
- * synchronises the stream once).  Members are addressed by index 0..count-1;
+ * synchronises the stream once) unless params[0].tile names one of the
+ * TMA-fed configurations 1..7.  Members are addressed by index 0..count-1;
  * their arrays follow the single-handle conventions above.  params[0].stream
  * is used for all work.  Member i's FP64 simulated time is t0_i + steps*dt_i
  * accumulated on the device. */
@@ -303,9 +304,12 @@ phx_status phx_batch_set_state(phx_batch* b, int32_t i, const void* psi, const v
 phx_status phx_batch_get_state(phx_batch* b, int32_t i, void* psi, void* n, int on_device);
 phx_status phx_batch_step_n(phx_batch* b, int64_t nsteps);
 /* Per-member FP64 norm and energy (arrays of count doubles; either may be
- * NULL), same definitions as phx_norm_energy.  Synchronises. */
+ * NULL), same definitions as phx_norm_energy.  Synchronises.  Every member's
+ * values are written before PHX_ENONFINITE reports that some member's state
+ * holds NaN or Inf (that member's values are then non-finite). */
 phx_status phx_batch_norm_energy(phx_batch* b, double* norms, double* energies);
-/* Per-member steady-state residuals (arrays of count; any may be NULL). */
+/* Per-member steady-state residuals (arrays of count; any may be NULL);
+ * PHX_ENONFINITE as for phx_batch_norm_energy. */
 phx_status phx_batch_residual(phx_batch* b, double* r_psi, double* r_n, double* omega);
 /* Common step counter and per-member FP64 times (t: count doubles or NULL). */
 phx_status phx_batch_time(phx_batch* b, int64_t* step, double* t);
@@ -339,8 +343,11 @@ phx_status phx_noise_sample(uint64_t seed, int64_t step, uint32_t instance,
  * nx*ny > 16777216 (2^24) do not fit that scratch and return PHX_EINVAL.
  *
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls on a device share the array and leave their partials
+ * device, with that device current; a look-up that failed is tried again by
+ * the next call); make that first call before any stream capture.  The
+ * address is kept for the life of the process: after cudaDeviceReset of a
+ * device this entry point must not be called on that device again (the kept
+ * address would be stale).  All calls on a device share the array and leave their partials
  * in it; each call writes every slot it reads, so nothing needs clearing,
  * but calls whose kernels can overlap on the GPU (unordered streams) race.
  * Synchronises p->stream.  Errors (status only; no message is recorded,

@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libphx.so")
 
 PHX_OK = 0
+PHX_ENONFINITE = 4
 STATUS = {0: "PHX_OK", 1: "PHX_EINVAL", 2: "PHX_ENOMEM", 3: "PHX_ECUDA",
           4: "PHX_ENONFINITE", 5: "PHX_ETIMEOUT", 6: "PHX_ESTATE",
           7: "PHX_ENODEV"}
@@ -390,9 +391,27 @@ def phx_norm_energy_static(p, psi, n=None, V=None):
     """Allocation-free norm/energy of caller-owned CUDA tensors (plain layout).
     Raises PhxError with the status code on failure (this call records no
     message)."""
+    import torch
     for t in (psi, n, V):
         if t is not None and (not t.is_cuda or not t.is_contiguous()):
             raise ValueError("inputs must be contiguous CUDA tensors")
+    # The C entry point cannot see buffer sizes: check every array against
+    # the grid and the precision here, before any kernel reads it.
+    ncomp = 2 if p.spinor else 1
+    sites = int(p.nx) * int(p.ny)
+    cplx = torch.complex64 if p.precision == 32 else torch.complex128
+    real = torch.float32 if p.precision == 32 else torch.float64
+    if psi.dtype != cplx or psi.numel() != ncomp * sites:
+        raise ValueError("psi must be a %s tensor of ncomp*ny*nx = %d elements"
+                         % (cplx, ncomp * sites))
+    if p.reservoir:
+        if n is None or n.dtype != real or n.numel() != ncomp * sites:
+            raise ValueError("n must be a %s tensor of ncomp*ny*nx = %d elements"
+                             % (real, ncomp * sites))
+    else:
+        n = None
+    if V is not None and (V.dtype != real or V.numel() != sites):
+        raise ValueError("V must be a %s tensor of ny*nx = %d elements" % (real, sites))
     N, E = ctypes.c_double(), ctypes.c_double()
     ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
     st = lib().phx_norm_energy_static(ctypes.byref(p), ptr(psi), ptr(n), ptr(V),
@@ -469,18 +488,27 @@ def phx_batch_step_n(b, nsteps):
     _bcheck(lib().phx_batch_step_n(b.ptr, int(nsteps)), b)
 
 
-def phx_batch_norm_energy(b):
+def phx_batch_norm_energy(b, allow_nonfinite=False):
+    """Per-member (norms, energies).  allow_nonfinite: a member whose state
+    holds NaN or Inf reports non-finite values instead of raising (the C call
+    fills every member's values before it returns PHX_ENONFINITE)."""
     N = np.zeros(b.count)
     E = np.zeros(b.count)
-    _bcheck(lib().phx_batch_norm_energy(b.ptr, N.ctypes.data, E.ctypes.data), b)
+    st = lib().phx_batch_norm_energy(b.ptr, N.ctypes.data, E.ctypes.data)
+    if not (allow_nonfinite and st == PHX_ENONFINITE):
+        _bcheck(st, b)
     return N, E
 
 
-def phx_batch_residual(b):
+def phx_batch_residual(b, allow_nonfinite=False):
+    """Per-member (r_psi, r_n, omega); allow_nonfinite as for
+    phx_batch_norm_energy."""
     r = np.zeros(b.count)
     rn = np.zeros(b.count)
     om = np.zeros(b.count)
-    _bcheck(lib().phx_batch_residual(b.ptr, r.ctypes.data, rn.ctypes.data, om.ctypes.data), b)
+    st = lib().phx_batch_residual(b.ptr, r.ctypes.data, rn.ctypes.data, om.ctypes.data)
+    if not (allow_nonfinite and st == PHX_ENONFINITE):
+        _bcheck(st, b)
     return r, rn, om
 
 

@@ -5,9 +5,13 @@ approximate stationary state (psi, n) of Eqs. (PULSE_psi)/(PULSE_res); the
 RK4 relaxation then starts from that state instead of from noise.  This
 module drives the loop on the GPU through the C ABI:
 
+* ``spot_thresholds`` -- the condensation threshold of a single Gaussian pump
+  spot per waist, measured with the batched solver (a finite spot loses
+  particles to its surroundings, so it needs more than the homogeneous
+  threshold gamma_c gamma_r / R).
 * ``generate`` -- solver-generated training pairs: batches of instances (one
-  persistent launch per RK4 step) relaxed from noise; features and
-  gauge-fixed targets are formed on the device.
+  persistent launch per RK4 step) relaxed from a caller-given initial state;
+  features and gauge-fixed targets are formed on the device.
 * ``train``    -- mini-batch Adam on the GPU (forward, backward and update in
   this package's kernels).
 * ``screen``   -- a batch relaxed from cold or warm starts, recording for each
@@ -27,10 +31,6 @@ is below the threshold of its finite spot) and is reported as decayed.
 Only torch device memory, dtype casts and events come from PyTorch; every
 arithmetic step of the method runs in the package's CUDA kernels.
 """
-import argparse
-import json
-import os
-import sys
 import time
 
 import numpy as np
@@ -39,9 +39,10 @@ import torch
 from . import (phx_batch_create, phx_batch_get_state, phx_batch_norm_energy,
                phx_batch_residual, phx_batch_set_pump, phx_batch_set_state, phx_batch_step_n,
                phx_create, phx_fno_create, phx_fno_features, phx_fno_forward,
-               phx_fno_get_params, phx_fno_loss_grad, phx_fno_set_params, phx_fno_targets,
-               phx_fno_to_state, phx_fno_train_step, phx_get_state, phx_norm_energy,
-               phx_residual, phx_set_pump, phx_set_state, phx_step_n, params_from_dict)
+               phx_fno_loss_grad, phx_fno_set_params, phx_fno_targets,
+               phx_fno_to_state, phx_fno_train_step, phx_get_state,
+               phx_residual, phx_set_pump, phx_set_state, phx_stability_dt, phx_step_n,
+               params_from_dict)
 
 SCALE_PSI = 5.0     # |psi| ~ 5 at 1-3 P_thr: output normalisation of Re/Im psi
 SCALE_N = 15.0      # n ~ gamma_c / R = 15 in a condensate: normalisation of n
@@ -61,8 +62,95 @@ class Problem:
             raise ValueError("square grids only")
 
 
+def pump_threshold(params):
+    """Homogeneous condensation threshold P_thr = gamma_c gamma_r / R: with
+    psi = 0 the reservoir settles at n = P / gamma_r (Eq. PULSE_res), and the
+    gain R n of Eq. PULSE_psi balances the loss gamma_c at P = P_thr."""
+    return params["gamma_c"] * params["gamma_r"] / params["R"]
+
+
+def stable_dt(params, fraction):
+    """`fraction` of the RK4 stability limit of the grid (phx_stability_dt)."""
+    return fraction * phx_stability_dt(params_from_dict(dict(params, dt=0.0)))
+
+
 def _stream():
     return torch.cuda.current_stream()
+
+
+def _grid_r2(problem, cx=0.0, cy=0.0):
+    """|r - c|^2 on the cell positions -L/2 + i L/n (origin at the centre)."""
+    x = -0.5 * problem.length + np.arange(problem.n) * (problem.length / problem.n)
+    return (x[None, :] - cx) ** 2 + (x[:, None] - cy) ** 2
+
+
+def spot_thresholds(problem, waists, factors=(1.0, 1.25, 1.5, 2.0, 2.5, 3.0, 4.0, 5.0, 6.5,
+                                              8.0, 10.0, 13.0, 17.0, 22.0, 28.0, 36.0),
+                    chunks=120, chunk_steps=25, seed=0):
+    """Condensation threshold of one Gaussian spot P0 exp(-r^2/w^2) per waist
+    w, in units of the homogeneous threshold, measured with the solver.
+
+    Every (w, f) pair is one member of a batch: pump f P_thr exp(-r^2/w^2),
+    reservoir started at its below-threshold value n = P / gamma_r, psi at
+    weak seeded noise.  The batch runs `chunks` chunks of `chunk_steps` RK4
+    steps; after each chunk every member's psi is scaled back to the start
+    norm (|psi|^2 ~ 1e-10 per site, so the Kerr term and the reservoir
+    depletion stay negligible: the linearised dynamics around psi = 0).  Over
+    the second half, when the decaying modes have died out, the mean of
+    ln(N_after / N_before) per chunk is the growth rate of the leading mode's
+    |psi|^2; it is positive above threshold.  The threshold is the factor at
+    which that rate crosses zero (linear in log f between the bracketing
+    factors); inf if no factor in the list condenses.
+    Returns (thresholds [len(waists)], rates [len(waists), len(factors)],
+    rates in 1/ps)."""
+    pthr = pump_threshold(problem.params)
+    n = problem.n
+    members, pumps = [], []
+    for w in waists:
+        shape = np.exp(-_grid_r2(problem) / w ** 2)
+        for f in factors:
+            members.append(_member_params(problem, len(members)))
+            pumps.append((f * pthr * shape).astype(np.float32))
+    b = phx_batch_create(members)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    amp = 1e-5
+    for k, P in enumerate(pumps):
+        Pd = torch.as_tensor(P).cuda()
+        phx_batch_set_pump(b, k, Pd)
+        z = torch.complex(torch.randn(n, n, generator=g, device="cuda"),
+                          torch.randn(n, n, generator=g, device="cuda")) * amp
+        phx_batch_set_state(b, k, z.to(torch.complex64).contiguous(),
+                            (Pd / problem.params["gamma_r"]).contiguous())
+    N0, _ = phx_batch_norm_energy(b)
+    psi = torch.empty(n, n, dtype=torch.complex64, device="cuda")
+    nres = torch.empty(n, n, device="cuda")
+    logs = []
+    for c in range(chunks):
+        phx_batch_step_n(b, chunk_steps)
+        N1, _ = phx_batch_norm_energy(b)
+        logs.append(np.log(np.maximum(N1, 1e-300) / N0))
+        for k in range(len(members)):  # back to the start norm
+            phx_batch_get_state(b, k, psi, nres)
+            psi *= float(np.sqrt(N0[k] / max(N1[k], 1e-300)))
+            phx_batch_set_state(b, k, psi, nres)
+    del b
+    half = np.asarray(logs[chunks // 2:])
+    rate = half.mean(axis=0) / (chunk_steps * problem.params["dt"])
+    rate = rate.reshape(len(waists), len(factors))
+    lf = np.log(np.asarray(factors, np.float64))
+    thr = np.full(len(waists), np.inf)
+    for a in range(len(waists)):
+        up = np.where(rate[a] > 0)[0]
+        if len(up) == 0:
+            continue
+        k = int(up[0])
+        if k == 0:
+            thr[a] = factors[0]
+            continue
+        r0, r1 = rate[a, k - 1], rate[a, k]
+        thr[a] = float(np.exp(lf[k - 1] + (lf[k] - lf[k - 1]) * (-r0) / (r1 - r0)))
+    return thr, rate
 
 
 def features(problem, pumps):
@@ -99,12 +187,15 @@ def screen(problem, pumps, init, tol32=1e-5, check_every=100, cap=200000, tiny=1
     step).  init(i0, i1) -> (psi [m,H,W] complex64, n [m,H,W] float32) device
     tensors for members i0..i1-1.  Returns a dict of host arrays: steps (first
     check with r < tol32, or -1), r (at that check, else final), decayed,
-    and with collect=True the final states as device tensors."""
+    diverged (the state became non-finite: a strongly pumped spot whose
+    transient density left the time step's stability region), and with
+    collect=True the final states as device tensors."""
     N = len(pumps)
     n = problem.n
     steps = np.full(N, -1, np.int64)
     r_at = np.zeros(N)
     decayed = np.zeros(N, bool)
+    diverged = np.zeros(N, bool)
     psi_all = torch.empty(N, n, n, dtype=torch.complex64, device="cuda") if collect else None
     n_all = torch.empty(N, n, n, device="cuda") if collect else None
     for c0 in range(0, N, chunk):
@@ -121,16 +212,18 @@ def screen(problem, pumps, init, tol32=1e-5, check_every=100, cap=200000, tiny=1
         while s < cap and not done.all():
             phx_batch_step_n(b, check_every)
             s += check_every
-            norms, _ = phx_batch_norm_energy(b)
-            dec = norms / (problem.cell * n * n) < tiny
-            r, _, _ = _safe_residual(b, dec)
-            newly = (~done) & (r < tol32) & (~dec)
+            norms, _ = phx_batch_norm_energy(b, allow_nonfinite=True)
+            bad = ~np.isfinite(norms)
+            dec = (norms / (problem.cell * n * n) < tiny) & ~bad
+            r, _, _ = _safe_residual(b, dec | bad)
+            newly = (~done) & (r < tol32) & (~dec) & (~bad)
             steps[c0:c1][newly] = s
             r_at[c0:c1][newly] = r[newly]
             decayed[c0:c1] |= (~done) & dec
-            done |= newly | dec
+            diverged[c0:c1] |= (~done) & bad
+            done |= newly | dec | bad
         if not done.all():
-            r, _, _ = _safe_residual(b, decayed[c0:c1])
+            r, _, _ = _safe_residual(b, decayed[c0:c1] | diverged[c0:c1])
             r_at[c0:c1][~done] = r[~done]
         if collect:
             for k in range(m):
@@ -140,33 +233,28 @@ def screen(problem, pumps, init, tol32=1e-5, check_every=100, cap=200000, tiny=1
                 % (c0, c1 - 1, s, time.time() - t0, int((steps[c0:c1] >= 0).sum()),
                    int(decayed[c0:c1].sum())))
         del b
-    out = dict(steps=steps, r=r_at, decayed=decayed)
+    out = dict(steps=steps, r=r_at, decayed=decayed, diverged=diverged)
     if collect:
         out["psi"], out["nres"] = psi_all, n_all
     return out
 
 
-def _safe_residual(b, decayed):
-    """Per-member residuals; members whose psi has decayed to (near) zero
-    report r = 1 (their ratio of two vanishing norms is meaningless)."""
-    r, rn, om = phx_batch_residual(b)
-    r = np.where(decayed, 1.0, r)
+def _safe_residual(b, skip):
+    """Per-member residuals; members whose psi has decayed to (near) zero or
+    become non-finite report r = 1 (their ratio is meaningless)."""
+    r, rn, om = phx_batch_residual(b, allow_nonfinite=True)
+    r = np.where(skip | ~np.isfinite(r), 1.0, r)
     return r, rn, om
 
 
-def generate(problem, pumps, noise_seed0, steps=40000, tol32=1e-5, chunk=512, log=None):
-    """Training pairs: each pump relaxed from seeded noise (std 1e-2 per
-    quadrature) until r_psi < tol32 or `steps`; the final state, gauge-fixed
-    and scaled, is the target.  Returns (features, targets, screen dict)."""
-    import synth
+def generate(problem, pumps, init, steps=40000, tol32=1e-5, chunk=512, log=None):
+    """Training pairs: each pump relaxed from init(i0, i1) (see ``screen``)
+    until r_psi < tol32 or `steps`; the final state, gauge-fixed and scaled,
+    is the target.  Returns (features, targets, screen dict); the screen
+    dict's ``steps`` is >= 0 exactly for the pairs that reached tol32."""
     n = problem.n
-
-    def cold(i0, i1):
-        z = np.stack([synth.complex_normal((n, n), 1e-2, noise_seed0 + i) for i in range(i0, i1)])
-        return (torch.as_tensor(z.astype(np.complex64)).cuda(),
-                torch.zeros(i1 - i0, n, n, device="cuda"))
-
-    res = screen(problem, pumps, cold, tol32=tol32, cap=steps, chunk=chunk, collect=True, log=log)
+    res = screen(problem, pumps, init, tol32=tol32, cap=steps, chunk=chunk, collect=True,
+                 log=log)
     feats = features(problem, pumps)
     targs = torch.empty(len(pumps), n, n, 3, device="cuda")
     phx_fno_targets(res.pop("psi"), res.pop("nres"), SCALE_PSI, SCALE_N, targs, _stream())
@@ -297,9 +385,8 @@ def new_network(problem, max_batch=8, channels=32, layers=4, modes_x=16, modes_y
 
 
 def initial_weights(net, seed):
-    """Seeded initial weights in the flat layout (spectral ~ U[0, 1/C^2),
-    dense ~ U[-1/sqrt(fan_in), 1/sqrt(fan_in)), biases 0)."""
-    import synth
+    """Seeded initial weights in the flat layout (spectral ~ U[0, 1/C^2)
+    (Li et al.), dense ~ U[-1/sqrt(fan_in), 1/sqrt(fan_in)), biases 0)."""
     c = net.cfg
     C, MX, MY, Pp = c["channels"], c["modes_x"], c["modes_y"], c["proj_hidden"]
     shapes = [("W_lift", (c["in_channels"], C)), ("b_lift", (C,))]
@@ -308,7 +395,18 @@ def initial_weights(net, seed):
                    ("W%d" % l, (C, C)), ("b%d" % l, (C,))]
     shapes += [("Q1", (C, Pp)), ("q1", (Pp,)), ("Q2", (Pp, c["out_channels"])),
                ("q2", (c["out_channels"],))]
-    w = synth.fno_init_weights(shapes, seed, C)
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in shapes:
+        size = int(np.prod(shape))
+        if name.startswith("R"):
+            parts.append(rng.uniform(0.0, 1.0 / (C * C), size))
+        elif len(shape) == 2:
+            bound = 1.0 / np.sqrt(shape[0])
+            parts.append(rng.uniform(-bound, bound, size))
+        else:
+            parts.append(np.zeros(size))
+    w = np.concatenate(parts).astype(np.float32)
     assert w.size == net.num_params
     return w
 
@@ -318,126 +416,3 @@ def density_match(psi_a, psi_b):
     a = psi_a.abs().double() ** 2
     b = psi_b.abs().double() ** 2
     return float(torch.linalg.vector_norm(a - b) / max(float(torch.linalg.vector_norm(b)), 1e-300))
-
-
-def run_experiment(n_train=2000, n_test=200, gen_steps=40000, epochs=40, cap=200000,
-                   tol=1e-6, tol32=1e-5, check_every=100, seed=0, time_limit=None, log=print):
-    """Generate, train, and compare warm and cold relaxations on held-out
-    pumps.  Returns a JSON-able report."""
-    import synth
-    c = synth.load_constants()["steady_256_L128"]
-    pthr = synth.load_constants()["pump_threshold"]
-    d = synth.base_params(256, 256, 128.0, 128.0, dt=c["dt"], **synth.reservoir_physics())
-    prob = Problem(d, pthr)
-    n = prob.n
-    rep = {"workload": "steady_256: 256x256, 128 um periodic, config-2 physics, dt %.6g ps "
-                       "(0.85 of the RK4 limit); pumps: sums of 1-4 Gaussians, waist 3-15 um, "
-                       "peak 1-3 P_thr" % c["dt"],
-           "n_train": n_train, "n_test": n_test, "gen_steps": gen_steps, "epochs": epochs,
-           "tol": tol, "tol32": tol32, "check_every": check_every, "cap": cap}
-    t_all = time.time()
-    train_pumps = synth.random_gaussian_pumps(256, 128.0, n_train, seed=5000)
-    test_pumps = synth.random_gaussian_pumps(256, 128.0, n_test, seed=5000 + n_train)
-    t0 = time.time()
-    feats, targs, gen = generate(prob, train_pumps, 105000, steps=gen_steps, tol32=tol32, log=log)
-    rep["generate_s"] = time.time() - t0
-    rep["train_converged_fraction"] = float((gen["steps"] >= 0).mean())
-    rep["train_decayed_fraction"] = float(gen["decayed"].mean())
-    # held-out targets from the same protocol (for the held-out loss)
-    tf, tt, tgen = generate(prob, test_pumps, 105000 + n_train, steps=gen_steps, tol32=tol32,
-                            log=log)
-    net = new_network(prob)
-    phx_fno_set_params(net, initial_weights(net, seed))
-    t0 = time.time()
-    hist = train(net, feats, targs, epochs, log=log)
-    torch.cuda.synchronize()
-    rep["train_s"] = time.time() - t0
-    rep["train_loss"] = hist
-    rep["heldout_loss"] = eval_loss(net, tf, tt)
-    del feats, targs
-    # screening of held-out pumps: cold (fresh noise) and warm (prediction)
-    cold_seed = 205000
-
-    def cold(i0, i1):
-        z = np.stack([synth.complex_normal((n, n), 1e-2, cold_seed + i) for i in range(i0, i1)])
-        return (torch.as_tensor(z.astype(np.complex64)).cuda(),
-                torch.zeros(i1 - i0, n, n, device="cuda"))
-
-    wpsi, wn = predict_states(net, prob, tf)
-
-    def warm(i0, i1):
-        return wpsi[i0:i1].contiguous(), wn[i0:i1].contiguous()
-
-    t0 = time.time()
-    sc = screen(prob, test_pumps, cold, tol32=tol32, cap=cap, check_every=check_every, log=log)
-    sw = screen(prob, test_pumps, warm, tol32=tol32, cap=cap, check_every=check_every, log=log)
-    rep["screen_s"] = time.time() - t0
-    both = np.where((sc["steps"] >= 0) & (sw["steps"] >= 0))[0]
-    rep["screen"] = {
-        "cold_converged": int((sc["steps"] >= 0).sum()), "warm_converged": int((sw["steps"] >= 0).sum()),
-        "cold_decayed": int(sc["decayed"].sum()), "warm_decayed": int(sw["decayed"].sum()),
-        "both_converged": int(len(both)),
-        "cold_steps32_median": float(np.median(sc["steps"][both])) if len(both) else None,
-        "warm_steps32_median": float(np.median(sw["steps"][both])) if len(both) else None}
-    # timed single-instance relaxations to tol for members converged in both
-    rows = []
-    for i in both:
-        if time_limit and time.time() - t_all > time_limit:
-            break
-        z = cold(int(i), int(i) + 1)
-        rc = relax(prob, test_pumps[i], init=(z[0][0], z[1][0]), tol=tol, tol32=tol32,
-                   check_every=check_every, cap=cap, instance=int(i))
-        rw = relax(prob, test_pumps[i], net=net, tol=tol, tol32=tol32, check_every=check_every,
-                   cap=cap, instance=int(i))
-        row = {"i": int(i), "cold_steps": rc["steps"], "warm_steps": rw["steps"],
-               "cold_ms": rc["ms"], "warm_ms": rw["ms"], "cold_r": rc["r"], "warm_r": rw["r"],
-               "cold_converged": rc["converged"], "warm_converged": rw["converged"]}
-        if rc["converged"] and rw["converged"]:
-            row["density_rel_diff"] = density_match(rw["state"][0], rc["state"][0])
-        rows.append(row)
-    rep["relax"] = rows
-    ok = [r for r in rows if r["cold_converged"] and r["warm_converged"]]
-    if ok:
-        cs = np.array([r["cold_steps"] for r in ok])
-        ws = np.array([r["warm_steps"] for r in ok])
-        cm = np.array([r["cold_ms"] for r in ok])
-        wm = np.array([r["warm_ms"] for r in ok])
-        dm = np.array([r.get("density_rel_diff", np.nan) for r in ok])
-        q = lambda a: [float(np.percentile(a, 25)), float(np.median(a)), float(np.percentile(a, 75))]
-        rep["summary"] = {"pairs": len(ok), "cold_steps_q": q(cs), "warm_steps_q": q(ws),
-                          "cold_ms_q": q(cm), "warm_ms_q": q(wm),
-                          "warm_faster_fraction": float((wm < cm).mean()),
-                          "speedup_median_ms": float(np.median(cm / wm)),
-                          "same_state_fraction": float((dm < 1e-3).mean()),
-                          "density_rel_diff_median": float(np.nanmedian(dm))}
-    rep["total_s"] = time.time() - t_all
-    return rep, net
-
-
-def main(argv=None):
-    ap = argparse.ArgumentParser(description="FNO warm start: generate, train, compare")
-    ap.add_argument("--train", type=int, default=2000)
-    ap.add_argument("--test", type=int, default=200)
-    ap.add_argument("--gen-steps", type=int, default=40000)
-    ap.add_argument("--epochs", type=int, default=40)
-    ap.add_argument("--cap", type=int, default=200000)
-    ap.add_argument("--time-limit", type=float, default=None)
-    ap.add_argument("--out", default=None)
-    ap.add_argument("--save-weights", default=None)
-    a = ap.parse_args(argv)
-    from . import _build
-    _build.build()
-    rep, net = run_experiment(a.train, a.test, a.gen_steps, a.epochs, a.cap,
-                              time_limit=a.time_limit,
-                              log=lambda s: print(s, file=sys.stderr, flush=True))
-    if a.save_weights:
-        np.save(a.save_weights, phx_fno_get_params(net))
-    js = json.dumps(rep, indent=1)
-    if a.out:
-        with open(a.out, "w") as f:
-            f.write(js)
-    print(js)
-
-
-if __name__ == "__main__":
-    main()

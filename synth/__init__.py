@@ -14,6 +14,8 @@ files are not available, so these stand in for them):
   psi0 = 5 exp(-r^2/3^2) + complex normal noise (std 1e-2 per quadrature).
 * ``reservoir_1024``   -- scalar + reservoir, 1024x1024, 100 um, periodic, ring
   pump of radius 20 um and width 3 um at 1.5 P_thr, psi0 = noise, n0 = 0.
+* ``reservoir_2048``   -- the same physics, cell size and time step on
+  2048x2048 over 200 um.
 * ``spinor_2048``      -- TE-TM spinor + reservoir, 2048x2048, 200 um, Gaussian
   pump of waist 10 um at 1.5 P_thr on both components, per-step noise.
 * ``ensemble``         -- 256 reservoir instances, 64 each at 128^2 .. 1024^2,
@@ -116,6 +118,14 @@ def reservoir_grid(n, length=100.0, pump_factor=1.5, seed=2, dt=None,
 
 def reservoir_1024(seed=2):
     return reservoir_grid(1024, seed=seed, const_key="reservoir_1024_L100")
+
+
+def reservoir_2048(seed=2):
+    """The reservoir workload's physics, cell size (100/1024 um) and time step
+    on a 2048^2 grid over 200 um (ring pump radius 20 um, width 3 um)."""
+    cfg = reservoir_grid(2048, length=200.0, seed=seed, const_key="reservoir_2048_L200")
+    cfg["name"] = "reservoir_2048"
+    return cfg
 
 
 def spinor_grid(n, length=200.0, seed=3, const_key=None):
@@ -234,10 +244,15 @@ def crop(cfg, m):
                 V=win(cfg.get("V")), E=win(cfg.get("E")))
 
 
-def random_gaussian_pumps(n=256, length=128.0, count=1, seed=5000):
+def random_gaussian_pumps(n=256, length=128.0, count=1, seed=5000, threshold=None):
     """count pump images, each a sum of 1-4 Gaussians exp(-|r-c|^2/w^2) with
-    w ~ U[3, 15] um, peak ~ U[1, 3] P_thr, centres within L/2 - 2w."""
+    w ~ U[3, 15] um, peak ~ U[1, 3] x threshold(w), centres within L/2 - 2w.
+    threshold: callable waist -> threshold pump peak of a spot of that waist
+    (supplied by the caller, e.g. measured with the solver); default the
+    homogeneous P_thr for every waist."""
     pthr = load_constants()["pump_threshold"]
+    if threshold is None:
+        threshold = lambda w: pthr  # noqa: E731
     imgs = np.empty((count, n, n))
     for k in range(count):
         rng = np.random.default_rng(seed + k)
@@ -245,7 +260,7 @@ def random_gaussian_pumps(n=256, length=128.0, count=1, seed=5000):
         img = np.zeros((n, n))
         for _ in range(m):
             w = float(rng.uniform(3.0, 15.0))
-            amp = float(rng.uniform(1.0, 3.0)) * pthr
+            amp = float(rng.uniform(1.0, 3.0)) * float(threshold(w))
             lim = 0.5 * length - 2.0 * w
             cx, cy = rng.uniform(-lim, lim, size=2)
             img += gaussian(n, n, length, length, amp, w, cx, cy)

@@ -30,6 +30,8 @@ def main():
     for n in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192):
         out["reservoir_%d_L100" % n] = {"dt": half_limit(nx=n, ny=n, lx=100.0,
                                                          ly=100.0, **res)}
+    # config-2 physics at 2048^2 with config 2's cell size (200 um box)
+    out["reservoir_2048_L200"] = {"dt": half_limit(nx=2048, ny=2048, lx=200.0, ly=200.0, **res)}
     for n, L in ((2048, 200.0), (512, 50.0), (64, 6.25), (96, 9.375)):
         out["spinor_%d_L%g" % (n, L)] = {"dt": half_limit(
             nx=n, ny=n, lx=L, ly=L, spinor=True, delta_lt=0.025, **res)}

@@ -1,11 +1,13 @@
 """What the learned warm start gains over the plain method.
 
 A reduced run of the whole loop on the steady-state workload (256 x 256,
-128 um, random sums of 1-4 Gaussian pumps at 1-3 P_thr): training pairs
-generated by the batched solver, the network trained on the GPU by this
-package's kernels, then held-out pumps relaxed to r_psi < 1e-6 from noise
-(cold) and from the network's prediction (warm) under the same protocol.
-Every kernel is deterministic, so the outcome is reproducible."""
+128 um, random sums of 1-4 Gaussian pumps at 1-3 times the solver-measured
+threshold of a spot of that waist): training pairs generated by the batched
+solver, the network trained on the GPU by this package's kernels on the
+pairs that reached the FP32 tolerance, then held-out pumps relaxed to
+r_psi < 1e-6 from noise (cold) and from the network's prediction (warm)
+under the same protocol.  Every kernel is deterministic, so the outcome is
+reproducible."""
 import numpy as np
 import pytest
 
@@ -14,23 +16,45 @@ from gpu_util import phx
 pytestmark = pytest.mark.gpu
 
 
-def test_warm_start_beats_cold_start():
+@pytest.fixture(scope="module")
+def experiment():
     phx()
-    from paper_2411_18341_gb300 import warmstart
-    rep, net = warmstart.run_experiment(n_train=192, n_test=96, gen_steps=30000, epochs=12,
-                                        cap=60000, log=lambda s: None)
+    import bench
+    import json
+    rep, net = bench.steady_experiment(n_train=384, n_test=48, gen_steps=30000, epochs=15,
+                                       cap=60000)
+    print(json.dumps({k: v for k, v in rep.items() if k != "relax"}))
+    return rep, net
+
+
+def test_spot_thresholds_rise_for_small_spots(experiment):
+    """A smaller spot loses more particles to its surroundings: its measured
+    threshold is never below a wider spot's, and every spot needs at least
+    the homogeneous threshold."""
+    rep, _ = experiment
+    thr = [rep["spot_threshold_factors"][k] for k in sorted(rep["spot_threshold_factors"],
+                                                            key=float)]
+    assert all(np.isfinite(thr)), thr
+    assert all(t >= 0.99 for t in thr), thr
+    assert all(a >= b * 0.98 for a, b in zip(thr, thr[1:])), thr
+
+
+def test_warm_start_beats_cold_start(experiment):
+    rep, net = experiment
+    # pumps drawn relative to the spot threshold mostly condense and relax
+    assert rep["train_converged"] >= 0.5 * rep["n_train"], rep["train_converged"]
     # the network learned something it did not know at initialisation
     assert rep["heldout_loss"] < 0.5 * rep["train_loss"][0]
     s = rep.get("summary")
-    assert s is not None and s["pairs"] >= 3, rep["screen"]
+    assert s is not None and s["pairs"] >= 10, rep["screen"]
     # warm and cold relax to the same stationary state (densities agree); a
     # pump with two stationary states may, rarely, pick different ones
-    assert s["same_state_fraction"] >= 0.75, s
-    # the warm start gets there in fewer steps and less GPU time, per pump
-    # (medians over the pairs) and on most pumps
+    assert s["same_state_fraction"] >= 0.8, s
+    # the warm start gets there in fewer steps and less GPU time: median
+    # speed-up of at least 1.2x over the pairs, faster on most pumps
     assert s["warm_steps_q"][1] < s["cold_steps_q"][1], s
-    assert s["speedup_median_ms"] > 1.0, s
-    assert s["warm_faster_fraction"] >= 0.5, s
+    assert s["speedup_median_ms"] >= 1.2, s
+    assert s["warm_faster_fraction"] >= 0.6, s
     # every converged relaxation really reached the tolerance
     pairs = [r for r in rep["relax"] if r["cold_converged"] and r["warm_converged"]]
     assert all(r["cold_r"] < 1e-6 and r["warm_r"] < 1e-6 for r in pairs)
