@@ -41,8 +41,10 @@ RK4_STEPS = 10000
 # stages plus the final combination.  The coherent drive adds the complex
 # product E exp(-i omega t)/hbar into H, 4 FMA per stage.
 FLOPS_PER_SITE = {"reservoir": 194, "conservative": 144, "driven": 176}
-# FP64 pipe of GB300: 2 DFMA per SM per cycle (152 SMs, 2.07 GHz max clock).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 pipe of GB300 from unit counts: 2 DFMA per SM per cycle (152 SMs,
+# 2.07 GHz max clock) -- context only; the roofline uses the measured peak
+# (phx_alu_peak_probe).
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 BYTES_PER_SITE = {  # algorithmic bytes per site per RK4 step (read + write once)
     (32, "reservoir"): 28, (64, "reservoir"): 56,
     (32, "conservative"): 16, (64, "conservative"): 32,
@@ -68,6 +70,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--integrator", default="rk4", choices=["rk4", "ssf"],
                     help="time stepper of the single-handle workloads: fused RK4 or split-step Fourier")
+    ap.add_argument("--dt-factor", type=float, default=1.0,
+                    help="split-step only: time step = this x the workload's (half the RK4 "
+                         "limit); above 2 the handle is created with the split-step integrator")
     ap.add_argument("--tile", type=int, default=0,
                     help="step-kernel configuration (0 = autotune, 1..7 TMA-fed, 9 generic)")
     ap.add_argument("--no-steady", action="store_true",
@@ -769,6 +774,11 @@ def main():
     real = torch.float32 if prec == 32 else torch.float64
     cplx = torch.complex64 if prec == 32 else torch.complex128
     d = cfg["params"]
+    if args.dt_factor != 1.0:
+        if args.integrator != "ssf":
+            raise SystemExit("--dt-factor applies to --integrator ssf only")
+        d = dict(d, dt=d["dt"] * args.dt_factor, integrator=1)
+        cfg = dict(cfg, params=d)
     nx, ny = d["nx"], d["ny"]
     nc = 2 if d["spinor"] else 1
     sites = nx * ny
@@ -886,11 +896,14 @@ def main():
     if prec == 64 and kind in FLOPS_PER_SITE and args.integrator == "rk4":
         # the FP64 stencil is bound by the FP64 pipe, not by HBM
         tf = FLOPS_PER_SITE[kind] * sites / kern_s / 1e12
-        roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+        fp64_peak = phx.phx_alu_peak_probe(64)
+        roof = {"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": tf / fp64_peak, "traffic": traffic,
                 "kernel": "rk4_step_generic (FP64)", "algorithmic_flops_per_site": FLOPS_PER_SITE[kind],
                 "hbm_gbs_algorithmic": achieved, "avg_launch_us": kern_s * 1e6,
-                "peak_source": "derived: 152 SMs x 2 DFMA/cycle x 2 flop x 2.07 GHz"}
+                "peak_source": "measured: phx_alu_peak_probe(64), independent DFMA chains "
+                               "timed with CUDA events in this run (nominal from unit counts "
+                               "%.2f TFLOP/s)" % FP64_NOMINAL_TFLOPS}
     else:
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
@@ -922,6 +935,8 @@ def main():
                        else "fused RK4 steps"),
                    "l2": l2_note,
                    "tile": phx.phx_tile(h), "integrator": args.integrator,
+                   "dt_ps": d["dt"],
+                   "simulated_ps_per_s": d["dt"] * rk4_steps / (ms * 1e-3),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": world * sites * rk4_steps / e2e_s, "unit": "site-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

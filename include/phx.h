@@ -59,7 +59,7 @@ extern "C" {
 
 typedef enum phx_status {
   PHX_OK = 0,
-  PHX_EINVAL = 1,      /* bad argument (null pointer, size, dt above the RK4 limit, ...) */
+  PHX_EINVAL = 1,      /* bad argument (null pointer, size, dt above its limit, ...) */
   PHX_ENOMEM = 2,      /* device or host allocation failed */
   PHX_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
   PHX_ENONFINITE = 4,  /* a reduction found NaN or Inf in the state */
@@ -95,15 +95,21 @@ typedef struct phx_params {
   double R;                  /* ps^-1 um^2 */
   double gamma_c, gamma_r;   /* ps^-1 */
   double delta_lt;           /* TE-TM splitting Delta_LT, meV um^2 (spinor only) */
-  double dt;                 /* RK4 step, ps; rejected above the stability limit */
+  double dt;                 /* time step, ps; rejected above the integrator's limit */
   double noise_var;          /* E|xi|^2 added per site and step; 0 = off */
   double wigner_nu;          /* truncated-Wigner noise intensity nu >= 0; 0 = off */
   double drive_omega;        /* angular frequency of the coherent drive, rad/ps */
   uint64_t seed;             /* Philox key */
   uint32_t instance;         /* Philox counter word 1 (ensemble member id) */
-  uint32_t reserved;
+  uint32_t integrator;       /* PHX_INTEGRATOR_RK4 (default): dt must lie within
+                                phx_stability_dt; PHX_INTEGRATOR_SPLIT: the handle
+                                is stepped by phx_step_ssf, whose linear part is
+                                exact, and dt is validated against the split-step
+                                scheme's own limit instead (see phx_create) */
   void* stream;              /* cudaStream_t */
 } phx_params;
+
+enum { PHX_INTEGRATOR_RK4 = 0, PHX_INTEGRATOR_SPLIT = 1 };
 
 typedef struct phx_handle phx_handle;
 
@@ -122,8 +128,18 @@ phx_status phx_stability_dt(const phx_params* p, double* dt_max);
 /* Validate p, allocate the device state on the current CUDA device and
  * zero it (psi = 0, n = 0, P = 0, V absent, step 0, t = 0).
  * EINVAL: bad sizes, BC, precision, spinor-only terms on a scalar problem,
- * dt <= 0 or dt > phx_stability_dt.  ENODEV: no sm_103 (GB300) device.
- * ENOMEM / ECUDA on allocation failure.  *out is NULL on error. */
+ * dt <= 0, an unknown integrator, or a dt above the integrator's limit:
+ *   PHX_INTEGRATOR_RK4   -- dt > phx_stability_dt;
+ *   PHX_INTEGRATOR_SPLIT -- the split-step scheme (phx_step_ssf) propagates
+ *     the linear part exactly, so the stencil's limit does not apply; the
+ *     handle needs periodic boundaries and no truncated-Wigner noise, and with
+ *     a reservoir the local half steps (one RK4 step of dt/2 of the local
+ *     ODE) need dt/2 x gamma_r within RK4's real-axis extent (2.78).  The
+ *     state-dependent local rates (Kerr phase, gain) are not checked.
+ *     phx_step_n on such a handle returns ESTATE when dt exceeds
+ *     phx_stability_dt.
+ * ENODEV: no sm_103 (GB300) device.  ENOMEM / ECUDA on allocation failure.
+ * *out is NULL on error. */
 phx_status phx_create(const phx_params* p, phx_handle** out);
 
 /* Bytes of the five state buffers a handle with parameters p holds, for
@@ -179,6 +195,9 @@ phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
  * handle is periodic in x and y and has neither a drive nor truncated-Wigner
  * noise; ECUDA if cuFFT is missing. */
 phx_status phx_step_ssf(phx_handle* h, int64_t nsteps);
+
+/* (Time steps above the RK4 limit: create the handle with
+ * integrator = PHX_INTEGRATOR_SPLIT.) */
 
 /* nsteps imaginary-time steps (t -> -i tau in the conservative part of
  * Eq. PULSE_psi; the conclusions name the method without details), split
@@ -250,6 +269,16 @@ int32_t phx_tile(const phx_handle* h);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t phx_launch_count(void);
+
+/* Measured non-tensor FMA throughput of the current device (no counterpart in
+ * the paper; the denominator of the arithmetic roofline of the FP64 step):
+ * a kernel of independent fused multiply-add chains in `precision` (32 or
+ * 64), 8 CTAs of 256 threads per SM, timed with CUDA events on the legacy
+ * default stream after one warm-up launch; *tflops = 2 x FMAs / time, in
+ * TFLOP/s.  Allocates and frees a small output buffer; synchronises.
+ * Changes no device setting.  EINVAL (bad precision, NULL), ENODEV, ENOMEM,
+ * ECUDA. */
+phx_status phx_alu_peak_probe(int32_t precision, double* tflops);
 
 /* Failure-injection hook for tests (no counterpart in the paper).  Arms, for
  * the next matching event in this process, one of:

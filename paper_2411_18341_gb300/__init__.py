@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libphx.so")
 
 PHX_OK = 0
 PHX_ENONFINITE = 4
+INTEGRATOR_RK4, INTEGRATOR_SPLIT = 0, 1
 STATUS = {0: "PHX_OK", 1: "PHX_EINVAL", 2: "PHX_ENOMEM", 3: "PHX_ECUDA",
           4: "PHX_ENONFINITE", 5: "PHX_ETIMEOUT", 6: "PHX_ESTATE",
           7: "PHX_ENODEV"}
@@ -52,7 +53,7 @@ class phx_params(ctypes.Structure):
         ("wigner_nu", ctypes.c_double),
         ("drive_omega", ctypes.c_double),
         ("seed", ctypes.c_uint64),
-        ("instance", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("instance", ctypes.c_uint32), ("integrator", ctypes.c_uint32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -95,6 +96,7 @@ _SIGS = {
     "phx_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "phx_tile": (ctypes.c_int32, [ctypes.c_void_p]),
     "phx_launch_count": (ctypes.c_uint64, []),
+    "phx_alu_peak_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "phx_debug_inject": (ctypes.c_int, [ctypes.c_uint32]),
     "phx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "phx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -361,6 +363,13 @@ def phx_launch_count():
     return int(lib().phx_launch_count())
 
 
+def phx_alu_peak_probe(precision):
+    """Measured FMA throughput (TFLOP/s) of the current device in FP32 or FP64."""
+    out = ctypes.c_double()
+    _check(lib().phx_alu_peak_probe(int(precision), ctypes.byref(out)))
+    return out.value
+
+
 INJECT_ALLOC, INJECT_LAUNCH, INJECT_TIMEOUT = 1, 2, 4
 
 
@@ -533,7 +542,8 @@ def phx_batch_destroy(b):
 
 PARAM_KEYS = ("nx", "ny", "lx", "ly", "bc_x", "bc_y", "spinor", "reservoir",
               "kappa", "g", "g_x", "g_r", "R", "gamma_c", "gamma_r", "delta_lt",
-              "dt", "noise_var", "wigner_nu", "drive_omega", "seed", "instance")
+              "dt", "noise_var", "wigner_nu", "drive_omega", "seed", "instance",
+              "integrator")
 
 
 def params_from_dict(d, precision=32, stream=None, tile=0):
