@@ -82,6 +82,8 @@ const char* check_params(const phx_params* p, double* dtmax_out) {
   if (!p->spinor && (p->g_x != 0.0 || p->delta_lt != 0.0)) return "g_x and delta_lt need spinor = 1";
   if (p->noise_var < 0) return "noise_var must be >= 0";
   if (p->wigner_nu < 0) return "wigner_nu must be >= 0";
+  if (p->integrator != PHX_INTEGRATOR_RK4 && p->integrator != PHX_INTEGRATOR_SPLIT)
+    return "integrator must be PHX_INTEGRATOR_RK4 or PHX_INTEGRATOR_SPLIT";
   double lam = spectral_radius(*p);
   double dtmax = lam > 0 ? 2.0 * std::sqrt(2.0) * HBAR / lam : INFINITY;
   if (dtmax_out) *dtmax_out = dtmax;

@@ -56,6 +56,7 @@ struct phx_handle {
   int device = 0;
   int num_sms = 0;
   int* err_dev = nullptr;      // set by kernels whose bounded waits gave up
+  double dt_rk4 = 0;           // RK4 stability limit of the grid (phx_stability_dt)
   int tile_cfg = 0;            // chosen tile configuration of the FP32 scalar kernel
   bool tuned = false;          // tile_cfg settled (explicit or autotuned)
   bool maps_ok = false;        // TMA tensor maps encoded for (tile_cfg, has_V)
@@ -396,7 +397,20 @@ phx_status create_impl(const phx_params* p, void* const* ext, phx_handle** out) 
   phx_status st = validate(p, &dtmax);
   if (st != PHX_OK) return st;
   if (!(p->dt > 0.0)) return fail(nullptr, PHX_EINVAL, "dt must be > 0");
-  if (p->dt > dtmax * (1.0 + 1e-12)) {
+  if (p->integrator == PHX_INTEGRATOR_SPLIT) {
+    // split-step: exact linear propagator; the local half steps of the
+    // reservoir model are one RK4 step of dt/2 with decay rate gamma_r
+    if (p->bc_x != PHX_BC_PERIODIC || p->bc_y != PHX_BC_PERIODIC)
+      return fail(nullptr, PHX_EINVAL, "integrator = split-step needs periodic boundaries");
+    if (p->wigner_nu > 0.0)
+      return fail(nullptr, PHX_EINVAL, "integrator = split-step excludes truncated-Wigner noise");
+    if (p->reservoir && 0.5 * p->dt * p->gamma_r > 2.78) {
+      char buf[160];
+      std::snprintf(buf, sizeof buf,
+                    "dt = %.6g ps: the local RK4 half step needs dt/2 * gamma_r <= 2.78", p->dt);
+      return fail(nullptr, PHX_EINVAL, buf);
+    }
+  } else if (p->dt > dtmax * (1.0 + 1e-12)) {
     char buf[160];
     std::snprintf(buf, sizeof buf, "dt = %.6g ps exceeds the RK4 stability limit %.6g ps",
                   p->dt, dtmax);
@@ -415,6 +429,7 @@ phx_status create_impl(const phx_params* p, void* const* ext, phx_handle** out) 
   phx_handle* h = new (std::nothrow) phx_handle();
   if (!h) return fail(nullptr, PHX_ENOMEM, "host allocation failed");
   h->p = *p;
+  h->dt_rk4 = dtmax;
   h->device = dev;
   h->num_sms = prop.multiProcessorCount;
   h->stream = static_cast<cudaStream_t>(p->stream);
@@ -587,6 +602,9 @@ phx_status phx_get_state(phx_handle* h, void* psi, void* n, int on_device) {
 phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
   if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(h, PHX_EINVAL, "nsteps must be >= 0");
+  if (h->p.dt > h->dt_rk4 * (1.0 + 1e-12))
+    return fail(h, PHX_ESTATE, "dt exceeds the RK4 stability limit (a split-step handle: use "
+                               "phx_step_ssf)");
   DeviceGuard dg(h->device);
   const Coeffs k = make_coeffs(h->p);
   const NoiseKey nz = make_noise_key(h->p);

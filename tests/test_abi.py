@@ -84,6 +84,31 @@ def test_invalid_params_rejected_before_device(phx):
         assert e.value.status == 1, (kw, e.value)
 
 
+def test_integrator_limits_checked_before_device(phx):
+    """dt above the RK4 limit: rejected (EINVAL) for the RK4 integrator,
+    accepted by validation for the split-step integrator (then ENODEV on a
+    machine without a GB300, PHX_OK with one); the split-step integrator
+    refuses zero boundaries, truncated-Wigner noise, a reservoir time step
+    beyond its local RK4 half step, and unknown integrator codes."""
+    base = dict(nx=16, ny=16, lx=4.0, ly=4.0)
+    lim = phx.phx_stability_dt(phx.phx_params_init(**base, dt=1e-3))
+    with pytest.raises(phx.PhxError) as e:
+        phx.phx_create(phx.phx_params_init(**base, dt=5 * lim))
+    assert e.value.status == 1
+    try:
+        h = phx.phx_create(phx.phx_params_init(**base, dt=5 * lim, integrator=1))
+        phx.phx_destroy(h)
+    except phx.PhxError as err:
+        assert err.status == 7, err  # ENODEV: validation passed
+    for kw in (dict(bc_x=1), dict(wigner_nu=1.0),
+               dict(reservoir=1, gamma_r=1.0, dt=6.0), dict(integrator=2)):
+        q = dict(base, dt=5 * lim, integrator=1)
+        q.update(kw)
+        with pytest.raises(phx.PhxError) as e:
+            phx.phx_create(phx.phx_params_init(**q))
+        assert e.value.status == 1, kw
+
+
 def test_struct_size_checked(phx):
     p = phx.phx_params_init(dt=1e-3)
     p.struct_size = 8

@@ -138,3 +138,52 @@ def test_ssf_reservoir_parity(prec, spinor):
     o_psi, o_n = gp.run(o_psi, o_n, P, V, gp.Params(**d), 3, step0=16)
     assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
     assert rel_l2(g_n, o_n) <= TOL[prec], rel_l2(g_n, o_n)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("factor", [4.0, 12.0])
+@pytest.mark.parametrize("kind", ["loss", "reservoir", "spinor_tetm"])
+def test_ssf_time_step_above_the_rk4_limit(prec, factor, kind):
+    """A split-step handle (integrator = split) steps at dt = factor x the RK4
+    stability limit: the exact linear propagator is stable there; parity with
+    the oracle's split-step at the same dt (reservoir model: local RK4 half
+    steps, still well inside their own limit).  phx_step_n refuses the
+    handle's dt."""
+    m = phx()
+    real, cplx = (np.float64, np.complex128) if prec == 64 else (np.float32, np.complex64)
+    if kind == "reservoir":
+        d = synth.base_params(96, 64, 28.8, 19.2, g=0.3, g_r=0.5, R=0.3, gamma_c=0.15,
+                              gamma_r=0.4, reservoir=True, noise_var=1e-4, seed=49)
+        nc, res = 1, True
+    elif kind == "spinor_tetm":
+        d = synth.base_params(96, 64, 28.8, 19.2, g=0.3, g_x=0.1, gamma_c=0.1, spinor=True,
+                              delta_lt=0.2, noise_var=1e-4, seed=51)
+        nc, res = 2, False
+    else:
+        d = synth.base_params(96, 64, 28.8, 19.2, g=0.3, gamma_c=0.1, noise_var=1e-4, seed=53)
+        nc, res = 1, False
+    lim = gp.stability_dt_max(gp.Params(**d))
+    d.update(dt=factor * lim, integrator=1)
+    psi0, n0, P, V = synth.random_state(nc, 64, 96, 17, amp=0.5, reservoir=res, smooth=True)
+    psi0, n0, P, V = (rounded(x, prec) for x in (psi0, n0, P, V))
+    h = m.phx_create(m.params_from_dict(d, precision=prec))
+    if res:
+        m.phx_set_pump(h, np.ascontiguousarray(P[0], real))
+    m.phx_set_potential(h, np.ascontiguousarray(V, real))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, cplx),
+                    None if n0 is None else np.ascontiguousarray(n0, real))
+    m.phx_step_ssf(h, 10)
+    g_psi, g_n = get_state(h, prec)
+    p = gp.Params(**{k: v for k, v in d.items() if k != "integrator"})
+    if res:
+        o_psi, o_n = gp.run_ssf_reservoir(psi0, n0, P, V, p, 10)
+        assert rel_l2(g_n, o_n) <= TOL[prec], rel_l2(g_n, o_n)
+    else:
+        o_psi = gp.run_ssf(psi0, V, p, 10)
+    assert rel_l2(g_psi, o_psi) <= TOL[prec], rel_l2(g_psi, o_psi)
+    assert np.all(np.isfinite(g_psi))
+    s, t = m.phx_time(h)
+    assert s == 10 and abs(t - 10 * d["dt"]) <= 1e-12 * t
+    with pytest.raises(m.PhxError) as e:
+        m.phx_step_n(h, 1)
+    assert e.value.status == 6  # PHX_ESTATE
