@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--workload", default="reservoir_2048",
                     choices=["reservoir_2048", "reservoir_1024", "reservoir", "spinor_2048",
                              "conservative_64", "ensemble", "twa_ensemble", "driven_9000",
-                             "steady_256"])
+                             "steady_256", "fno_train"])
     ap.add_argument("--grid", type=int, default=1024,
                     help="grid size of the 'reservoir' workload (100 um box, config-2 physics)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -75,6 +75,8 @@ def parse():
                          "limit); above 2 the handle is created with the split-step integrator")
     ap.add_argument("--tile", type=int, default=0,
                     help="step-kernel configuration (0 = autotune, 1..7 TMA-fed, 9 generic)")
+    ap.add_argument("--no-precision-error", action="store_true",
+                    help="skip the FP64 run that measures the FP32 error (profiling runs)")
     ap.add_argument("--no-steady", action="store_true",
                     help="skip the reduced warm-vs-cold steady-state measurement")
     # steady_256 (warm-start experiment) sizes
@@ -507,7 +509,7 @@ def run_ensemble(args, world, rank, local, pg):
     # FP32 error per result: two members (the smallest and the largest grid
     # of the ensemble; member 0 of the truncated-Wigner ensemble) against
     # the FP64 path over the same steps (noise bits identical in both)
-    picks = [0] if twa else [0, len(members) - 1]
+    picks = [] if args.no_precision_error else ([0] if twa else [0, len(members) - 1])
     prec_err = []
     for i in picks:
         m = members[i]
@@ -717,6 +719,70 @@ def steady_key(rep):
             "seconds": rep["total_s"]}
 
 
+def run_fno_train(args, world, rank, local):
+    """--workload fno_train: Adam training steps of the warm-start network
+    (256x256 grid, 4 layers, width 32, 16 x 32 kept modes, batch 8) on seeded
+    synthetic features and targets, through the C ABI.  value = training
+    samples/s; roofline = the algorithmic GEMM flops the steps issue (BF16
+    operands, FP32 accumulation) against the measured BF16 tensor peak."""
+    import torch
+    import synth
+    import paper_2411_18341_gb300 as phx
+    from paper_2411_18341_gb300 import warmstart as ws
+    torch.cuda.set_device(local)
+    d = synth.base_params(256, 256, 128.0, 128.0, dt=0.0, **synth.reservoir_physics())
+    d["dt"] = ws.stable_dt(d, 0.7)
+    prob = ws.Problem(d, ws.pump_threshold(d))
+    net = ws.new_network(prob, max_batch=8)
+    phx.phx_fno_set_params(net, ws.initial_weights(net, 0))
+    pumps = synth.random_gaussian_pumps(256, 128.0, 64, seed=9000)
+    feats = ws.features(prob, pumps)
+    rng = np.random.default_rng(9)
+    targs = torch.tensor(rng.normal(0.0, 0.3, size=(64, 256, 256, 3)).astype(np.float32),
+                         device="cuda")
+    per_step = 16   # Adam steps per bench step (128 samples)
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        for k in range(per_step):
+            b = (k * 8) % 64
+            phx.phx_fno_train_step(net, feats[b:b + 8], targs[b:b + 8], 1e-4)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    f0 = phx.phx_fno_gemm_flops(net)
+    launches0 = phx.phx_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(torch.cuda.current_device())
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = (phx.phx_fno_gemm_flops(net) - f0) / args.steps
+    pk, pk_kind = peaks()
+    tf = flops / (ms * 1e-3) / 1e12
+    line = {"metric": "FNO training samples/s", "value": per_step * 8 / (ms * 1e-3),
+            "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
+            "config": {"workload": "fno_train", "network": "4 layers, width 32, 16 x 32 modes, "
+                       "projection 64, 256 x 256 grid", "batch": 8,
+                       "per_step": "%d Adam steps (forward, backward, update)" % per_step,
+                       "ms_per_adam_step": ms / per_step},
+            "gpu_launches": int(phx.phx_launch_count() - launches0),
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": tf / pk["bf16_tflops"], "traffic": None,
+                         "kernel": "all GEMMs of the step (tcgen05 and mma.sync)",
+                         "algorithmic_gflops_per_adam_step": flops / per_step / 1e9,
+                         "peak_source": pk_kind + " (bf16 burst)"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_steady(args, world, rank):
     """--workload steady_256: the warm-start experiment as one JSON line."""
     if rank != 0:
@@ -753,6 +819,12 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
+    if args.workload == "fno_train":
+        if rank == 0:
+            run_fno_train(args, world, rank, local)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
     if args.workload == "steady_256":
         run_steady(args, world, rank)
         if pg is not None:
@@ -866,7 +938,9 @@ def main():
         phx.phx_get_state(h, out_psi, out_n)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(pg, (time.perf_counter() - t0) / e2e_steps)
-    if prec == 32:
+    if prec == 32 and args.no_precision_error:
+        prec_err = None
+    elif prec == 32:
         psi64, n64 = fp64_run(phx, d, cfg, rk4_steps, stream, dev,
                               "phx_step_ssf" if args.integrator == "ssf" else "phx_step_n")
         prec_err = precision_error(out_psi, out_n, psi64, n64,
@@ -948,10 +1022,10 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_steady and args.workload == "reservoir_2048":
         # reduced warm-vs-cold time to steady state (the metric's second part)
-        rep, _ = steady_experiment(n_train=256, n_test=64, gen_steps=30000, epochs=12,
-                                   cap=60000, time_limit=100)
+        rep, _ = steady_experiment(n_train=1024, n_test=128, gen_steps=30000, epochs=12,
+                                   cap=60000, time_limit=120)
         line["steady_state"] = dict(steady_key(rep), reduced=(
-            "256 training / 64 held-out pumps, 12 epochs, cap 6e4 steps; the full "
+            "1024 training / 128 held-out pumps, 12 epochs, cap 6e4 steps; the full "
             "experiment is --workload steady_256"))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if sites > 1 << 24:

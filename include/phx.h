@@ -433,6 +433,11 @@ phx_status phx_fno_config_init(phx_fno_config* c);
  * moments, DFT tables and activations for max_batch samples. */
 phx_status phx_fno_create(const phx_fno_config* c, phx_fno** out);
 int64_t phx_fno_num_params(const phx_fno* f);
+/* Algorithmic GEMM work issued on f since its creation: the sum over every
+ * product of 2 M N K flops (forward, backward and weight-gradient GEMMs,
+ * counted when queued), for throughput against the tensor-core roofline.
+ * EINVAL if f or flops is NULL. */
+phx_status phx_fno_gemm_flops(const phx_fno* f, double* flops);
 /* Copies the flat parameters in and resets the Adam moments and step. */
 phx_status phx_fno_set_params(phx_fno* f, const float* w, int on_device);
 phx_status phx_fno_get_params(phx_fno* f, float* w, int on_device);

@@ -128,6 +128,7 @@ _SIGS = {
     "phx_fno_config_init": (ctypes.c_int, [ctypes.POINTER(phx_fno_config)]),
     "phx_fno_create": (ctypes.c_int, [ctypes.POINTER(phx_fno_config), ctypes.POINTER(ctypes.c_void_p)]),
     "phx_fno_num_params": (ctypes.c_int64, [ctypes.c_void_p]),
+    "phx_fno_gemm_flops": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "phx_fno_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_fno_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "phx_fno_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -650,6 +651,13 @@ def phx_fno_train_step(f, x, target, lr):
                                      _fno_io(f, target, B, f.cfg["out_channels"], "target"), B,
                                      float(lr), ctypes.byref(loss)), f)
     return loss.value
+
+
+def phx_fno_gemm_flops(f):
+    """Algorithmic GEMM flops (2 M N K per product) issued on f so far."""
+    out = ctypes.c_double()
+    _fcheck(lib().phx_fno_gemm_flops(f.ptr, ctypes.byref(out)), f)
+    return out.value
 
 
 def phx_fno_destroy(f):

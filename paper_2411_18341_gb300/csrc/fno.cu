@@ -558,6 +558,7 @@ struct phx_fno {
   long long splitk_len = 0;
   float* colpart = nullptr;
   int* tc_err = nullptr;  // set by a tensor-core GEMM whose bounded wait gave up
+  double gemm_flops = 0;  // algorithmic GEMM flops issued since creation (2 M N K per product)
   double* lpart = nullptr;
   double* lpart_host = nullptr;
   int device = 0;
@@ -620,6 +621,8 @@ cudaError_t run_gemm_tc(phx_fno* f, const GemmDesc& d) {
 // short ones (the forward truncated DFTs, the per-mode mixing, the split-K
 // weight gradients) on the mma.sync kernel, whose 64-row tile wastes less.
 cudaError_t run_gemm(phx_fno* f, const GemmDesc& d) {
+  // every product of the batch has K columns except the last, which has K_last
+  f->gemm_flops += 2.0 * d.M * d.N * ((double)d.K * (d.nb1 * d.nb2 - 1) + d.K_last);
   if (d.M >= TC_BM && d.N <= 256) {
     if (d.N <= 32) return run_gemm_tc<32>(f, d);
     if (d.N <= 64) return run_gemm_tc<64>(f, d);
@@ -1066,6 +1069,12 @@ phx_status phx_fno_create(const phx_fno_config* cfg, phx_fno** out) {
 }
 
 int64_t phx_fno_num_params(const phx_fno* f) { return f ? f->nparams : 0; }
+
+phx_status phx_fno_gemm_flops(const phx_fno* f, double* flops) {
+  if (!f || !flops) return PHX_EINVAL;
+  *flops = f->gemm_flops;
+  return PHX_OK;
+}
 
 phx_status phx_fno_set_params(phx_fno* f, const float* w, int on_device) {
   if (!f || !w) return ffail(f, PHX_EINVAL, "NULL argument");
