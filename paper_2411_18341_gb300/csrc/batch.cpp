@@ -341,8 +341,11 @@ phx_status phx_batch_create(const phx_params* params, int32_t count, phx_batch**
     return failc(e, "cudaMalloc times");
   if ((e = cudaMemsetAsync(b->t_inst, 0, sizeof(double) * 2 * count, b->stream)) != cudaSuccess)
     return failc(e, "memset");
-  if ((e = cudaMalloc(&b->partials, sizeof(double) * 1216 * 8)) != cudaSuccess)
+  const size_t plen = sizeof(double) * reduce_partials_len(b->geo[0]);
+  if ((e = cudaMalloc(&b->partials, plen)) != cudaSuccess)
     return failc(e, "cudaMalloc partials");
+  if ((e = cudaMemsetAsync(b->partials, 0, plen, b->stream)) != cudaSuccess)
+    return failc(e, "memset");
   if ((e = cudaMalloc(&b->red_dev, sizeof(double) * 8 * count)) != cudaSuccess)
     return failc(e, "cudaMalloc results");
   if ((e = cudaMallocHost(&b->red_host, sizeof(double) * 8 * count)) != cudaSuccess)

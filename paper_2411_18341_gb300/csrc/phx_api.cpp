@@ -286,6 +286,18 @@ TileArgs tile_args(phx_handle* h, int inj) {
   return ta;
 }
 
+// The device error word copied to the host with the results (slot 8 of
+// red_host, already synchronised): clears it on the device when it is set.
+phx_status took_device_error(phx_handle* h) {
+  int e = 0;
+  std::memcpy(&e, h->red_host + 8, sizeof e);
+  if (e) {
+    PHX_CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
+    return fail(h, PHX_ETIMEOUT, "a bounded wait in the step kernel gave up (TMA copy did not complete)");
+  }
+  return PHX_OK;
+}
+
 // Reads and clears the device error word (synchronises the stream).
 phx_status check_device_error(phx_handle* h) {
   int e = 0;
@@ -469,7 +481,8 @@ phx_status create_impl(const phx_params* p, void* const* ext, phx_handle** out) 
   if (ce == cudaSuccess)
     ce = alloc((void**)&h->partials, reduce_partials_len(g) * sizeof(double));
   if (ce == cudaSuccess) ce = alloc((void**)&h->red_dev, 8 * sizeof(double));
-  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&h->red_host, 8 * sizeof(double));
+  // 8 results + one slot that receives the device error word in the same round trip
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&h->red_host, 9 * sizeof(double));
   if (ce == cudaSuccess) ce = alloc((void**)&h->err_dev, sizeof(int));
   if (ce == cudaSuccess) ce = alloc((void**)&h->d_inst, sizeof(TileInst));
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
@@ -770,9 +783,11 @@ phx_status phx_norm_energy(phx_handle* h, double* norm, double* energy) {
   PHX_CK(h, launch_norm_energy(r, h->partials, h->red_dev, h->stream));
   PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 2 * sizeof(double),
                             cudaMemcpyDeviceToHost, h->stream));
+  PHX_CK(h, cudaMemcpyAsync(h->red_host + 8, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost,
+                            h->stream));
   PHX_CK(h, cudaStreamSynchronize(h->stream));
   {
-    phx_status es = check_device_error(h);
+    phx_status es = took_device_error(h);
     if (es != PHX_OK) return es;
   }
   const double dV = (h->p.lx / h->p.nx) * (h->p.ly / h->p.ny);
@@ -790,9 +805,11 @@ phx_status phx_residual(phx_handle* h, double* r_psi, double* r_n, double* omega
   PHX_CK(h, launch_residual(r, h->partials, h->red_dev, h->stream));
   PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 8 * sizeof(double),
                             cudaMemcpyDeviceToHost, h->stream));
+  PHX_CK(h, cudaMemcpyAsync(h->red_host + 8, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost,
+                            h->stream));
   PHX_CK(h, cudaStreamSynchronize(h->stream));
   {
-    phx_status es = check_device_error(h);
+    phx_status es = took_device_error(h);
     if (es != PHX_OK) return es;
   }
   const double* o = h->red_host;
