@@ -273,27 +273,78 @@ def energy(clk, seconds, updates):
             "power_w_median": clk["power_w_median"], "source": "nvidia-smi power.draw"}
 
 
-def cpu_baseline(name, cfg, budget_s=15.0):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the workload."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+def _oracle_steps(path, warmup, nsteps, per, budget_s):
+    """One worker process: the FP64 oracle as it stands (numpy, one thread)
+    on its own copy of the workload: `warmup` untimed steps, then either
+    nsteps x per steps or, with nsteps None, steps until budget_s (at most
+    50).  Returns (timed steps, seconds)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import pickle
     from oracle import gp
+    with open(path, "rb") as f:
+        cfg = pickle.load(f)
     p = gp.Params(**cfg["params"])
     psi, n = np.array(cfg["psi0"], complex), cfg["n0"]
     P = None if cfg["P"] is None else np.broadcast_to(cfg["P"], (p.ncomp, p.ny, p.nx))
     V, E = cfg.get("V"), cfg.get("E")
+    for _ in range(warmup):
+        gp.run(psi, n, P, V, p, 1, E=E)
     t0 = time.perf_counter()
     steps = 0
     while True:
-        psi, n = gp.run(psi, n, P, V, p, 1, step0=steps, E=E, t0=steps * p.dt)
-        steps += 1
-        if time.perf_counter() - t0 > budget_s or steps >= 50:
+        k = per if nsteps is not None else 1
+        psi, n = gp.run(psi, n, P, V, p, k, step0=steps, E=E, t0=steps * p.dt)
+        steps += k
+        if nsteps is not None:
+            if steps >= nsteps * per:
+                break
+        elif time.perf_counter() - t0 > budget_s or steps >= 50:
             break
-    dt = time.perf_counter() - t0
-    sites = p.nx * p.ny
-    return {"value": sites * steps / dt, "unit": "site-updates/s", "cores": 1,
-            "kind": "oracle",
-            "sample": "%d RK4 steps of the %dx%d %s workload (numpy FP64, 1 thread), %.1f s"
-                      % (steps, p.nx, p.ny, name, dt)}
+    return steps, time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_on_cores(cfg, warmup=0, nsteps=None, per=1, budget_s=15.0, cores=None):
+    """The oracle timed on every host core at once: one process per core
+    (spawned, so no GPU context is inherited), each running its own copy of
+    the workload.  Returns (site-updates/s of all processes together, the
+    processes used, per-process site-updates/s)."""
+    import multiprocessing as mp
+    import pickle
+    import tempfile
+    cores = cores or host_cores()
+    fd, path = tempfile.mkstemp(suffix=".pkl")
+    with os.fdopen(fd, "wb") as f:
+        pickle.dump(cfg, f, protocol=pickle.HIGHEST_PROTOCOL)
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            res = pool.starmap(_oracle_steps, [(path, warmup, nsteps, per, budget_s)] * cores)
+    finally:
+        os.unlink(path)
+    sites = cfg["params"]["nx"] * cfg["params"]["ny"]
+    total = sites * sum(s for s, _ in res) / max(e for _, e in res)
+    per_proc = [sites * s / e for s, e in res]
+    return total, cores, per_proc, res
+
+
+def cpu_baseline(name, cfg, budget_s=15.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the
+    workload, on all host cores (one process per core)."""
+    total, cores, per_proc, res = oracle_on_cores(cfg, budget_s=budget_s)
+    p = cfg["params"]
+    return {"value": total, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+            "per_core_value": float(np.median(per_proc)),
+            "sample": "%d processes x %d-%d RK4 steps of the %dx%d %s workload (numpy FP64, one "
+                      "thread each, all at once), %.1f s" % (
+                          cores, min(s for s, _ in res), max(s for s, _ in res), p["nx"], p["ny"],
+                          name, max(e for _, e in res))}
 
 
 def _rel_l2(a, b):
@@ -363,30 +414,24 @@ def run_reference(args, world, rank):
         desc = "512x512 corner window of the driven 9000x9000 lattice"
     else:
         cfg, kind, desc = workload(args.workload, grid=args.grid)
-    from oracle import gp
-    p = gp.Params(**cfg["params"])
-    psi, n = np.array(cfg["psi0"], complex), cfg["n0"]
-    P = None if cfg["P"] is None else np.broadcast_to(cfg["P"], (p.ncomp, p.ny, p.nx))
-    per = 1 if p.nx * p.ny >= 1 << 20 else 20
-    V, E = cfg.get("V"), cfg.get("E")
-    for w in range(args.warmup):
-        gp.run(psi, n, P, V, p, 1, E=E)
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        psi, n = gp.run(psi, n, P, V, p, per, step0=k * per, E=E, t0=k * per * p.dt)
-    el = time.perf_counter() - t0
-    val = p.nx * p.ny * per * args.steps / el
+    d = cfg["params"]
+    per = 1 if d["nx"] * d["ny"] >= 1 << 20 else 20
+    # every host core runs its own copy (one process each), all at once
+    val, cores, per_proc, res = oracle_on_cores(cfg, warmup=args.warmup, nsteps=args.steps,
+                                                per=per)
+    el = max(e for _, e in res)
     line = {"metric": "RK4 site-updates/s", "impl": "reference", "value": val,
             "unit": "site-updates/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc,
-                       "grid": "%dx%d" % (p.nx, p.ny), "sample_rk4_steps_per_step": per},
-            "cpu_baseline": {"value": val, "unit": "site-updates/s", "cores": 1,
-                             "kind": "oracle",
-                             "sample": "%d RK4 steps per bench step of the %s workload"
-                                       % (per, args.workload)},
+                       "grid": "%dx%d" % (d["nx"], d["ny"]), "sample_rk4_steps_per_step": per},
+            "cpu_baseline": {"value": val, "unit": "site-updates/s", "cores": cores,
+                             "kind": "oracle", "per_core_value": float(np.median(per_proc)),
+                             "sample": "%d processes, each %d RK4 steps per bench step of the "
+                                       "%s workload (numpy FP64, one thread each)"
+                                       % (cores, per, args.workload)},
             "e2e": {"value": val, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
