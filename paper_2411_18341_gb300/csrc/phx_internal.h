@@ -122,8 +122,7 @@ cudaError_t launch_fill_ghosts(void* base, int esize, int nplanes,
                                const Geometry& g, cudaStream_t s);
 
 // Reductions in FP64.  `partials` is device scratch of reduce_partials_len()
-// doubles, zeroed once when allocated (its last slots hold the arrival counter
-// the reductions leave at zero); `out` receives the final sums on the device.
+// doubles; `out` receives the final sums on the device.
 int reduce_blocks(const Geometry& g);
 size_t reduce_partials_len(const Geometry& g);
 

@@ -10,7 +10,8 @@ constexpr int RED_THREADS = 256;
 constexpr int RED_MAX_BLOCKS = 1216;  // 152 SMs x 8
 constexpr int RED_Q = 8;              // quantities per partial record
 // After the records: an arrival counter (read as unsigned) that the last CTA
-// of a reduction resets to zero; the buffer is zeroed once when allocated.
+// of a reduction resets to zero, and the residual's -hbar omega as a
+// double-float; callers zero the whole buffer once when they allocate it.
 constexpr int RED_COUNTER = RED_MAX_BLOCKS * RED_Q;
 
 // CTAs of the double-float kernels: about 16 sites per thread (their
