@@ -1,7 +1,7 @@
 // k-space smoothing of psi (Sec. III.B): a forward FFT of each component,
 // the product with a low-pass mask, and the inverse FFT back into the padded
 // state, whose ghost ring is then refilled.  The paper leaves the mask's
-// shape open; this build uses the super-Gaussian
+// shape open; this library uses the super-Gaussian
 //   M(k) = exp(-((k_x^2 + k_y^2) / k_c^2)^p),  k = 2 pi m / L (FFT order),
 // with the 1/(nx ny) normalisation of the inverse transform folded in.
 //
