@@ -354,20 +354,29 @@ def _rel_l2(a, b):
     return float(torch.linalg.vector_norm(a - b)) / den if den > 0 else None
 
 
-def fp64_run(phx, d, cfg, nsteps, stream, dev, step_fn_name="phx_step_n"):
-    """The same workload run by the FP64 path (parity-pinned to the oracle at
-    1e-11) from the workload's FP64 inputs: the yardstick of the FP32 error."""
+def fresh_run(phx, d, cfg, nsteps, stream, dev, step_fn_name="phx_step_n", prec=64):
+    """The workload run from step 0 and time 0 on a new handle in `prec`
+    (inputs rounded to it): with prec 64 the FP64 path, pinned to the oracle
+    at 1e-11, the yardstick of the FP32 error; with prec 32 the FP32 result
+    it is compared with (same noise counters and drive phases)."""
     import torch
-    h = phx.phx_create(phx.params_from_dict(d, precision=64, stream=stream.cuda_stream))
-    f64, c128 = torch.float64, torch.complex128
-    if cfg.get("P") is not None:
-        phx.phx_set_pump(h, torch.tensor(np.asarray(cfg["P"])[0], dtype=f64, device=dev))
-    if cfg.get("V") is not None:
-        phx.phx_set_potential(h, torch.tensor(np.asarray(cfg["V"]), dtype=f64, device=dev))
-    if cfg.get("E") is not None:
-        phx.phx_set_drive(h, torch.tensor(np.asarray(cfg["E"])[0], dtype=c128, device=dev))
-    psi0 = torch.tensor(np.ascontiguousarray(cfg["psi0"]), dtype=c128, device=dev)
-    n0 = None if cfg.get("n0") is None else torch.tensor(cfg["n0"], dtype=f64, device=dev)
+    h = phx.phx_create(phx.params_from_dict(d, precision=prec, stream=stream.cuda_stream))
+    f64, c128 = (torch.float64, torch.complex128) if prec == 64 else (torch.float32,
+                                                                      torch.complex64)
+    dt = lambda a, t: None if a is None else torch.tensor(np.asarray(a), dtype=t, device=dev)  # noqa: E731
+    P = None if cfg.get("P") is None else dt(np.asarray(cfg["P"])[0], f64)
+    V = dt(cfg.get("V"), f64)
+    E = None if cfg.get("E") is None else dt(np.asarray(cfg["E"])[0], c128)
+    psi0 = dt(np.ascontiguousarray(cfg["psi0"]), c128)
+    n0 = dt(cfg.get("n0"), f64)
+    # the copies above run on torch's stream; the handle reads them on its own
+    torch.cuda.synchronize()
+    if P is not None:
+        phx.phx_set_pump(h, P)
+    if V is not None:
+        phx.phx_set_potential(h, V)
+    if E is not None:
+        phx.phx_set_drive(h, E)
     phx.phx_set_state(h, psi0, n0)
     getattr(phx, step_fn_name)(h, nsteps)
     psi = torch.empty_like(psi0)
@@ -376,6 +385,10 @@ def fp64_run(phx, d, cfg, nsteps, stream, dev, step_fn_name="phx_step_n"):
     torch.cuda.synchronize()
     phx.phx_destroy(h)
     return psi, n
+
+
+def fp64_run(phx, d, cfg, nsteps, stream, dev, step_fn_name="phx_step_n"):
+    return fresh_run(phx, d, cfg, nsteps, stream, dev, step_fn_name, 64)
 
 
 def precision_error(psi32, n32, psi64, n64, what):
@@ -474,10 +487,14 @@ def run_ensemble(args, world, rank, local, pg):
     b = phx.phx_batch_create([phx.params_from_dict(m["params"], precision=32,
                                                    stream=stream.cuda_stream) for m in members])
     psi_d, n_d = [], []
+    P_d = [torch.tensor(m["P"][0], dtype=torch.float32, device=dev) for m in members]
+    # the copies run on torch's stream; the batch reads them on its own
+    torch.cuda.synchronize()
     for i, m in enumerate(members):
-        phx.phx_batch_set_pump(b, i, torch.tensor(m["P"][0], dtype=torch.float32, device=dev))
+        phx.phx_batch_set_pump(b, i, P_d[i])
         psi_d.append(torch.tensor(m["psi0"][0], dtype=torch.complex64, device=dev))
         n_d.append(torch.tensor(m["n0"][0], dtype=torch.float32, device=dev))
+    del P_d
     sites = sum(m["params"]["nx"] * m["params"]["ny"] for m in members)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -558,12 +575,14 @@ def run_ensemble(args, world, rank, local, pg):
     prec_err = []
     for i in picks:
         m = members[i]
-        psi64, n64 = fp64_run(phx, m["params"], m, rk4_steps, stream, dev)
-        e = precision_error(out_psi[i][None], out_n[i][None], psi64, n64,
-                            "member %d (%dx%d) after %d steps" % (
-                                i, m["params"]["nx"], m["params"]["ny"], rk4_steps))
+        psi32, n32 = fresh_run(phx, m["params"], m, rk4_steps, stream, dev, prec=32)
+        psi64, n64 = fresh_run(phx, m["params"], m, rk4_steps, stream, dev, prec=64)
+        e = precision_error(psi32, n32, psi64, n64,
+                            "member %d (%dx%d) run on its own handle, %d steps from step 0, "
+                            "both precisions" % (i, m["params"]["nx"], m["params"]["ny"],
+                                                 rk4_steps))
         prec_err.append(e)
-        del psi64, n64
+        del psi32, n32, psi64, n64
     pk, pk_kind = peaks()
     achieved = 28 * sites / kern_s / 1e9
     if twa:
@@ -746,6 +765,41 @@ def steady_experiment(n_train=2000, n_test=200, gen_steps=40000, epochs=40, cap=
     return rep, net
 
 
+def quick_rate(phx, torch, name, steps=500, warmup=50):
+    """Site-updates/s of one workload's step kernel (CUDA events around
+    `steps` steps after `warmup`), for an extra key of the default line."""
+    cfg, kind, desc = workload(name)
+    d = cfg["params"]
+    stream = torch.cuda.Stream()
+    h = phx.phx_create(phx.params_from_dict(d, precision=32, stream=stream.cuda_stream))
+    real, cplx = torch.float32, torch.complex64
+    P = None if cfg.get("P") is None else torch.tensor(np.asarray(cfg["P"])[0], dtype=real,
+                                                           device="cuda")
+    psi0 = torch.tensor(np.ascontiguousarray(cfg["psi0"]), dtype=cplx, device="cuda")
+    n0 = None if cfg.get("n0") is None else torch.tensor(cfg["n0"], dtype=real, device="cuda")
+    torch.cuda.synchronize()  # the handle reads the copies on its own stream
+    if P is not None:
+        phx.phx_set_pump(h, P)
+    phx.phx_set_state(h, psi0, n0)
+    phx.phx_step_n(h, warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    phx.phx_step_n(h, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    sites = d["nx"] * d["ny"]
+    pk, _ = peaks()
+    bps = BYTES_PER_SITE[(32, kind)]
+    out = {"workload": name, "description": desc, "site_updates_per_s": sites / (us * 1e-6),
+           "us_per_step": us, "tile": phx.phx_tile(h),
+           "roofline_frac": bps * sites / (us * 1e-6) / 1e9 / pk["hbm_gbs"],
+           "algorithmic_bytes_per_site": bps, "steps_timed": steps}
+    phx.phx_destroy(h)
+    return out
+
+
 def steady_key(rep):
     """The warm-vs-cold summary carried in a bench line."""
     s = rep.get("summary") or {}
@@ -907,10 +961,12 @@ def main():
     psi0_d = torch.tensor(np.ascontiguousarray(cfg["psi0"]), dtype=cplx, device=dev)
     n0_d = None if cfg["n0"] is None else torch.tensor(cfg["n0"], dtype=real, device=dev)
     P_d = None if cfg["P"] is None else torch.tensor(cfg["P"][0], dtype=real, device=dev)
-    if P_d is not None:
-        phx.phx_set_pump(h, P_d)
     V_d = None if cfg.get("V") is None else torch.tensor(cfg["V"], dtype=real, device=dev)
     E_d = None if cfg.get("E") is None else torch.tensor(cfg["E"][0], dtype=cplx, device=dev)
+    # the copies above run on torch's stream; the handle reads them on its own
+    torch.cuda.synchronize()
+    if P_d is not None:
+        phx.phx_set_pump(h, P_d)
     if V_d is not None:
         phx.phx_set_potential(h, V_d)
     if E_d is not None:
@@ -986,11 +1042,13 @@ def main():
     if prec == 32 and args.no_precision_error:
         prec_err = None
     elif prec == 32:
-        psi64, n64 = fp64_run(phx, d, cfg, rk4_steps, stream, dev,
-                              "phx_step_ssf" if args.integrator == "ssf" else "phx_step_n")
-        prec_err = precision_error(out_psi, out_n, psi64, n64,
-                                   "final state after the bench step's %d steps" % rk4_steps)
-        del psi64, n64
+        fn = "phx_step_ssf" if args.integrator == "ssf" else "phx_step_n"
+        psi32, n32 = fresh_run(phx, d, cfg, rk4_steps, stream, dev, fn, 32)
+        psi64, n64 = fresh_run(phx, d, cfg, rk4_steps, stream, dev, fn, 64)
+        prec_err = precision_error(psi32, n32, psi64, n64,
+                                   "final state after %d steps from step 0, both precisions"
+                                   % rk4_steps)
+        del psi32, n32, psi64, n64
     else:
         prec_err = {"note": "FP64 run: the FP64 path is the yardstick of the FP32 error"}
     esz = 4 if prec == 32 else 8
@@ -1065,6 +1123,9 @@ def main():
         "energy": energy(clk, ms * 1e-3, sites * rk4_steps),
         "precision_error": prec_err,
     }
+    if rank == 0 and world == 1 and args.workload == "reservoir_2048":
+        # the two-component TE-TM workload's step (noise every step), timed briefly
+        line["spinor_2048"] = quick_rate(phx, torch, "spinor_2048")
     if rank == 0 and world == 1 and not args.no_steady and args.workload == "reservoir_2048":
         # reduced warm-vs-cold time to steady state (the metric's second part)
         rep, _ = steady_experiment(n_train=1024, n_test=128, gen_steps=30000, epochs=12,

@@ -40,7 +40,10 @@
  *     precision 32 and double for precision 64.
  *   - `on_device` = 1: the pointer is CUDA device memory of the handle's
  *     device; 0: host memory (pinned or pageable).  Inputs are copied;
- *     the caller keeps ownership of every pointer it passes.
+ *     the caller keeps ownership of every pointer it passes.  A device
+ *     input is read by work queued on params.stream: whatever writes it on
+ *     another stream must be complete (or ordered before that stream) when
+ *     the call is made.
  *   - Work is queued on params.stream (a cudaStream_t; NULL = legacy default
  *     stream).  Calls that return values to the host synchronise that stream.
  *   - A handle is not thread-safe; distinct handles are independent.

@@ -79,27 +79,31 @@ def test_reservoir_1024_invariants_and_time():
     assert step == 2000 and t == acc
 
 
-def test_driven_9000_sampled_step():
-    """The coherently driven 9000^2 lattice (the TMA-fed drive mode) at full
-    size: one step after 20, sampled against the oracle's windowed step with
-    the same drive amplitude and the FP64 time of the device clock."""
+@pytest.mark.parametrize("prec", [32, 64])
+def test_driven_9000_sampled_step(prec):
+    """The coherently driven 9000^2 lattice at full size (FP32: the TMA-fed
+    drive mode; FP64: the generic kernel): one step after 20, sampled against
+    the oracle's windowed step with the same drive amplitude and the FP64
+    time of the device clock."""
     m = phx()
     cfg = synth.driven_lattice(9000)
     d = cfg["params"]
-    h = make_handle(d, 32, cfg["psi0"], None, None, cfg["V"])
-    m.phx_set_drive(h, np.ascontiguousarray(cfg["E"][0], np.complex64))
+    h = make_handle(d, prec, cfg["psi0"], None, None, cfg["V"])
+    m.phx_set_drive(h, np.ascontiguousarray(cfg["E"][0],
+                                            np.complex64 if prec == 32 else np.complex128))
     m.phx_step_n(h, 20)
-    psi_s, _ = get_state(h, 32)
+    psi_s, _ = get_state(h, prec)
     step, t = m.phx_time(h)
     m.phx_step_n(h, 1)
-    psi_1, _ = get_state(h, 32)
-    assert m.phx_tile(h) in TMA_SCALAR_TILES
+    psi_1, _ = get_state(h, prec)
+    if prec == 32:
+        assert m.phx_tile(h) in TMA_SCALAR_TILES
     sites = sample_sites(9000, 9000, np.random.default_rng(4))
     sp, _ = gp.step_at_sites(psi_s.astype(np.complex128), None, None, cfg["V"], gp.Params(**d),
                              sites, step, E=cfg["E"], t=t)
     jj = np.array([s[0] for s in sites])
     ii = np.array([s[1] for s in sites])
-    assert rel_l2(psi_1[0, jj, ii], sp[0]) <= TOL[32], rel_l2(psi_1[0, jj, ii], sp[0])
+    assert rel_l2(psi_1[0, jj, ii], sp[0]) <= TOL[prec], rel_l2(psi_1[0, jj, ii], sp[0])
 
 
 def test_twa_ensemble_member_matches_oracle():
