@@ -55,7 +55,7 @@ struct phx_handle {
   cudaStream_t stream = nullptr;
   int device = 0;
   int num_sms = 0;
-  int* err_dev = nullptr;      // set by kernels whose bounded waits gave up
+  int* err_dev = nullptr;      // set by kernels whose bounded waits gave up (in red_dev)
   double dt_rk4 = 0;           // RK4 stability limit of the grid (phx_stability_dt)
   int tile_cfg = 0;            // chosen tile configuration of the FP32 scalar kernel
   bool tuned = false;          // tile_cfg settled (explicit or autotuned)
@@ -63,6 +63,8 @@ struct phx_handle {
   bool maps_V = false;
   TileInst h_inst;             // descriptor of this handle for the persistent kernel
   TileInst* d_inst = nullptr;  // its device copy
+  int* ms_done = nullptr;      // per-tile step counters of a multi-step launch
+  int ms_done_len = 0;
   std::string err;
 };
 
@@ -126,8 +128,8 @@ void free_all(phx_handle* h) {
   if (h->partials) cudaFree(h->partials);
   if (h->red_dev) cudaFree(h->red_dev);
   if (h->red_host) cudaFreeHost(h->red_host);
-  if (h->err_dev) cudaFree(h->err_dev);
   if (h->d_inst) cudaFree(h->d_inst);
+  if (h->ms_done) cudaFree(h->ms_done);
   cudaSetDevice(prev);
 }
 
@@ -183,6 +185,53 @@ cudaError_t launch_tma(phx_handle* h, int cfg, const TileArgs& ta, int grid) {
   return launch_rk4_tma_f32(cfg, mode, h->has_V, periodic(h->p), ta, h->stream, grid);
 }
 
+// Steps per multi-step launch (configuration 8): long enough that the launch
+// and its ramp are negligible, short enough that a chunk is a few ms.
+constexpr int MS_CHUNK = 128;
+
+// Steps the next multi-step launch may take out of `want` (0: it does not
+// apply, one single-step launch instead).  Needs the tensor maps encoded.
+int ms_steps_possible(const phx_handle* h, int64_t want) {
+  if (!tma_has_multistep(h->tile_cfg) || h->m.precision != 32 || h->m.ncomp != 1 || h->has_E)
+    return 0;
+  const int tx = h->h_inst.tiles_x, nt = tx * h->h_inst.tiles_y;
+  const int G = h->num_sms * tma_ctas_per_sm(h->tile_cfg);
+  // an item must never wait for this CTA's previous item, whose counter is
+  // published only after the next item started (see the kernel)
+  if (G >= nt - 4 * tx && G <= nt + 4 * tx) return 0;
+  int64_t S = want < MS_CHUNK ? want : MS_CHUNK;
+  if (h->kf.every > 0) {  // end the chunk where the k-space filter applies
+    const int64_t to = h->kf.every - h->host_step % h->kf.every;
+    if (S > to) S = to;
+  }
+  return S >= 2 ? (int)S : 0;
+}
+
+// One multi-step launch of S steps on the handle's buffers (the state ends in
+// buffer cur ^ (S & 1)); with the clock advanced unless `clock` is false.
+cudaError_t launch_ms(phx_handle* h, int S, int inj, bool clock) {
+  const int tx = h->h_inst.tiles_x, ty = h->h_inst.tiles_y, nt = tx * ty;
+  if (h->ms_done_len < nt) {
+    if (h->ms_done) cudaFree(h->ms_done);
+    h->ms_done = nullptr;
+    h->ms_done_len = 0;
+    cudaError_t e = cudaMalloc((void**)&h->ms_done, sizeof(int) * nt);
+    if (e != cudaSuccess) return e;
+    h->ms_done_len = nt;
+  }
+  cudaError_t e = cudaMemsetAsync(h->ms_done, 0, sizeof(int) * nt, h->stream);
+  if (e != cudaSuccess) return e;
+  TileArgs ta = tile_args(h, inj);
+  ta.done = h->ms_done;
+  ta.ms_steps = S;
+  ta.tiles_y = ty;
+  const int grid = h->num_sms * tma_ctas_per_sm(h->tile_cfg);
+  e = launch_rk4_tma_f32_ms(h->tile_cfg, h->m.reservoir ? 1 : 0, h->has_V, periodic(h->p), ta,
+                            h->stream, grid);
+  if (e != cudaSuccess || !clock) return e;
+  return launch_clock_advance(h->clock, h->parity, S, h->p.dt, h->stream);
+}
+
 // Time every tile configuration of the FP32 scalar kernel on this handle's
 // own state and keep the fastest.  A step reads the current buffer and writes
 // the other one, so repeating it without swapping leaves the state intact.
@@ -200,17 +249,37 @@ phx_status autotune(phx_handle* h) {
       return PHX_OK;
     }
   }
-  const int scalar_cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64,
-                              TILE_64x32, TILE_64x32_M2_2, TILE_64x32_M4_2};
+  const int scalar_cands[] = {TILE_64x48_M2, TILE_64x64_M2,   TILE_64x48,
+                              TILE_64x64,    TILE_64x32,      TILE_64x32_M2_2,
+                              TILE_64x32_M4_2, TILE_64x32_M4_2_MS};
   const int spinor_cands[] = {TILE_SPINOR_64x24, TILE_SPINOR_64x16, TILE_SPINOR_64x32};
   const bool sp = h->m.ncomp == 2;
   const int* cands = sp ? spinor_cands : scalar_cands;
   cudaEvent_t e0, e1;
   PHX_CK(h, cudaEventCreate(&e0));
   PHX_CK(h, cudaEventCreate(&e1));
+  // The multi-step configuration advances the state: it runs on the
+  // handle's buffers after the current state is saved, which is copied back
+  // afterwards (the clock is not advanced while tuning).
+  const size_t psi_bytes = (size_t)h->geo.plane * h->m.ncomp * 2 * h->esize;
+  const size_t n_bytes = h->m.reservoir ? (size_t)h->geo.plane * h->m.ncomp * h->esize : 0;
+  void* saved = nullptr;
+  const bool try_ms = !sp && !h->has_E;
+  if (try_ms && cudaMalloc(&saved, psi_bytes + n_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    saved = nullptr;
+  }
+  if (saved) {
+    PHX_CK(h, cudaMemcpyAsync(saved, h->psi[h->cur], psi_bytes, cudaMemcpyDeviceToDevice,
+                              h->stream));
+    if (n_bytes)
+      PHX_CK(h, cudaMemcpyAsync(static_cast<char*>(saved) + psi_bytes, h->n[h->cur], n_bytes,
+                                cudaMemcpyDeviceToDevice, h->stream));
+  }
   // three interleaved rounds; each configuration keeps its fastest round
-  const int nc = sp ? 3 : 7;
-  float cfg_ms[7];
+  // (time per step)
+  const int nc = sp ? 3 : (saved ? 8 : 7);
+  float cfg_ms[8];
   for (int c = 0; c < nc; ++c) cfg_ms[c] = 1e30f;
   for (int round = 0; round < 3; ++round) {
     for (int c = 0; c < nc; ++c) {
@@ -221,11 +290,17 @@ phx_status autotune(phx_handle* h) {
       const TileArgs ta = tile_args(h, 0);
       const int slots = h->num_sms * tma_ctas_per_sm(cfg);
       const int grid = ta.ntiles < slots ? ta.ntiles : slots;
-      auto launch = [&]() { return launch_tma(h, cfg, ta, grid); };
+      const int ms_n = tma_has_multistep(cfg) ? ms_steps_possible(h, 8) : 0;
+      if (tma_has_multistep(cfg) && ms_n < 2) continue;
+      auto launch = [&]() {
+        return ms_n ? launch_ms(h, ms_n, 0, false) : launch_tma(h, cfg, ta, grid);
+      };
+      const int reps = ms_n ? 2 : 5;
+      const int per_rep = ms_n ? ms_n : 1;
       cudaError_t e = cudaSuccess;
       for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch();
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-      for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = launch();
+      for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch();
       if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -234,8 +309,18 @@ phx_status autotune(phx_handle* h) {
         cudaGetLastError();
         continue;
       }
+      ms /= (float)(reps * per_rep);
       if (ms < cfg_ms[c]) cfg_ms[c] = ms;
     }
+  }
+  if (saved) {
+    PHX_CK(h, cudaMemcpyAsync(h->psi[h->cur], saved, psi_bytes, cudaMemcpyDeviceToDevice,
+                              h->stream));
+    if (n_bytes)
+      PHX_CK(h, cudaMemcpyAsync(h->n[h->cur], static_cast<char*>(saved) + psi_bytes, n_bytes,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    PHX_CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(saved);
   }
   float best_ms = 1e30f;
   int best = cands[0];
@@ -283,6 +368,7 @@ TileArgs tile_args(phx_handle* h, int inj) {
   ta.t_inst = nullptr;
   ta.err = h->err_dev;
   ta.inject_timeout = inj;
+  ta.tiles_y = h->h_inst.tiles_y;
   return ta;
 }
 
@@ -480,10 +566,11 @@ phx_status create_impl(const phx_params* p, void* const* ext, phx_handle** out) 
   if (ce == cudaSuccess) ce = alloc((void**)&h->clock, sizeof(DevClock));
   if (ce == cudaSuccess)
     ce = alloc((void**)&h->partials, reduce_partials_len(g) * sizeof(double));
-  if (ce == cudaSuccess) ce = alloc((void**)&h->red_dev, 8 * sizeof(double));
-  // 8 results + one slot that receives the device error word in the same round trip
+  // 8 results and, in slot 8, the device error word, so that one copy
+  // brings both back
+  if (ce == cudaSuccess) ce = alloc((void**)&h->red_dev, 9 * sizeof(double));
+  if (ce == cudaSuccess) h->err_dev = reinterpret_cast<int*>(h->red_dev + 8);
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&h->red_host, 9 * sizeof(double));
-  if (ce == cudaSuccess) ce = alloc((void**)&h->err_dev, sizeof(int));
   if (ce == cudaSuccess) ce = alloc((void**)&h->d_inst, sizeof(TileInst));
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
   if (ce != cudaSuccess) {
@@ -623,6 +710,7 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
   const NoiseKey nz = make_noise_key(h->p);
   for (int64_t s = 0; s < nsteps; ++s) {
     cudaError_t e;
+    int taken = 1;  // steps of this launch
     if (take_injection(INJ_LAUNCH))
       return fail(h, PHX_ECUDA, "rk4 step launch: injected launch failure");
     const int inj = take_injection(INJ_TIMEOUT) ? 1 : 0;
@@ -659,10 +747,16 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
         if (!h->maps_ok || h->maps_V != h->has_V) {
           if (!encode_maps(h)) return fail(h, PHX_ECUDA, "cuTensorMapEncodeTiled failed");
         }
-        const TileArgs ta = tile_args(h, inj);
-        const int slots = h->num_sms * tma_ctas_per_sm(h->tile_cfg);
-        const int grid = ta.ntiles < slots ? ta.ntiles : slots;
-        e = launch_tma(h, h->tile_cfg, ta, grid);
+        const int ms_n = ms_steps_possible(h, nsteps - s);
+        if (ms_n) {
+          taken = ms_n;
+          e = launch_ms(h, ms_n, inj, true);
+        } else {
+          const TileArgs ta = tile_args(h, inj);
+          const int slots = h->num_sms * tma_ctas_per_sm(h->tile_cfg);
+          const int grid = ta.ntiles < slots ? ta.ntiles : slots;
+          e = launch_tma(h, h->tile_cfg, ta, grid);
+        }
       } else {
         e = launch_rk4_step_f32(h->m, a, h->stream, h->p.tile);
       }
@@ -688,9 +782,10 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       e = launch_rk4_step_f64(h->m, a, h->stream, h->p.tile);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "rk4 step launch");
-    h->cur ^= 1;
+    h->cur ^= taken & 1;
     h->parity ^= 1;
-    h->host_step += 1;
+    h->host_step += taken;
+    s += taken - 1;
     if (h->kf.every > 0 && h->host_step % h->kf.every == 0) {
       const char* msg = kfilter_apply(h->kf, h->psi[h->cur], h->geo, h->m.ncomp,
                                       h->m.precision, h->p.lx, h->p.ly, h->stream);
@@ -781,10 +876,8 @@ phx_status phx_norm_energy(phx_handle* h, double* norm, double* energy) {
   DeviceGuard dg(h->device);
   ReduceArgs r = make_reduce_args(h);
   PHX_CK(h, launch_norm_energy(r, h->partials, h->red_dev, h->stream));
-  PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 2 * sizeof(double),
+  PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 9 * sizeof(double),
                             cudaMemcpyDeviceToHost, h->stream));
-  PHX_CK(h, cudaMemcpyAsync(h->red_host + 8, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost,
-                            h->stream));
   PHX_CK(h, cudaStreamSynchronize(h->stream));
   {
     phx_status es = took_device_error(h);
@@ -803,10 +896,8 @@ phx_status phx_residual(phx_handle* h, double* r_psi, double* r_n, double* omega
   DeviceGuard dg(h->device);
   ReduceArgs r = make_reduce_args(h);
   PHX_CK(h, launch_residual(r, h->partials, h->red_dev, h->stream));
-  PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 8 * sizeof(double),
+  PHX_CK(h, cudaMemcpyAsync(h->red_host, h->red_dev, 9 * sizeof(double),
                             cudaMemcpyDeviceToHost, h->stream));
-  PHX_CK(h, cudaMemcpyAsync(h->red_host + 8, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost,
-                            h->stream));
   PHX_CK(h, cudaStreamSynchronize(h->stream));
   {
     phx_status es = took_device_error(h);

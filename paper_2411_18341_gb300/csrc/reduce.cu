@@ -2,6 +2,8 @@
 // Each CTA reduces its grid-stride share with warp shuffles and writes one
 // FP64 partial per quantity; a single-CTA pass then sums the partials in a
 // fixed order, so results are deterministic for a given grid.
+#include <algorithm>
+
 #include "phx_internal.h"
 
 namespace phx {
@@ -14,11 +16,19 @@ constexpr int RED_Q = 8;              // quantities per partial record
 // double-float; callers zero the whole buffer once when they allocate it.
 constexpr int RED_COUNTER = RED_MAX_BLOCKS * RED_Q;
 
-// CTAs of the double-float kernels: about 16 sites per thread (their
-// epilogue sums warps in double-float and leaves FP64 to one lane per warp).
+// CTAs of the double-float kernels: their warps take items of 32 x DF_SEG
+// columns of one row, about DF_ITEMS items per warp (32 sites per thread),
+// so that the double-float warp and CTA sums (about 660 warp instructions
+// per warp for six quantities) stay a small part of the work; but at least
+// DF_MIN_BLOCKS CTAs (two per SM) while there is an item per warp.
+constexpr int DF_SEG = 8;
+constexpr int DF_ITEMS = 4;
+constexpr int DF_MIN_BLOCKS = 304;
 int df_reduce_blocks(const Geometry& g) {
-  const long long sites = (long long)g.nx * g.ny;
-  long long b = (sites + RED_THREADS * 16 - 1) / (RED_THREADS * 16);
+  const long long nseg = (g.nx + 32 * DF_SEG - 1) / (32 * DF_SEG);
+  const long long items = nseg * g.ny, wpb = RED_THREADS / 32;
+  long long b = (items + wpb * DF_ITEMS - 1) / (wpb * DF_ITEMS);
+  if (b < DF_MIN_BLOCKS) b = std::min<long long>(DF_MIN_BLOCKS, (items + wpb - 1) / wpb);
   if (b > RED_MAX_BLOCKS) b = RED_MAX_BLOCKS;
   if (b < 1) b = 1;
   return (int)b;
@@ -257,16 +267,30 @@ residual_kernel(SiteView<R> v, PhysArgs a, int nx, int ny, int mode,
 //
 // A double-float (hi, lo) is an unevaluated sum of two FP32 numbers carrying
 // about 44-48 significant bits.  The error-free transformations are the
-// classical ones (Knuth's and Dekker's two-sum, the fused-multiply-add
-// two-product), written with explicitly rounded FP32 operations so that the
-// compiler neither contracts nor reorders them.  The FP32 inputs convert
-// exactly, the stencil's second differences E + W - 2C are formed without
-// rounding error in the leading part, and the grid's coefficients (kappa/dx^2,
-// g, 1/hbar, ...) are applied once per thread in FP64 to the double-float
-// sums, or, where a per-site value is needed (the residual's second pass), as
-// double-float constants split from their FP64 values.  The FP64 pipe, about
-// 64x slower than the FP32 pipe on this GPU, then only accumulates per-thread
-// and per-CTA partials.
+// classical ones (Knuth's two-sum, Dekker's fast two-sum, the
+// fused-multiply-add two-product), written with explicitly rounded FP32
+// operations so that the compiler neither contracts nor reorders them.  The
+// FP32 inputs convert exactly; products of two FP32 values and differences of
+// neighbours are formed without rounding error in their leading part.
+//
+// Per thread, each quantity is summed by the cascaded scheme of Ogita, Rump
+// and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005,
+// Sum2): the running FP32 sum takes every term through a two-sum and the
+// rounding errors collect in a second FP32 word, which keeps the result as
+// accurate as a sum in twice the working precision.  Warps, CTAs and the
+// final pass over the CTA records add double-floats in a fixed order; the FP64
+// pipe (about 1/64 of the FP32 pipe on this GPU) is used by one thread of the
+// last CTA only, to apply the grid's coefficients to the totals.
+//
+// Kinetic term.  For ghost cells that hold periodic images or zeros, the
+// discrete Green identity
+//   sum_sites Re(conj(psi) (E + W - 2C)) = - sum_bonds |psi_b - psi_a|^2
+// (bonds: every pair of x neighbours, including the pair between a zero
+// ghost and the first site of a zero-BC axis) gives the kinetic energy as a
+// sum of non-negative squares of neighbour differences, and
+// sum_sites Im(conj(psi) Lap psi) = 0.  Both are identities of the sums, so
+// the norm/energy and the residual's first pass read each site's east and
+// north neighbour only.
 struct DF {
   float hi, lo;
 };
@@ -281,34 +305,58 @@ __device__ __forceinline__ DF df_norm(float a, float b) {  // |a| >= |b| or a ==
   const float s = __fadd_rn(a, b);
   return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
+// accurate sum of two double-floats (two two-sums)
 __device__ __forceinline__ DF df_add(DF x, DF y) {
   const DF s = df_two_sum(x.hi, y.hi);
   const DF t = df_two_sum(x.lo, y.lo);
   const DF u = df_norm(s.hi, __fadd_rn(s.lo, t.hi));
   return df_norm(u.hi, __fadd_rn(u.lo, t.lo));
 }
+// sum of two double-floats whose low words are added in FP32: the error is of
+// the order 2^-48 of the larger operand, which is the accuracy the residual's
+// per-site terms need (they are compared with terms of that size)
+__device__ __forceinline__ DF df_add_s(DF x, DF y) {
+  const DF s = df_two_sum(x.hi, y.hi);
+  return df_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
 __device__ __forceinline__ DF df_prod(float a, float b) {  // a * b exactly
   const float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
 }
-__device__ __forceinline__ DF df_mul(DF x, DF y) {
+// x * y, x * b and x^2 with the low word left unnormalised (every consumer
+// takes the high words through a two-sum)
+__device__ __forceinline__ DF df_mul_s(DF x, DF y) {
   const DF p = df_prod(x.hi, y.hi);
-  return df_norm(p.hi, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo)));
+  return {p.hi, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo))};
 }
-__device__ __forceinline__ DF df_mulf(DF x, float b) {
+__device__ __forceinline__ DF df_mulf_s(DF x, float b) {
   const DF p = df_prod(x.hi, b);
-  return df_norm(p.hi, __fmaf_rn(x.lo, b, p.lo));
+  return {p.hi, __fmaf_rn(x.lo, b, p.lo)};
+}
+__device__ __forceinline__ DF df_sqr_s(DF x) {
+  const DF p = df_prod(x.hi, x.hi);
+  return {p.hi, __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, p.lo)};
 }
 __device__ __forceinline__ DF df_neg(DF x) { return {-x.hi, -x.lo}; }
-__device__ __forceinline__ double df_d(DF x) { return (double)x.hi + (double)x.lo; }
 constexpr DF DF0 = {0.f, 0.f};
 
-// Double-float coefficients of the residual, split from their FP64 values on
-// the host (so that no thread spends FP64 instructions on them).
+// Running sum of one quantity (Sum2): s + c.
+struct Acc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(DF x) {
+    const DF t = df_two_sum(s, x.hi);
+    s = t.hi;
+    c = __fadd_rn(c, __fadd_rn(t.lo, x.lo));
+  }
+  __device__ __forceinline__ DF df() const { return df_two_sum(s, c); }
+};
+
+// Double-float coefficients, split from their FP64 values on the host (so
+// that no thread spends FP64 instructions on them).
 struct DfCoeffs {
   DF kx, ky;      // kappa / (hbar dx^2), kappa / (hbar dy^2)
   DF ih;          // 1 / hbar
-  DF g, g_r;      // meV um^2
+  DF gh, grh;     // g / hbar, g_r / hbar
   DF hR, hgc;     // R / 2, -gamma_c / 2
   DF gamma_r, R;
 };
@@ -326,202 +374,238 @@ __device__ __forceinline__ DF df_warp_sum(DF x) {
   return x;
 }
 
-// CTA sum of NQ FP64 values held by lane 0 of each warp (sh: NQ x 32
-// doubles); the result is valid in thread 0.
-template <int NQ>
-__device__ void warp_leaders_sum(double (&v)[NQ], double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0)
-    for (int q = 0; q < NQ; ++q) sh[q * 32 + wid] = v[q];
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    for (int q = 0; q < NQ; ++q) {
-      double s = lane < nw ? sh[q * 32 + lane] : 0.0;
-      v[q] = warp_sum(s);
-    }
-  }
-  __syncthreads();
-}
-
-// a + b - 2c for FP32 a, b, c: exact up to the last term's rounding
+// a + b - 2c for FP32 a, b, c, exact up to the rounding of the low word
 __device__ __forceinline__ DF df_second_diff(float a, float b, float c) {
   const DF s = df_two_sum(a, b);
   const DF t = df_two_sum(s.hi, __fmul_rn(-2.0f, c));  // -2c is exact
-  return df_norm(t.hi, __fadd_rn(t.lo, s.lo));
+  return {t.hi, __fadd_rn(t.lo, s.lo)};
 }
-// |C|^2 of an FP32 complex value
+// |C|^2 of an FP32 complex value, exact up to the rounding of the low word
 __device__ __forceinline__ DF df_abs2(float2 c) {
-  return df_add(df_prod(c.x, c.x), df_prod(c.y, c.y));
+  const DF x = df_prod(c.x, c.x), y = df_prod(c.y, c.y);
+  const DF s = df_two_sum(x.hi, y.hi);
+  return df_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+// |b - a|^2 of two FP32 complex values (the differences are exact)
+__device__ __forceinline__ DF df_bond(float2 a, float2 b) {
+  const DF dx = df_two_sum(b.x, -a.x), dy = df_two_sum(b.y, -a.y);
+  const DF px = df_sqr_s(dx), py = df_sqr_s(dy);
+  const DF s = df_two_sum(px.hi, py.hi);
+  return {s.hi, __fadd_rn(s.lo, __fadd_rn(px.lo, py.lo))};
 }
 
-struct DfSite {
-  float2 C;
-  DF lxr, lxi, lyr, lyi;  // second differences of Re and Im along x and y (unscaled)
-  DF dens;
-};
+// Site loop of the double-float kernels: each warp takes items of
+// 32 x DF_SEG consecutive columns of one row (coalesced loads, one integer
+// division per item); the grid strides over the items.
+template <typename F>
+__device__ __forceinline__ void df_sites(int nx, int ny, F&& f) {
+  const int lane = threadIdx.x & 31;
+  const unsigned nseg = (unsigned)(nx + 32 * DF_SEG - 1) / (32 * DF_SEG);
+  const unsigned items = nseg * (unsigned)ny;
+  const unsigned wpb = blockDim.x >> 5;
+  for (unsigned it = blockIdx.x * wpb + (threadIdx.x >> 5); it < items;
+       it += gridDim.x * wpb) {
+    const unsigned gy = it / nseg;
+    const int x0 = (int)(it - gy * nseg) * (32 * DF_SEG) + lane;
+#pragma unroll
+    for (int j = 0; j < DF_SEG; ++j) {
+      const int gx = x0 + 32 * j;
+      if (gx < nx) f(gx, (int)gy);
+    }
+  }
+}
 
-__device__ __forceinline__ DfSite df_site(const float* psi, long long off, int pitch) {
-  auto ld = [&](long long o) { return *reinterpret_cast<const float2*>(psi + 2 * o); };
-  DfSite s;
-  s.C = ld(off);
-  const float2 E = ld(off + 1), W = ld(off - 1), N = ld(off + pitch), S = ld(off - pitch);
-  s.lxr = df_second_diff(E.x, W.x, s.C.x);
-  s.lxi = df_second_diff(E.y, W.y, s.C.y);
-  s.lyr = df_second_diff(N.x, S.x, s.C.x);
-  s.lyi = df_second_diff(N.y, S.y, s.C.y);
-  s.dens = df_abs2(s.C);
+// CTA sum of NQ double-floats, one per thread: warp butterflies, then thread
+// q < NQ adds the warps' sums of quantity q in warp order.  The result is
+// valid in threads 0..NQ-1 (quantity = thread index).  sh: NQ x 32 float2.
+template <int NQ>
+__device__ __forceinline__ DF df_block_sum(DF (&v)[NQ], float2* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const DF w = df_warp_sum(v[q]);
+    if (lane == 0) sh[q * 32 + wid] = make_float2(w.hi, w.lo);
+  }
+  __syncthreads();
+  DF s = DF0;
+  if (threadIdx.x < NQ) {
+    const float2* r = sh + threadIdx.x * 32;
+    s = DF{r[0].x, r[0].y};
+    for (int w = 1; w < nw; ++w) s = df_add(s, DF{r[w].x, r[w].y});
+  }
   return s;
 }
 
-// Norm and energy of an FP32 scalar field.  Per thread: sums of |C|^2,
-// Re(C* Lx C), Re(C* Ly C) (unscaled second differences), V|C|^2, n|C|^2 and
-// |C|^4; then e = -kappa (Sx/dx^2 + Sy/dy^2) + S_V + (g/2) S_4 + g_r S_n in FP64.
-__global__ void __launch_bounds__(RED_THREADS)
-df_norm_energy_kernel(const float* psi, const float* nres, const float* V, int pitch, int nx,
-                      int ny, PhysArgs a, double* partials, double* out) {
-  __shared__ double sh[5 * 32];
-  DF s0 = DF0, sx = DF0, sy = DF0, sv = DF0, sn = DF0, s4 = DF0;
-  const long long sites = (long long)nx * ny;
-  // 32-bit site index (nx * ny < 2^31 is checked when parameters are validated)
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (unsigned)sites;
-       t += gridDim.x * blockDim.x) {
-    const unsigned gy = t / (unsigned)nx, gx = t - gy * (unsigned)nx;
-    const long long off = (long long)(gy + HALO) * pitch + gx + HALO;
-    const DfSite q = df_site(psi, off, pitch);
-    s0 = df_add(s0, q.dens);
-    sx = df_add(sx, df_add(df_mulf(q.lxr, q.C.x), df_mulf(q.lxi, q.C.y)));
-    sy = df_add(sy, df_add(df_mulf(q.lyr, q.C.x), df_mulf(q.lyi, q.C.y)));
-    if (a.has_V) sv = df_add(sv, df_mulf(q.dens, V[off]));
-    if (a.reservoir) sn = df_add(sn, df_mulf(q.dens, nres[off]));
-    s4 = df_add(s4, df_mul(q.dens, q.dens));
+// The CTA's record: NQ double-floats (as float2 in the record's double
+// slots), written by threads 0..NQ-1; then the CTA that arrives last sums all
+// records in a fixed order (deterministic whatever the arrival order),
+// converts the NQ totals to FP64 (one per thread, so that the narrow FP64
+// pipe sees a few warp instructions) and hands them to `fin` in thread 0.
+template <int NQ, typename Fin>
+__device__ void df_record_and_finish(DF (&v)[NQ], float2* sh, double* partials, Fin&& fin) {
+  __shared__ bool last;
+  __shared__ double tot[NQ];
+  float2* rec = reinterpret_cast<float2*>(partials);
+  {
+    const DF s = df_block_sum<NQ>(v, sh);
+    if (threadIdx.x < NQ) {
+      rec[(size_t)blockIdx.x * RED_Q + threadIdx.x] = make_float2(s.hi, s.lo);
+      __threadfence();  // the record visible device-wide before the arrival counts
+    }
   }
-  // warp sums in double-float; FP64 only in each warp's lane 0
-  s0 = df_warp_sum(s0);
-  sx = df_warp_sum(sx);
-  sy = df_warp_sum(sy);
-  if (a.has_V) sv = df_warp_sum(sv);
-  if (a.reservoir) sn = df_warp_sum(sn);
-  s4 = df_warp_sum(s4);
-  double acc[2] = {0.0, 0.0};
-  if ((threadIdx.x & 31) == 0) {
-    acc[0] = df_d(s0);
-    acc[1] = -a.kappa * (df_d(sx) * a.idx2 + df_d(sy) * a.idy2) + df_d(sv) +
-             0.5 * a.g * df_d(s4) + a.g_r * df_d(sn);
-  }
-  warp_leaders_sum<2>(acc, sh);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    partials[blockIdx.x * RED_Q + 0] = acc[0];
-    partials[blockIdx.x * RED_Q + 1] = acc[1];
+    unsigned int* cnt = reinterpret_cast<unsigned int*>(partials + RED_COUNTER);
+    last = atomicAdd(cnt, 1u) == gridDim.x - 1;
   }
-  finish_reduction(partials, 0, out, sh);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  DF w[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) w[q] = DF0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const float2 r = __ldcg(rec + (size_t)b * RED_Q + q);
+      w[q] = df_add(w[q], DF{r.x, r.y});
+    }
+  }
+  const DF s = df_block_sum<NQ>(w, sh);
+  if (threadIdx.x < NQ) tot[threadIdx.x] = (double)s.hi + (double)s.lo;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fin(tot);
+    *reinterpret_cast<unsigned int*>(partials + RED_COUNTER) = 0u;
+  }
 }
 
-// Residual of an FP32 scalar field.  Pass 1 (mode 0) accumulates per thread
-// |C|^2, Re and Im of C* Lx C and C* Ly C, V|C|^2, n|C|^2, |C|^4, f_n^2 and
-// n^2 and forms, in FP64,
-//   Re S_pK = -(kappa/hbar) Im(C* Lap C) + sum G|C|^2,  G = (R n - gamma_c)/2
-//   Im S_pK =  (kappa/hbar) Re(C* Lap C) - sum loc |C|^2 / hbar,
-//   loc = V + g|C|^2 + g_r n  (the terms of K = -(i/hbar) H psi + G psi).
-// Pass 2 (mode 1) forms Q = K + i omega psi per site in double-float:
-//   Q.x = -(kx Lx_i + ky Ly_i) + (mu/hbar) C.y + G C.x
-//   Q.y =  (kx Lx_r + ky Ly_r) - (mu/hbar) C.x + G C.y,
-//   kx = kappa/(hbar dx^2), mu = loc - hbar omega,
-// and accumulates |Q|^2.
+struct DfField {
+  const float2* psi;  // padded, interleaved complex
+  const float* n;     // padded planes (nullptr when absent)
+  const float* P;
+  const float* V;
+  int pitch, nx, ny;
+  int zx, zy;         // axis with zero boundary condition
+};
+
+// Per-site terms shared by the norm/energy and the residual's first pass:
+// |C|^2, the x and y bond sums, |C|^4, V|C|^2, n|C|^2.
+struct DfSums {
+  Acc s0, sbx, sby, sv, sn, s4;
+  __device__ __forceinline__ DF site(const DfField& f, const PhysArgs& a, int gx, int gy,
+                                     long long off) {
+    const float2 C = f.psi[off], E = f.psi[off + 1], N = f.psi[off + f.pitch];
+    const DF dens = df_abs2(C);
+    s0.add(dens);
+    sbx.add(df_bond(C, E));
+    sby.add(df_bond(C, N));
+    if (f.zx && gx == 0) sbx.add(dens);  // bond from the zero ghost at x = -1
+    if (f.zy && gy == 0) sby.add(dens);  // and at y = -1
+    s4.add(df_sqr_s(dens));
+    if (a.has_V) sv.add(df_mulf_s(dens, f.V[off]));
+    if (a.reservoir) sn.add(df_mulf_s(dens, f.n[off]));
+    return dens;
+  }
+};
+
+// Norm and energy of an FP32 scalar field (sums without dV):
+//   N = sum |C|^2,
+//   E = kappa (S_bx/dx^2 + S_by/dy^2) + sum V|C|^2 + (g/2) sum |C|^4 + g_r sum n|C|^2,
+// the kinetic part by the Green identity above (equal to
+// sum Re(conj(C) (-kappa Lap C))).
 __global__ void __launch_bounds__(RED_THREADS)
-df_residual_kernel(const float* psi, const float* nres, const float* P, const float* V,
-                   int pitch, int nx, int ny, PhysArgs a, DfCoeffs k, int mode, double* out,
-                   double* partials) {
-  __shared__ double sh[5 * 32];
-  const long long sites = (long long)nx * ny;
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  const double ih = 1.0 / HBAR;
-  if (mode == 0) {
-    DF s0 = DF0, sxr = DF0, syr = DF0, sxi = DF0, syi = DF0, sv = DF0, sn = DF0, s4 = DF0,
-       sfn = DF0, snn = DF0;
-    const DF gr_ = k.gamma_r, R_ = k.R;
-    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (unsigned)sites;
-         t += gridDim.x * blockDim.x) {
-      const unsigned gy = t / (unsigned)nx, gx = t - gy * (unsigned)nx;
-      const long long off = (long long)(gy + HALO) * pitch + gx + HALO;
-      const DfSite q = df_site(psi, off, pitch);
-      s0 = df_add(s0, q.dens);
-      // Re(C* L) = C.x L.x + C.y L.y,  Im(C* L) = C.x L.y - C.y L.x
-      sxr = df_add(sxr, df_add(df_mulf(q.lxr, q.C.x), df_mulf(q.lxi, q.C.y)));
-      syr = df_add(syr, df_add(df_mulf(q.lyr, q.C.x), df_mulf(q.lyi, q.C.y)));
-      sxi = df_add(sxi, df_add(df_mulf(q.lxi, q.C.x), df_neg(df_mulf(q.lxr, q.C.y))));
-      syi = df_add(syi, df_add(df_mulf(q.lyi, q.C.x), df_neg(df_mulf(q.lyr, q.C.y))));
-      if (a.has_V) sv = df_add(sv, df_mulf(q.dens, V[off]));
-      s4 = df_add(s4, df_mul(q.dens, q.dens));
-      if (a.reservoir) {
-        const float nv = nres[off];
-        sn = df_add(sn, df_mulf(q.dens, nv));
-        // f_n = P - (gamma_r + R|C|^2) n
-        const DF rate = df_add(gr_, df_mul(R_, q.dens));
-        const DF fn = df_add(df_prod(P[off], 1.0f), df_neg(df_mulf(rate, nv)));
-        sfn = df_add(sfn, df_mul(fn, fn));
-        snn = df_add(snn, df_prod(nv, nv));
-      }
-    }
-    // warp sums in double-float; FP64 only in each warp's lane 0
-    s0 = df_warp_sum(s0);
-    sxr = df_warp_sum(sxr);
-    syr = df_warp_sum(syr);
-    sxi = df_warp_sum(sxi);
-    syi = df_warp_sum(syi);
-    if (a.has_V) sv = df_warp_sum(sv);
-    s4 = df_warp_sum(s4);
+df_norm_energy_kernel(DfField f, PhysArgs a, double* partials, double* out) {
+  __shared__ float2 sh[6 * 32];
+  DfSums t;
+  df_sites(f.nx, f.ny, [&](int gx, int gy) {
+    t.site(f, a, gx, gy, (long long)(gy + HALO) * f.pitch + gx + HALO);
+  });
+  DF v[6] = {t.s0.df(), t.sbx.df(), t.sby.df(), t.sv.df(), t.sn.df(), t.s4.df()};
+  df_record_and_finish<6>(v, sh, partials, [&](const double* S) {
+    out[0] = S[0];
+    out[1] = a.kappa * (S[1] * a.idx2 + S[2] * a.idy2) + S[3] + 0.5 * a.g * S[5] +
+             a.g_r * S[4];
+  });
+}
+
+// Residual pass 1 of an FP32 scalar field: S_pp, <psi, K> and the reservoir
+// sums.  With K = -(i/hbar) H psi + G psi, G = (R n - gamma_c)/2 and the
+// identities above,
+//   Re <psi, K> = sum G|C|^2,
+//   Im <psi, K> = -(1/hbar) [kinetic + sum (V + g|C|^2 + g_r n)|C|^2],
+// omega = -Im<psi, K> / S_pp; f_n = P - (gamma_r + R|C|^2) n per site.
+__global__ void __launch_bounds__(RED_THREADS)
+df_residual1_kernel(DfField f, PhysArgs a, DfCoeffs k, double* partials, double* out) {
+  __shared__ float2 sh[8 * 32];
+  DfSums t;
+  Acc sfn, snn;
+  df_sites(f.nx, f.ny, [&](int gx, int gy) {
+    const long long off = (long long)(gy + HALO) * f.pitch + gx + HALO;
+    const DF dens = t.site(f, a, gx, gy, off);
     if (a.reservoir) {
-      sn = df_warp_sum(sn);
-      sfn = df_warp_sum(sfn);
-      snn = df_warp_sum(snn);
+      const float nv = f.n[off];
+      const DF rate = df_add_s(k.gamma_r, df_mul_s(k.R, dens));
+      const DF fn = df_add_s(DF{f.P[off], 0.f}, df_neg(df_mulf_s(rate, nv)));
+      sfn.add(df_sqr_s(fn));
+      snn.add(df_prod(nv, nv));
     }
-    if ((threadIdx.x & 31) == 0) {
-      const double kh = a.kappa * ih;
-      const double re_l = df_d(sxr) * a.idx2 + df_d(syr) * a.idy2;
-      const double im_l = df_d(sxi) * a.idx2 + df_d(syi) * a.idy2;
-      const double loc2 = df_d(sv) + a.g * df_d(s4) + a.g_r * df_d(sn);  // sum loc |C|^2
-      const double g2 = 0.5 * a.R * df_d(sn) - 0.5 * a.gamma_c * df_d(s0);  // sum G |C|^2
-      acc[0] = df_d(s0);
-      acc[1] = -kh * im_l + g2;
-      acc[2] = kh * re_l - loc2 * ih;
-      acc[3] = df_d(sfn);
-      acc[4] = df_d(snn);
+  });
+  DF v[8] = {t.s0.df(), t.sbx.df(), t.sby.df(), t.sv.df(), t.sn.df(), t.s4.df(),
+             sfn.df(),  snn.df()};
+  df_record_and_finish<8>(v, sh, partials, [&](const double* S) {
+    const double kin = a.kappa * (S[1] * a.idx2 + S[2] * a.idy2);
+    const double loc2 = S[3] + a.g * S[5] + a.g_r * S[4];
+    out[0] = S[0];
+    out[1] = a.reservoir ? 0.5 * (a.R * S[4] - a.gamma_c * S[0]) : -0.5 * a.gamma_c * S[0];
+    out[2] = -(kin + loc2) / HBAR;
+    out[3] = S[6];
+    out[4] = S[7];
+    const double om = S[0] > 0.0 ? -out[2] / S[0] : 0.0;
+    out[6] = om;
+    // -omega as a double-float for the second pass
+    const float hi = (float)(-om);
+    *reinterpret_cast<float2*>(partials + RED_COUNTER + 1) =
+        make_float2(hi, (float)(-om - (double)hi));
+  });
+}
+
+// Residual pass 2 of an FP32 scalar field: sum |Q|^2 of Q = K + i omega psi,
+//   Q.x = G C.x + M C.y - (kx Lx_i + ky Ly_i),
+//   Q.y = G C.y - M C.x + (kx Lx_r + ky Ly_r),
+//   M = (V + g|C|^2 + g_r n)/hbar - omega,  kx = kappa/(hbar dx^2),
+// L the unscaled second differences of Re / Im along x and y; every term in
+// double-float (Q is a small difference of terms of the size of K).
+__global__ void __launch_bounds__(RED_THREADS)
+df_residual2_kernel(DfField f, PhysArgs a, DfCoeffs k, double* partials, double* out) {
+  __shared__ float2 sh[32];
+  const float2 w2 = __ldcg(reinterpret_cast<const float2*>(partials + RED_COUNTER + 1));
+  const DF nom = {w2.x, w2.y};  // -omega, left by the first pass's last CTA
+  Acc sq;
+  df_sites(f.nx, f.ny, [&](int gx, int gy) {
+    const long long off = (long long)(gy + HALO) * f.pitch + gx + HALO;
+    const float2 C = f.psi[off], E = f.psi[off + 1], W = f.psi[off - 1];
+    const float2 N = f.psi[off + f.pitch], S = f.psi[off - f.pitch];
+    const DF dens = df_abs2(C);
+    const DF lr = df_add_s(df_mul_s(k.kx, df_second_diff(E.x, W.x, C.x)),
+                           df_mul_s(k.ky, df_second_diff(N.x, S.x, C.x)));
+    const DF li = df_add_s(df_mul_s(k.kx, df_second_diff(E.y, W.y, C.y)),
+                           df_mul_s(k.ky, df_second_diff(N.y, S.y, C.y)));
+    DF M = df_add_s(df_mul_s(k.gh, dens), nom);
+    if (a.has_V) M = df_add_s(M, df_mulf_s(k.ih, f.V[off]));
+    DF G = k.hgc;
+    if (a.reservoir) {
+      const float nv = f.n[off];
+      M = df_add_s(M, df_mulf_s(k.grh, nv));
+      G = df_add_s(k.hgc, df_mulf_s(k.hR, nv));
     }
-  } else {
-    const DF kx = k.kx, ky = k.ky, ihd = k.ih, g_ = k.g, gr_ = k.g_r, hR = k.hR, hgc = k.hgc;
-    // -hbar omega as a double-float, left by the first pass's last CTA
-    const float2 hw2 = __ldcg(reinterpret_cast<const float2*>(partials + RED_COUNTER + 1));
-    const DF hw = {hw2.x, hw2.y};
-    DF sq = DF0;
-    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (unsigned)sites;
-         t += gridDim.x * blockDim.x) {
-      const unsigned gy = t / (unsigned)nx, gx = t - gy * (unsigned)nx;
-      const long long off = (long long)(gy + HALO) * pitch + gx + HALO;
-      const DfSite q = df_site(psi, off, pitch);
-      DF mu = df_add(df_mul(g_, q.dens), hw);
-      if (a.has_V) mu = df_add(mu, df_prod(V[off], 1.0f));
-      DF G = hgc;
-      if (a.reservoir) {
-        const float nv = nres[off];
-        mu = df_add(mu, df_mulf(gr_, nv));
-        G = df_add(hgc, df_mulf(hR, nv));
-      }
-      const DF mh = df_mul(mu, ihd);
-      const DF lr = df_add(df_mul(kx, q.lxr), df_mul(ky, q.lyr));
-      const DF li = df_add(df_mul(kx, q.lxi), df_mul(ky, q.lyi));
-      const DF qx = df_add(df_add(df_neg(li), df_mulf(mh, q.C.y)), df_mulf(G, q.C.x));
-      const DF qy = df_add(df_add(lr, df_neg(df_mulf(mh, q.C.x))), df_mulf(G, q.C.y));
-      sq = df_add(sq, df_add(df_mul(qx, qx), df_mul(qy, qy)));
-    }
-    sq = df_warp_sum(sq);
-    if ((threadIdx.x & 31) == 0) acc[0] = df_d(sq);
-  }
-  warp_leaders_sum<5>(acc, sh);
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < 5; ++q) partials[blockIdx.x * RED_Q + q] = acc[q];
-  }
-  finish_reduction(partials, mode ? 2 : 1, out, sh);
+    const DF qx = df_add_s(df_add_s(df_mulf_s(G, C.x), df_mulf_s(M, C.y)), df_neg(li));
+    const DF qy = df_add_s(df_add_s(df_mulf_s(G, C.y), df_neg(df_mulf_s(M, C.x))), lr);
+    sq.add(df_sqr_s(qx));
+    sq.add(df_sqr_s(qy));
+  });
+  DF v[1] = {sq.df()};
+  df_record_and_finish<1>(v, sh, partials, [&](const double* S) { out[5] = S[0]; });
 }
 
 static PhysArgs make_phys(const ReduceArgs& r) {
@@ -557,14 +641,27 @@ static SiteView<R> make_view(const ReduceArgs& r) {
   return v;
 }
 
+static DfField make_df_field(const ReduceArgs& r) {
+  DfField f;
+  f.psi = static_cast<const float2*>(r.psi);
+  f.n = static_cast<const float*>(r.n);
+  f.P = static_cast<const float*>(r.P);
+  f.V = static_cast<const float*>(r.V);
+  f.pitch = r.geo.pitch;
+  f.nx = r.geo.nx;
+  f.ny = r.geo.ny;
+  f.zx = r.geo.bc_x == BC_ZERO;
+  f.zy = r.geo.bc_y == BC_ZERO;
+  return f;
+}
+
 cudaError_t launch_norm_energy(const ReduceArgs& r, double* partials,
                                double* out, cudaStream_t s) {
   PhysArgs a = make_phys(r);
   int nb = reduce_blocks(r.geo);
   if (r.precision == 32 && r.ncomp == 1)
-    df_norm_energy_kernel<<<df_reduce_blocks(r.geo), RED_THREADS, 0, s>>>(
-        static_cast<const float*>(r.psi), static_cast<const float*>(r.n),
-        static_cast<const float*>(r.V), r.geo.pitch, r.geo.nx, r.geo.ny, a, partials, out);
+    df_norm_energy_kernel<<<df_reduce_blocks(r.geo), RED_THREADS, 0, s>>>(make_df_field(r), a,
+                                                                         partials, out);
   else if (r.precision == 32)
     norm_energy_kernel<float><<<nb, RED_THREADS, 0, s>>>(make_view<float>(r), a,
                                                          r.geo.nx, r.geo.ny, partials, out);
@@ -578,31 +675,31 @@ cudaError_t launch_norm_energy(const ReduceArgs& r, double* partials,
 cudaError_t launch_residual(const ReduceArgs& r, double* partials, double* out,
                             cudaStream_t s) {
   PhysArgs a = make_phys(r);
-  int nb = reduce_blocks(r.geo);
-  DfCoeffs k;
-  k.kx = df_host(a.kappa / HBAR * a.idx2);
-  k.ky = df_host(a.kappa / HBAR * a.idy2);
-  k.ih = df_host(1.0 / HBAR);
-  k.g = df_host(a.g);
-  k.g_r = df_host(a.g_r);
-  k.hR = df_host(0.5 * a.R);
-  k.hgc = df_host(-0.5 * a.gamma_c);
-  k.gamma_r = df_host(a.gamma_r);
-  k.R = df_host(a.R);
-  for (int mode = 0; mode < 2; ++mode) {
-    if (r.precision == 32 && r.ncomp == 1)
-      df_residual_kernel<<<df_reduce_blocks(r.geo), RED_THREADS, 0, s>>>(
-          static_cast<const float*>(r.psi), static_cast<const float*>(r.n),
-          static_cast<const float*>(r.P), static_cast<const float*>(r.V), r.geo.pitch,
-          r.geo.nx, r.geo.ny, a, k, mode, out, partials);
-    else if (r.precision == 32)
-      residual_kernel<float><<<nb, RED_THREADS, 0, s>>>(make_view<float>(r), a,
-                                                        r.geo.nx, r.geo.ny, mode,
-                                                        out, partials);
-    else
-      residual_kernel<double><<<nb, RED_THREADS, 0, s>>>(make_view<double>(r), a,
-                                                         r.geo.nx, r.geo.ny, mode,
-                                                         out, partials);
+  if (r.precision == 32 && r.ncomp == 1) {
+    DfCoeffs k;
+    k.kx = df_host(a.kappa / HBAR * a.idx2);
+    k.ky = df_host(a.kappa / HBAR * a.idy2);
+    k.ih = df_host(1.0 / HBAR);
+    k.gh = df_host(a.g / HBAR);
+    k.grh = df_host(a.g_r / HBAR);
+    k.hR = df_host(0.5 * a.R);
+    k.hgc = df_host(-0.5 * a.gamma_c);
+    k.gamma_r = df_host(a.gamma_r);
+    k.R = df_host(a.R);
+    const DfField f = make_df_field(r);
+    const int nb = df_reduce_blocks(r.geo);
+    df_residual1_kernel<<<nb, RED_THREADS, 0, s>>>(f, a, k, partials, out);
+    df_residual2_kernel<<<nb, RED_THREADS, 0, s>>>(f, a, k, partials, out);
+  } else {
+    const int nb = reduce_blocks(r.geo);
+    for (int mode = 0; mode < 2; ++mode) {
+      if (r.precision == 32)
+        residual_kernel<float><<<nb, RED_THREADS, 0, s>>>(make_view<float>(r), a, r.geo.nx,
+                                                          r.geo.ny, mode, out, partials);
+      else
+        residual_kernel<double><<<nb, RED_THREADS, 0, s>>>(make_view<double>(r), a, r.geo.nx,
+                                                           r.geo.ny, mode, out, partials);
+    }
   }
   count_launch(2);
   return cudaGetLastError();

@@ -20,7 +20,7 @@ TmaBox tma_box(int tile_cfg) {
   if (tile_cfg == TILE_64x48_M2) { MR = 2; WY = 24; }
   if (tile_cfg == TILE_64x64_M2) { MR = 2; WY = 32; }
   if (tile_cfg == TILE_64x32_M2_2) { MR = 2; WY = 16; }
-  if (tile_cfg == TILE_64x32_M4_2) { MR = 4; WY = 8; }
+  if (tile_cfg == TILE_64x32_M4_2 || tile_cfg == TILE_64x32_M4_2_MS) { MR = 4; WY = 8; }
   if (tile_cfg == TILE_SPINOR_64x16) { MR = 2; WY = 8; }
   if (tile_cfg == TILE_SPINOR_64x24) { MR = 2; WY = 12; }
   if (tile_cfg == TILE_SPINOR_64x32) { MR = 2; WY = 16; }
@@ -35,7 +35,10 @@ TmaBox tma_box(int tile_cfg) {
 }
 
 int tma_ctas_per_sm(int tile_cfg) {
-  return tile_cfg == TILE_64x32_M2_2 || tile_cfg == TILE_64x32_M4_2 ? 2 : 1;
+  return tile_cfg == TILE_64x32_M2_2 || tile_cfg == TILE_64x32_M4_2 ||
+                 tile_cfg == TILE_64x32_M4_2_MS
+             ? 2
+             : 1;
 }
 
 cudaError_t launch_rk4_tma_f32(int tile_cfg, int mode, bool pot, bool per,
@@ -48,10 +51,33 @@ cudaError_t launch_rk4_tma_f32(int tile_cfg, int mode, bool pot, bool per,
     case TILE_64x48_M2: return launch_tma_cfg4(mode, pot, per, one, ta, s, grid);
     case TILE_64x64_M2: return launch_tma_cfg5(mode, pot, per, one, ta, s, grid);
     case TILE_64x32_M2_2: return launch_tma_cfg6(mode, pot, per, one, ta, s, grid);
-    case TILE_64x32_M4_2: return launch_tma_cfg7(mode, pot, per, one, ta, s, grid);
+    case TILE_64x32_M4_2:
+    case TILE_64x32_M4_2_MS: return launch_tma_cfg7(mode, pot, per, one, ta, s, grid);
     default: break;
   }
   return cudaErrorInvalidValue;
+}
+
+bool tma_has_multistep(int tile_cfg) { return tile_cfg == TILE_64x32_M4_2_MS; }
+
+cudaError_t launch_rk4_tma_f32_ms(int tile_cfg, int mode, bool pot, bool per,
+                                  const TileArgs& ta, cudaStream_t s, int grid) {
+  if (tile_cfg == TILE_64x32_M4_2_MS) return launch_tma_cfg7_ms(mode, pot, per, ta, s, grid);
+  return cudaErrorInvalidValue;
+}
+
+__global__ void clock_advance_kernel(DevClock* c, int parity, int nsteps, double dt) {
+  double t = c->t[parity];
+  for (int i = 0; i < nsteps; ++i) t += dt;
+  c->t[parity ^ 1] = t;
+  c->step[parity ^ 1] = c->step[parity] + nsteps;
+}
+
+cudaError_t launch_clock_advance(DevClock* clock, int parity, int nsteps, double dt,
+                                 cudaStream_t s) {
+  clock_advance_kernel<<<1, 1, 0, s>>>(clock, parity, nsteps, dt);
+  count_launch();
+  return cudaGetLastError();
 }
 
 // ---- tensor-map encoding (driver entry point, no libcuda link needed) -----

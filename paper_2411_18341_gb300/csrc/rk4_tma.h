@@ -18,6 +18,7 @@ enum {
   TILE_64x64_M2 = 5,  // 2 x 2, 32 warps
   TILE_64x32_M2_2 = 6,  // 2 x 2, 16 warps, two CTAs per SM
   TILE_64x32_M4_2 = 7,  // 4 x 2, 8 warps, two CTAs per SM
+  TILE_64x32_M4_2_MS = 8,  // configuration 7, several steps per launch (single handles)
   // two-component field with reservoirs (2 x 2 micro-tiles of both components)
   TILE_SPINOR_64x16 = 21,  // 8 warps
   TILE_SPINOR_64x24 = 22,  // 12 warps
@@ -81,6 +82,13 @@ struct TileArgs {
   double* t_inst;        // [2][ninst] FP64 times of all instances, or nullptr
   int* err;              // set when a bounded wait gives up
   int inject_timeout;    // test hook: leave the first tile's barrier unarmed
+  // Several steps in one launch (single instance): items (step, tile) in a
+  // fixed order, a tile's load issued once its neighbours completed the
+  // previous step.  done[ky * tiles_x + kx] = steps of this launch completed
+  // by that tile (zeroed before the launch).
+  int* done = nullptr;
+  int ms_steps = 1;      // steps in this launch
+  int tiles_y = 0;
 };
 
 struct TmaBox {
@@ -131,5 +139,19 @@ cudaError_t launch_tma_cfg6(int mode, bool pot, bool per, bool one, const TileAr
                             cudaStream_t s, int grid);
 cudaError_t launch_tma_cfg7(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid);
+
+// Several steps per launch (single instance, mode 0 or 1; ta.done zeroed,
+// ta.ms_steps, ta.tiles_y set).  Configurations with such a variant:
+bool tma_has_multistep(int tile_cfg);
+cudaError_t launch_rk4_tma_f32_ms(int tile_cfg, int mode, bool pot, bool per,
+                                  const TileArgs& ta, cudaStream_t s, int grid);
+cudaError_t launch_tma_cfg7_ms(int mode, bool pot, bool per, const TileArgs& ta, cudaStream_t s,
+                               int grid);
+
+// Advance the step counter and FP64 time by nsteps steps (slot parity ->
+// parity ^ 1; the time as nsteps sequential additions of dt, like nsteps
+// single-step launches).
+cudaError_t launch_clock_advance(DevClock* clock, int parity, int nsteps, double dt,
+                                 cudaStream_t s);
 
 }  // namespace phx

@@ -9,4 +9,9 @@ cudaError_t launch_tma_cfg7(int mode, bool pot, bool per, bool one, const TileAr
   return tma::launch_variants<4, 8, 2>(mode, pot, per, one, ta, s, grid);
 }
 
+cudaError_t launch_tma_cfg7_ms(int mode, bool pot, bool per, const TileArgs& ta, cudaStream_t s,
+                               int grid) {
+  return tma::launch_variants_ms<4, 8, 2>(mode, pot, per, ta, s, grid);
+}
+
 }  // namespace phx

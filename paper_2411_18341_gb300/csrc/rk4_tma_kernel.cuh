@@ -84,6 +84,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// Completion counters of the multi-step launch: relaxed loads and stores at
+// GPU scope; the ordering comes from fence.acq_rel.gpu around them.
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(int* p, int v) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+// orders this thread's generic-proxy view of global memory (data other CTAs
+// stored, acquired above) before its following async-proxy (TMA) reads
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y,
                                             int z, uint64_t* bar) {
   asm volatile(
@@ -125,11 +144,32 @@ struct Cfg {
 // (ta.one: constant-bank operands, hoisted out of the tile loop) and whose
 // tile coordinates advance incrementally; otherwise per-tile instance
 // records and precomputed tile coordinates (ta.tile_info).
-template <int MODE, bool POT, bool PER, bool ONE, int MR, int WY, int MINB>
+//
+// MS: ta.ms_steps steps in one launch (single instance, no drive).  Work item
+// i = s * ntiles + pos is tile pos of step s; CTA c takes items c, c + G,
+// c + 2G, ... (G = gridDim.x), so no CTA idles at a step boundary.  Tile
+// rows are visited in the folded order 0, ty-1, 1, ty-2, ..., which puts the
+// rows a tile depends on (its own and the two next to it, periodic wrap
+// included) within two positions of its own, and rows 0 and ty-2 (which
+// depend on each other through the ghost rows when the last tile row is thin,
+// see dep_axis) within three.  A tile's load for step s is issued once the
+// counters done[] of the tiles it exchanges data with reached s: their
+// outputs of step s-1 (the input of step s) are stored, and their reads of
+// the buffer that step s writes are over.  Warp 0 loads the counters of the
+// next item with relaxed loads ahead of time and checks them after the stage
+// barriers, so the poll seldom stalls; an item whose neighbours are not done
+// when it becomes current is waited for (bounded).  A tile's counter is
+// published after the next item's first stage barrier (or at the next item's
+// start when that item waits), so the waiting item never depends on an
+// unpublished item of its own CTA unless the host's check
+// G not in [ntiles - 4 tiles_x, ntiles + 4 tiles_x] fails (the folded order
+// keeps every dependency within 4 tiles_x - 1 positions).
+template <int MODE, bool POT, bool PER, bool ONE, int MR, int WY, int MINB, bool MS = false>
 __global__ void __launch_bounds__(32 * WY, MINB)
 rk4_f32_tma(const TileArgs ta) {
   constexpr bool RES = MODE == 1, DRV = MODE == 2;
   using C = Cfg<MODE, POT, MR, WY, MINB>;
+  static_assert(!MS || (ONE && !DRV && C::NBUF == 2), "multi-step: single instance, no drive");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[3];
   __shared__ float2 s_dph[4];  // drive phase exp(-i omega t_s) / hbar per stage
@@ -198,15 +238,15 @@ rk4_f32_tma(const TileArgs ta) {
       c = coord_of(t_next);
     }
   };
-  auto issue = [&](const Coord& c, int b) {
+  auto issue = [&](const Coord& c, int b, int cur) {
     const TileInst* I = ta.inst + c.inst;
     const int xp = c.kx * C::TX;  // padded column of region column 0
     const int yp = c.ky * C::TY;  // padded row of region row -1
     mbar_arrive_expect_tx(&bar[b], C::TX_BYTES);
-    tma_load_3d(psi_buf(b), &I->psi[ta.cur], 2 * (xp - 2), yp, 0, &bar[b]);
+    tma_load_3d(psi_buf(b), &I->psi[cur], 2 * (xp - 2), yp, 0, &bar[b]);
     int f = 0;
     if (RES) {
-      tma_load_3d(f_buf(b, f++), &I->n[ta.cur], xp & ~3, yp + 1, 0, &bar[b]);
+      tma_load_3d(f_buf(b, f++), &I->n[cur], xp & ~3, yp + 1, 0, &bar[b]);
       tma_load_3d(f_buf(b, f++), &I->P, xp & ~3, yp + 1, 0, &bar[b]);
     }
     if (DRV) {
@@ -230,7 +270,7 @@ rk4_f32_tma(const TileArgs ta) {
 
   // FP64 simulated time: instance 0 in the clock, all instances in t_inst
   const long long step = ta.clock->step[ta.parity];
-  if (blockIdx.x == 0) {
+  if (!MS && blockIdx.x == 0) {
     if (tid == 0) {
       ta.clock->step[ta.parity ^ 1] = step + 1;
       ta.clock->t[ta.parity ^ 1] = ta.clock->t[ta.parity] + ta.inst[0].dt64;
@@ -241,25 +281,144 @@ rk4_f32_tma(const TileArgs ta) {
             ta.t_inst[ta.parity * ta.ninst + i] + ta.inst[i].dt64;
   }
 
-  int t = blockIdx.x, k = 0;
+  // multi-step items: step s of the launch and tile (kx, ky) of item i
+  const int nitems = MS ? ta.ntiles * ta.ms_steps : ta.ntiles;
+  const int G = (int)gridDim.x;
+  auto ms_coord = [&](int i, Coord& c, int& s) {
+    s = i / ta.ntiles;
+    const int pos = i - s * ta.ntiles;
+    const int rp = pos / tiles_x1;
+    c.inst = 0;
+    c.kx = pos - rp * tiles_x1;
+    c.ky = (rp & 1) ? ta.tiles_y - 1 - (rp >> 1) : (rp >> 1);
+  };
+  // warp 0 of a multi-step launch: the item whose load waits for its
+  // neighbours (or -1; in shared memory, which only warp 0 uses, to spare a
+  // register), lanes 0..8 holding the counter of one neighbour each in fv.
+  // Coordinates, step and buffer are recomputed from the item.  A counter is
+  // published with atomicMax, so that publishing an item twice is harmless.
+  __shared__ int s_pend;
+  int fv = 0x7fffffff;
+  auto set_pend = [&](int v) {
+    __syncwarp();
+    if (lane == 0) s_pend = v;
+    __syncwarp();
+  };
+  // Along an axis a tile exchanges data with its two neighbours (periodic
+  // wrap included) and, when the last tile holds fewer rows (columns) than
+  // its box reaches past them, tiles 0 and n-2 exchange too: the box of tile
+  // n-2 then reaches the ghost rows that tile 0 writes, and tile 0 writes
+  // them from rows that tile n-2 computes.  Candidate c of 0..3 along an axis
+  // of n tiles: k-1, k, k+1 (mod n), or that partner (-1: none).
+  auto dep_axis = [&](int k, int c, int n, bool thin) {
+    if (c < 3) {
+      const int v = k + c - 1;
+      return v < 0 ? v + n : (v >= n ? v - n : v);
+    }
+    if (!thin) return -1;
+    return k == 0 ? n - 2 : (k == n - 2 ? 0 : -1);
+  };
+  // (tile kx's box ends at domain column (kx + 1) TX + 3, tile ky's at row
+  // (ky + 1) TY + HALO)
+  const bool thin_x = (tiles_x1 - 1) * C::TX + 3 > ta.one.geo.nx;
+  const bool thin_y = (ta.tiles_y - 1) * C::TY + HALO > ta.one.geo.ny;
+  auto ms_load_deps = [&]() {  // warp 0: lanes 0..15 load one candidate each
+    fv = 0x7fffffff;
+    if (lane < 16) {
+      Coord c;
+      int sp;
+      ms_coord(s_pend, c, sp);
+      const int dx = dep_axis(c.kx, lane & 3, tiles_x1, thin_x);
+      const int dy = dep_axis(c.ky, lane >> 2, ta.tiles_y, thin_y);
+      if (dx >= 0 && dy >= 0) fv = ld_relaxed_gpu(ta.done + dy * tiles_x1 + dx);
+    }
+  };
+  auto ms_issue_pending = [&]() {  // warp 0, after fence.acq_rel.gpu
+    __syncwarp();  // every lane's acquire before lane 0's loads
+    if (lane == 0) {
+      const int pend = s_pend;
+      Coord c;
+      int sp;
+      ms_coord(pend, c, sp);
+      fence_proxy_async_global();  // the acquired outputs before the TMA reads
+      fence_proxy_async();         // this CTA's generic reads of the buffer before its refill
+      issue(c, ((pend - (int)blockIdx.x) / G) % C::NBUF, ta.cur ^ (sp & 1));
+    }
+    set_pend(-1);
+  };
+  auto ms_publish = [&](int item) {  // warp 0, after fence.acq_rel.gpu
+    if (lane == 0) {
+      Coord c;
+      int sp;
+      ms_coord(item, c, sp);
+      atomicMax(ta.done + c.ky * tiles_x1 + c.kx, sp + 1);
+    }
+  };
+  // publish this CTA's previous item (its stores precede a CTA barrier),
+  // then check the pending item's neighbours loaded earlier (warp 0)
+  auto ms_point = [&](bool publish, int t_now) {
+    const int pend = s_pend;
+    publish = publish && t_now >= (int)blockIdx.x + G;
+    if (!publish && pend < 0) return;
+    fence_acq_rel_gpu();
+    if (publish) ms_publish(t_now - G);
+    if (pend >= 0) {
+      if (__all_sync(0xffffffffu, fv >= pend / ta.ntiles)) ms_issue_pending();
+      else ms_load_deps();
+    }
+  };
+
+  int t = blockIdx.x, k = 0, s_cur = 0;
   Coord cc = coord_of(t < ta.ntiles ? t : 0);  // current tile
   Coord cn = cc;                               // next tile to issue (thread 0)
-  if (tid == 0) {  // prologue: the first NBUF-1 tiles
+  if (MS) {
+    if (warp == 0) {  // prologue: the first item, if it has no dependency
+      set_pend(t < nitems ? t : -1);
+      if (t < nitems && t < ta.ntiles) {
+        if (ta.inject_timeout) set_pend(-1);
+        else ms_issue_pending();
+      }
+    }
+  } else if (tid == 0) {  // prologue: the first NBUF-1 tiles
     for (int i = 0; i < C::NBUF - 1; ++i) {
       const int ti = t + i * (int)gridDim.x;
-      if (ti < ta.ntiles && !(i == 0 && ta.inject_timeout)) issue(cn, i);
+      if (ti < ta.ntiles && !(i == 0 && ta.inject_timeout)) issue(cn, i, ta.cur);
       advance(cn, ti + (int)gridDim.x);
     }
   }
-  for (; t < ta.ntiles; t += gridDim.x, ++k) {
+  for (; t < nitems; t += G, ++k) {
     const int b = k % C::NBUF;
     const uint32_t par = (uint32_t)((k / C::NBUF) & 1);
     const int tn = t + (C::NBUF - 1) * (int)gridDim.x;
+    int dep_fail = 0;
+    if (MS) {
+      ms_coord(t, cc, s_cur);
+      // the previous item's stores are done by every thread; does this item
+      // still wait for its neighbours?
+      if (__syncthreads_or(warp == 0 && s_pend == t) && warp == 0) {
+        fence_acq_rel_gpu();
+        if (k > 0) ms_publish(t - G);
+        const int need = t / ta.ntiles;
+        const unsigned long long t0 = global_ns();
+        for (uint32_t it = 0;; ++it) {
+          ms_load_deps();
+          if (__all_sync(0xffffffffu, fv >= need)) break;
+          if (it >= 4) __nanosleep(128);
+          if ((it & 63u) == 63u && global_ns() - t0 > 250000000ull) {
+            dep_fail = 1;
+            break;
+          }
+        }
+        fence_acq_rel_gpu();
+        if (dep_fail) set_pend(-1);
+        else ms_issue_pending();
+      }
+    }
     // every thread waits on the barrier (bounded); the CTA leaves together
     // if any thread gave up, after waiting (bounded) for its other loads.
     // This barrier also closes the previous tile: every thread has finished
     // reading its buffers and the shared stage buffer Y.
-    const int fail = !mbar_wait_bounded(&bar[b], par);
+    const int fail = dep_fail || !mbar_wait_bounded(&bar[b], par);
     if (__syncthreads_or(fail)) {
       if (tid == 0) {
         atomicExch(ta.err, 1);
@@ -270,20 +429,27 @@ rk4_f32_tma(const TileArgs ta) {
       return;
     }
     // refill the buffer the previous tile used
-    if (tid == 0 && tn < ta.ntiles) {
+    if (MS) {
+      if (warp == 0 && t + G < nitems) {
+        set_pend(t + G);
+        if (t + G < ta.ntiles) ms_issue_pending();  // step 0 reads the launch's input
+        else ms_load_deps();
+      }
+    } else if (tid == 0 && tn < ta.ntiles) {
       fence_proxy_async();  // its generic reads before the async-proxy write
-      issue(cn, (k + C::NBUF - 1) % C::NBUF);
+      issue(cn, (k + C::NBUF - 1) % C::NBUF, ta.cur);
       advance(cn, tn + (int)gridDim.x);
     }
 
     const int kx = cc.kx, ky = cc.ky;
     const TileInst* I = ta.inst + cc.inst;
     const Geometry g = ONE ? ta.one.geo : I->geo;
-    float2* const psi_out = ONE ? ta.one.psi_buf[ta.cur ^ 1] : I->psi_buf[ta.cur ^ 1];
-    float* const n_out = ONE ? ta.one.n_buf[ta.cur ^ 1] : I->n_buf[ta.cur ^ 1];
+    const int cur = MS ? ta.cur ^ (s_cur & 1) : ta.cur;
+    float2* const psi_out = ONE ? ta.one.psi_buf[cur ^ 1] : I->psi_buf[cur ^ 1];
+    float* const n_out = ONE ? ta.one.n_buf[cur ^ 1] : I->n_buf[cur ^ 1];
     const CoeffsT<float> q = ONE ? ta.one.k : I->k;
     const NoiseKey nz = ONE ? ta.one.noise : I->noise;
-    advance(cc, t + (int)gridDim.x);
+    if (!MS) advance(cc, t + (int)gridDim.x);
     const float2 ax2 = f2(q.ax, q.ax), ay2 = f2(q.ay, q.ay);
     // real coefficients as pairs: the thread's two columns go through the
     // real-valued terms (density, local term, gain, reservoir) together
@@ -309,6 +475,17 @@ rk4_f32_tma(const TileArgs ta) {
     bool ins[MR][2];
     const int gx0 = xp - HALO + c0;        // domain column of my first column
     const int gy0 = ky * C::TY - 3 + r0;   // domain row of my first row
+    // n0 and P of row j: held in registers, or (multi-step launch, whose
+    // bookkeeping needs the registers) read again from the tile's shared
+    // n and P boxes, which no stage overwrites
+    auto N0 = [&](int j) {
+      return (MS && RES) ? *reinterpret_cast<const float2*>(&Nb[(r0 + j) * C::FW + foff + c0])
+                         : n0[j];
+    };
+    auto PV = [&](int j) {
+      return (MS && RES) ? *reinterpret_cast<const float2*>(&Pb[(r0 + j) * C::FW + foff + c0])
+                         : Pv[j];
+    };
 #pragma unroll
     for (int j = 0; j < MR; ++j) {
       const float4 v = *reinterpret_cast<const float4*>(&P0[(r0 + j + 1) * C::PW + c0 + 2]);
@@ -325,10 +502,10 @@ rk4_f32_tma(const TileArgs ta) {
       // foff + c0 is even: the pair of a row is one 8-byte load
       const int fi = (r0 + j) * C::FW + foff + c0;
       auto ld2 = [&](const float* b) { return *reinterpret_cast<const float2*>(&b[fi]); };
-      n0[j] = RES ? ld2(Nb) : f2(0.f, 0.f);
-      nc[j] = n0[j];
+      n0[j] = (RES && !MS) ? ld2(Nb) : f2(0.f, 0.f);
+      nc[j] = RES ? ld2(Nb) : f2(0.f, 0.f);
       na[j] = f2(0.f, 0.f);
-      Pv[j] = RES ? ld2(Pb) : f2(0.f, 0.f);
+      Pv[j] = (RES && !MS) ? ld2(Pb) : f2(0.f, 0.f);
       Er[j] = DRV ? ld2(Erb) : f2(0.f, 0.f);
       Ei[j] = DRV ? ld2(Eib) : f2(0.f, 0.f);
       // the stencil's diagonal a0 rides with the local potential
@@ -404,9 +581,9 @@ rk4_f32_tma(const TileArgs ta) {
           if (!PER && !ins[j][i]) ny[j][i] = f2(0.f, 0.f);
         }
         if (RES) {  // Kn = P - (gamma_r + R|psi|^2) n for both sites
-          const float2 Kn = __ffma2_rn(__ffma2_rn(ncR2, dens, ncgam2), nc[j], Pv[j]);
+          const float2 Kn = __ffma2_rn(__ffma2_rn(ncR2, dens, ncgam2), nc[j], PV(j));
           na[j] = s == 0 ? Kn : __ffma2_rn(w2, Kn, na[j]);
-          nn[j] = __ffma2_rn(cs2, Kn, n0[j]);
+          nn[j] = __ffma2_rn(cs2, Kn, N0(j));
         } else {
           nn[j] = f2(0.f, 0.f);
         }
@@ -423,6 +600,7 @@ rk4_f32_tma(const TileArgs ta) {
                 make_float4(ny[j][0].x, ny[j][0].y, ny[j][1].x, ny[j][1].y);
         }
         __syncthreads();  // the last stage reads but writes no shared memory
+        if (MS && warp == 0) ms_point(s == 0, t);
       }
     }
 
@@ -434,7 +612,7 @@ rk4_f32_tma(const TileArgs ta) {
     for (int j = 0; j < MR; ++j) {
 #pragma unroll
       for (int i = 0; i < 2; ++i) o[j][i] = __ffma2_rn(d62, acc[j][i], p0[j][i]);
-      on[j] = __ffma2_rn(d62, na[j], n0[j]);
+      on[j] = __ffma2_rn(d62, na[j], N0(j));
     }
     if (nz.on) {  // grid-uniform branch: the generator is not issued when off
       // The micro-tile's columns gx0 (even) and gx0 + 1 hold the sites 2p and
@@ -453,15 +631,15 @@ rk4_f32_tma(const TileArgs ta) {
           const int gx = gx0 + i;
           site[i] = row + (uint32_t)((gx % g.nx + g.nx) % g.nx);
           sc[i] = nz.twa ? nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var,
-                                           RES ? (i ? n0[j].y : n0[j].x) : 0.f)
+                                           RES ? (i ? N0(j).y : N0(j).x) : 0.f)
                          : nz.scale;
         }
         if (paired) {
-          nz_pair(nz.seed, nz.instance, step, site[0] >> 1, sc[0], sc[1], xi[0], xi[1]);
+          nz_pair(nz.seed, nz.instance, MS ? step + s_cur : step, site[0] >> 1, sc[0], sc[1], xi[0], xi[1]);
         } else {
           float2 unused;
-          nz_site(nz.seed, nz.instance, step, site[0], sc[0], xi[0], unused, false);
-          nz_site(nz.seed, nz.instance, step, site[1], sc[1], xi[1], unused, false);
+          nz_site(nz.seed, nz.instance, MS ? step + s_cur : step, site[0], sc[0], xi[0], unused, false);
+          nz_site(nz.seed, nz.instance, MS ? step + s_cur : step, site[1], sc[1], xi[1], unused, false);
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -526,6 +704,13 @@ rk4_f32_tma(const TileArgs ta) {
       }
     }
   }
+  if (MS) {  // the last item
+    __syncthreads();
+    if (warp == 0 && k > 0) {
+      fence_acq_rel_gpu();
+      ms_publish(t - G);
+    }
+  }
 }
 
 template <int MODE, bool POT, bool PER, bool ONE, int MR, int WY, int MINB>
@@ -555,6 +740,58 @@ cudaError_t launch_cfg(const TileArgs& ta, cudaStream_t s, int grid) {
   count_launch();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+// Multi-step launch: cooperative, so that every CTA is resident (CTAs wait
+// for items of other CTAs).
+template <int MODE, bool POT, bool PER, int MR, int WY, int MINB>
+cudaError_t launch_cfg_ms(const TileArgs& ta, cudaStream_t s, int grid) {
+  using C = Cfg<MODE, POT, MR, WY, MINB>;
+  auto kern = rk4_f32_tma<MODE, POT, PER, true, MR, WY, MINB, true>;
+  static int configured_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_dev != dev) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+  }
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(C::NT);
+  lc.dynamicSmemBytes = C::SMEM;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&lc, kern, ta);
+  count_launch();
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// The multi-step variants of one tile configuration (mode 0 or 1).
+template <int MR, int WY, int MINB>
+cudaError_t launch_variants_ms(int mode, bool pot, bool per, const TileArgs& ta,
+                               cudaStream_t s, int grid) {
+#define PHX_TMA_MS(M_)                                                             \
+  if (per) {                                                                       \
+    if (pot) return launch_cfg_ms<M_, true, true, MR, WY, MINB>(ta, s, grid);      \
+    return launch_cfg_ms<M_, false, true, MR, WY, MINB>(ta, s, grid);              \
+  }                                                                                \
+  if (pot) return launch_cfg_ms<M_, true, false, MR, WY, MINB>(ta, s, grid);       \
+  return launch_cfg_ms<M_, false, false, MR, WY, MINB>(ta, s, grid);
+  if (mode == 1) {
+    PHX_TMA_MS(1)
+  }
+  if (mode == 0) {
+    PHX_TMA_MS(0)
+  }
+#undef PHX_TMA_MS
+  return cudaErrorInvalidValue;
 }
 
 // All model variants of one tile configuration (mode as in Cfg; the drive
