@@ -138,11 +138,18 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
     const NoiseKey nz = ONE ? ta.one.noise : I->noise;
     const int p_shared = ONE ? ta.one.p_shared : 0;
     const float2 ax2 = f2(q.ax, q.ax), ay2 = f2(q.ay, q.ay);
-    const float cg = q.g, cgx = q.gx, cgr = q.gr, cih = q.inv_hbar;
-    const float hR = q.half_R, hgc = q.half_gc, cR = q.R_, cgam = q.gamma_r, dt = q.dt;
+    // real coefficients as pairs: the real-valued terms (density, local
+    // term, gain, reservoir) of a micro-tile row's two columns go through the
+    // packed FP32x2 instructions together
+    const float2 cg2 = f2(q.g, q.g), cgx2 = f2(q.gx, q.gx), cgr2 = f2(q.gr, q.gr);
+    const float2 cih2 = f2(q.inv_hbar, q.inv_hbar), a02 = f2(q.a0, q.a0);
+    const float2 hR2 = f2(q.half_R, q.half_R), nhgc2 = f2(-q.half_gc, -q.half_gc);
+    const float2 ncR2 = f2(-q.R_, -q.R_), ncgam2 = f2(-q.gamma_r, -q.gamma_r);
+    const float dt = q.dt;
     const float2 tx2 = f2(q.tx, q.tx), nty2 = f2(-q.ty, -q.ty);
     const float2 dg2 = f2(2.f * (q.ty - q.tx), 2.f * (q.ty - q.tx));
-    const float2 txy2 = f2(q.txy, q.txy), ntxy2 = f2(-q.txy, -q.txy);
+    const float2 m12 = f2(-1.f, -1.f);
+    const float txy = q.txy;
     const float dt6 = dt / 6.0f;
     const int xp = cc.kx * C::TX;
     const int foff = xp & 3;
@@ -151,11 +158,22 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
     const float* Pb = p_buf(b);
     const float* Vb = POT ? v_buf(b) : nullptr;
 
+    // complex values [row][column][component]; real fields as pairs over the
+    // row's two columns, [row][component].  n0 and P are read again from the
+    // tile's shared n and P boxes (which no stage overwrites) where they are
+    // used, which keeps the register budget of 16 warps per CTA.
     float2 p0[MR][2][2], yc[MR][2][2], acc[MR][2][2];
-    float n0[MR][2][2], nc[MR][2][2], na[MR][2][2], Pv[MR][2][2], Vv[MR][2];
+    float2 nc[MR][2], na[MR][2], Vv[MR];
     bool ins[MR][2];
     const int gx0 = xp - HALO + c0;
     const int gy0 = cc.ky * C::TY - 3 + r0;
+    // foff + c0 is even and a plane holds an even number of floats: the pair
+    // of a row is one 8-byte load
+    auto ld2 = [&](const float* p, int j) {
+      return *reinterpret_cast<const float2*>(&p[(r0 + j) * C::FW + foff + c0]);
+    };
+    auto N0 = [&](int j, int c) { return ld2(Nb + c * C::F_PLANE, j); };
+    auto PV = [&](int j, int c) { return ld2(Pb + (p_shared ? 0 : c) * C::F_PLANE, j); };
 #pragma unroll
     for (int j = 0; j < MR; ++j) {
 #pragma unroll
@@ -164,22 +182,19 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
             *reinterpret_cast<const float4*>(&P0[c * C::PSI_PLANE + (r0 + j + 1) * C::PW + c0 + 2]);
         p0[j][0][c] = f2(v.x, v.y);
         p0[j][1][c] = f2(v.z, v.w);
+        yc[j][0][c] = p0[j][0][c];
+        yc[j][1][c] = p0[j][1][c];
       }
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const int gx = gx0 + i, gy = gy0 + j;
         ins[j][i] = PER || ((g.bc_x == BC_PERIODIC || (gx >= 0 && gx < g.nx)) &&
                             (g.bc_y == BC_PERIODIC || (gy >= 0 && gy < g.ny)));
-        const int fi = (r0 + j) * C::FW + foff + c0 + i;
-        Vv[j][i] = POT ? fmaf(Vb[fi], cih, q.a0) : q.a0;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          yc[j][i][c] = p0[j][i][c];
-          n0[j][i][c] = Nb[c * C::F_PLANE + fi];
-          nc[j][i][c] = n0[j][i][c];
-          Pv[j][i][c] = Pb[(p_shared ? 0 : c) * C::F_PLANE + fi];
-        }
       }
+      // the stencil's diagonal a0 rides with the local potential
+      Vv[j] = POT ? __ffma2_rn(ld2(Vb, j), cih2, a02) : a02;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) nc[j][c] = N0(j, c);
     }
 
 #pragma unroll
@@ -234,64 +249,65 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
         return yc[jj - 1][ii][c];
       };
       float2 ny[MR][2][2];
-      float nn[MR][2][2];
+      float2 nn[MR][2];
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
+        const int jj = j + 1;
+        // |psi_c|^2 of the row's two sites, per component
+        float2 dens[2];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int jj = j + 1;
-          float dens[2];
+        for (int c = 0; c < 2; ++c) {
+          dens[c].x = fmaf(yc[j][0][c].x, yc[j][0][c].x, yc[j][0][c].y * yc[j][0][c].y);
+          dens[c].y = fmaf(yc[j][1][c].x, yc[j][1][c].x, yc[j][1][c].y * yc[j][1][c].y);
+        }
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const float2 Cc = yc[j][i][c];
-            dens[c] = fmaf(Cc.x, Cc.x, Cc.y * Cc.y);
-          }
+        for (int c = 0; c < 2; ++c) {
+          const int o = 1 - c;
+          // a0 + V/hbar + g|psi_c|^2 + g_x|psi_o|^2 + g_r n_c and
+          // (R n_c - gamma_c)/2 for both sites
+          float2 loc = __ffma2_rn(cg2, dens[c], Vv[j]);
+          loc = __ffma2_rn(cgx2, dens[o], loc);
+          loc = __ffma2_rn(cgr2, nc[j][c], loc);
+          const float2 G = __ffma2_rn(hR2, nc[j][c], nhgc2);
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int o = 1 - c;
+          for (int i = 0; i < 2; ++i) {
             const float2 Cc = yc[j][i][c];
             const float2 E = at(jj, i + 1, c), W = at(jj, i - 1, c);
             const float2 N = at(jj + 1, i, c), S = at(jj - 1, i, c);
             float2 H = __fmul2_rn(ay2, __fadd2_rn(N, S));
             H = __ffma2_rn(ax2, __fadd2_rn(E, W), H);
-            const float ncur = nc[j][i][c];
-            float loc = fmaf(cg, dens[c], Vv[j][i]);
-            loc = fmaf(cgx, dens[o], loc);
-            loc = fmaf(cgr, ncur, loc);
-            H = __ffma2_rn(f2(loc, loc), Cc, H);
+            const float li = i ? loc.y : loc.x;
+            H = __ffma2_rn(f2(li, li), Cc, H);
             if (TETM) {
+              // tx (E+W-2C) - ty (N+S-2C) = tx (E+W) - ty (N+S) + 2 (ty - tx) C
+              // of the other component, accumulated into H
               const float2 Co = yc[j][i][o];
               const float2 Eo = at(jj, i + 1, o), Wo = at(jj, i - 1, o);
               const float2 No = at(jj + 1, i, o), So = at(jj - 1, i, o);
+              H = __ffma2_rn(tx2, __fadd2_rn(Eo, Wo), H);
+              H = __ffma2_rn(nty2, __fadd2_rn(No, So), H);
+              H = __ffma2_rn(dg2, Co, H);
+              // Q = NE - NW - SE + SW of the other component; J_+ adds
+              // -i txy Q, J_- adds +i txy Q
               const float2 NEo = at(jj + 1, i + 1, o), NWo = at(jj + 1, i - 1, o);
               const float2 SEo = at(jj - 1, i + 1, o), SWo = at(jj - 1, i - 1, o);
-              // tx (E+W-2C) - ty (N+S-2C) = tx (E+W) - ty (N+S) + 2 (ty - tx) C
-              float2 D = __fmul2_rn(tx2, __fadd2_rn(Eo, Wo));
-              D = __ffma2_rn(nty2, __fadd2_rn(No, So), D);
-              D = __ffma2_rn(dg2, Co, D);
-              // X = txy (NE - NW - SE + SW) = txy (NE + SW) - txy (NW + SE)
-              const float2 X = __ffma2_rn(txy2, __fadd2_rn(NEo, SWo),
-                                          __fmul2_rn(ntxy2, __fadd2_rn(NWo, SEo)));
-              // J_+ : D - i X ;  J_- : D + i X
-              if (c == 0) {
-                H.x += D.x + X.y;
-                H.y += D.y - X.x;
-              } else {
-                H.x += D.x - X.y;
-                H.y += D.y + X.x;
-              }
+              const float2 Q = __ffma2_rn(m12, __fadd2_rn(NWo, SEo), __fadd2_rn(NEo, SWo));
+              const float sx = c == 0 ? txy : -txy;
+              H.x = fmaf(sx, Q.y, H.x);
+              H.y = fmaf(-sx, Q.x, H.y);
             }
-            const float G = fmaf(hR, ncur, -hgc);
+            const float Gi = i ? G.y : G.x;
             float2 K;
-            K.x = fmaf(G, Cc.x, H.y);
-            K.y = fmaf(G, Cc.y, -H.x);
+            K.x = fmaf(Gi, Cc.x, H.y);
+            K.y = fmaf(Gi, Cc.y, -H.x);
             acc[j][i][c] = s == 0 ? K : __ffma2_rn(w2, K, acc[j][i][c]);
-            const float Kn = fmaf(-fmaf(cR, dens[c], cgam), ncur, Pv[j][i][c]);
-            na[j][i][c] = s == 0 ? Kn : fmaf(w, Kn, na[j][i][c]);
             ny[j][i][c] = __ffma2_rn(cs2, K, p0[j][i][c]);
             if (!PER && !ins[j][i]) ny[j][i][c] = f2(0.f, 0.f);
-            nn[j][i][c] = fmaf(cs, Kn, n0[j][i][c]);
           }
+          // K_n = P - (gamma_r + R|psi_c|^2) n_c for both sites
+          const float2 Kn = __ffma2_rn(__ffma2_rn(ncR2, dens[c], ncgam2), nc[j][c], PV(j, c));
+          na[j][c] = s == 0 ? Kn : __ffma2_rn(w2, Kn, na[j][c]);
+          nn[j][c] = __ffma2_rn(cs2, Kn, N0(j, c));
         }
       }
       if (s < 3) {
@@ -301,8 +317,7 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
           for (int c = 0; c < 2; ++c) {
             yc[j][0][c] = ny[j][0][c];
             yc[j][1][c] = ny[j][1][c];
-            nc[j][0][c] = nn[j][0][c];
-            nc[j][1][c] = nn[j][1][c];
+            nc[j][c] = nn[j][c];
             if (j == 0 || j == MR - 1)
               *reinterpret_cast<float4*>(&dst[c * C::PSI_PLANE + (r0 + j + 1) * C::PW + c0 + 2]) =
                   make_float4(ny[j][0][c].x, ny[j][0][c].y, ny[j][1][c].x, ny[j][1][c].y);
@@ -315,16 +330,15 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
     // psi' = psi0 + (K1 + 2K2 + 2K3 + K4) dt/6 (+ noise), both components
     const float2 d62 = f2(dt6, dt6);
     float2 o[MR][2][2];
-    float on[MR][2][2];
+    float2 on[MR][2];
 #pragma unroll
     for (int j = 0; j < MR; ++j)
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int c = 0; c < 2; ++c) {
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          o[j][i][c] = __ffma2_rn(d62, acc[j][i][c], p0[j][i][c]);
-          on[j][i][c] = fmaf(dt6, na[j][i][c], n0[j][i][c]);
-        }
+        for (int i = 0; i < 2; ++i) o[j][i][c] = __ffma2_rn(d62, acc[j][i][c], p0[j][i][c]);
+        on[j][c] = __ffma2_rn(d62, na[j][c], N0(j, c));
+      }
     if (nz.on) {
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
@@ -337,8 +351,8 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
           float2 xp_, xm_;
           float s0 = nz.scale, s1 = nz.scale;
           if (nz.twa) {
-            s0 = nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var, n0[j][i][0]);
-            s1 = nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var, n0[j][i][1]);
+            s0 = nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var, i ? N0(j, 0).y : N0(j, 0).x);
+            s1 = nz_wigner_scale(nz.R, nz.gc, nz.kw, nz.var, i ? N0(j, 1).y : N0(j, 1).x);
           }
           nz_site2(nz.seed, nz.instance, step, site, s0, s1, xp_, xm_, true);
           o[j][i][0].x = o[j][i][0].x + xp_.x;
@@ -368,13 +382,13 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
           if (lo && hi) {
             *reinterpret_cast<float4*>(po) =
                 make_float4(o[j][0][c].x, o[j][0][c].y, o[j][1][c].x, o[j][1][c].y);
-            *reinterpret_cast<float2*>(pn) = f2(on[j][0][c], on[j][1][c]);
+            *reinterpret_cast<float2*>(pn) = on[j][c];
           } else if (lo) {
             po[0] = o[j][0][c];
-            pn[0] = on[j][0][c];
+            pn[0] = on[j][c].x;
           } else if (hi) {
             po[1] = o[j][1][c];
-            pn[1] = on[j][1][c];
+            pn[1] = on[j][c].y;
           }
         }
       }
@@ -391,7 +405,7 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             store_with_ghosts(psi_out + c * g.plane, g, gx, gy, o[j][i][c]);
-            store_with_ghosts(n_out + c * g.plane, g, gx, gy, on[j][i][c]);
+            store_with_ghosts(n_out + c * g.plane, g, gx, gy, i ? on[j][c].y : on[j][c].x);
           }
         }
       }
