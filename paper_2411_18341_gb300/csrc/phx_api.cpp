@@ -177,11 +177,18 @@ std::map<std::tuple<int, int, int, int, int, int, int>, int> g_tune;
 bool encode_maps(phx_handle* h);
 TileArgs tile_args(phx_handle* h, int inj);
 
+// Whether a reservoir handle with a drive steps on the TMA-fed kernel: its
+// tile is autotuned (among the configurations with that variant) or fixed to
+// one of them.
+bool drive_reservoir_tile(const phx_handle* h) {
+  return h->p.tile == 0 || tma_has_drive_reservoir(h->p.tile);
+}
+
 // One persistent TMA-fed step launch in configuration cfg.
 cudaError_t launch_tma(phx_handle* h, int cfg, const TileArgs& ta, int grid) {
   if (spinor_tma_cfg(cfg))
     return launch_rk4_tma_spinor(cfg, h->has_V, periodic(h->p), h->m.tetm, ta, h->stream, grid);
-  const int mode = h->m.reservoir ? 1 : (h->has_E ? 2 : 0);
+  const int mode = h->m.reservoir ? (h->has_E ? 3 : 1) : (h->has_E ? 2 : 0);
   return launch_rk4_tma_f32(cfg, mode, h->has_V, periodic(h->p), ta, h->stream, grid);
 }
 
@@ -253,8 +260,11 @@ phx_status autotune(phx_handle* h) {
                               TILE_64x64,    TILE_64x32,      TILE_64x32_M2_2,
                               TILE_64x32_M4_2, TILE_64x32_M4_2_MS};
   const int spinor_cands[] = {TILE_SPINOR_64x24, TILE_SPINOR_64x16, TILE_SPINOR_64x32};
+  // reservoir and drive: the configurations with that variant
+  const int drive_res_cands[] = {TILE_64x48, TILE_64x32, TILE_64x48_M2};
   const bool sp = h->m.ncomp == 2;
-  const int* cands = sp ? spinor_cands : scalar_cands;
+  const bool drive_res = !sp && h->m.reservoir && h->has_E;
+  const int* cands = sp ? spinor_cands : (drive_res ? drive_res_cands : scalar_cands);
   cudaEvent_t e0, e1;
   PHX_CK(h, cudaEventCreate(&e0));
   PHX_CK(h, cudaEventCreate(&e1));
@@ -278,7 +288,7 @@ phx_status autotune(phx_handle* h) {
   }
   // three interleaved rounds; each configuration keeps its fastest round
   // (time per step)
-  const int nc = sp ? 3 : (saved ? 8 : 7);
+  const int nc = (sp || drive_res) ? 3 : (saved ? 8 : 7);
   float cfg_ms[8];
   for (int c = 0; c < nc; ++c) cfg_ms[c] = 1e30f;
   for (int round = 0; round < 3; ++round) {
@@ -341,8 +351,8 @@ phx_status autotune(phx_handle* h) {
 // Fill the handle's instance descriptor for the current tile configuration
 // and queue its upload on the handle's stream.
 bool encode_maps(phx_handle* h) {
-  // the TMA-fed drive variant: single-component fields without reservoir
-  void* E = (h->has_E && h->m.ncomp == 1 && !h->m.reservoir) ? h->E : nullptr;
+  // the TMA-fed drive variants: single-component fields
+  void* E = (h->has_E && h->m.ncomp == 1) ? h->E : nullptr;
   if (!fill_tile_inst(h->h_inst, h->p, h->geo, h->psi, h->n, h->P, h->has_V ? h->V : nullptr,
                       h->tile_cfg, E))
     return false;
@@ -640,7 +650,9 @@ phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
   if (!h) return fail(nullptr, PHX_EINVAL, "handle is NULL");
   DeviceGuard dg(h->device);
   if (!E_plus) {
+    if (h->has_E && h->p.tile == 0) h->tuned = false;
     h->has_E = false;
+    h->maps_ok = false;
     return PHX_OK;
   }
   const Geometry& g = h->geo;
@@ -664,6 +676,9 @@ phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
   }
   PHX_CK(h, launch_split_complex(stage, h->E, (int)h->esize, planes, g, h->stream));
   h->E_stride = planes == 2 ? 2 * g.plane : 0;
+  // a drive changes the kernel variant (and, with a reservoir, the tile
+  // configurations that have it): an autotuned handle is tuned again
+  if (!h->has_E && h->p.tile == 0) h->tuned = false;
   h->has_E = true;
   h->maps_ok = false;
   return PHX_OK;
@@ -733,8 +748,10 @@ phx_status phx_step_n(phx_handle* h, int64_t nsteps) {
       a.clock = h->clock;
       a.parity = h->parity;
       a.inject_timeout = inj;
-      // drive: TMA-fed for a scalar field without reservoir, else generic
-      const bool drive_ok = !h->has_E || (h->m.ncomp == 1 && !h->m.reservoir);
+      // drive: TMA-fed for a scalar field (with a reservoir only in the
+      // configurations that have that variant), else generic
+      const bool drive_ok =
+          !h->has_E || (h->m.ncomp == 1 && (!h->m.reservoir || drive_reservoir_tile(h)));
       if (h->tile_cfg != TILE_GENERIC && drive_ok &&
           (h->m.ncomp == 1 || spinor_tma_cfg(h->tile_cfg))) {
         if (!h->tuned) {
@@ -956,7 +973,8 @@ phx_status phx_debug_inject(uint32_t mask) {
 
 int32_t phx_tile(const phx_handle* h) {
   if (!h) return 0;
-  const bool drive_generic = h->has_E && (h->m.ncomp == 2 || h->m.reservoir);
+  const bool drive_generic =
+      h->has_E && (h->m.ncomp == 2 || (h->m.reservoir && !drive_reservoir_tile(h)));
   return (drive_generic && h->m.precision == 32) ? TILE_GENERIC : h->tile_cfg;
 }
 

@@ -60,6 +60,10 @@ cudaError_t launch_rk4_tma_f32(int tile_cfg, int mode, bool pot, bool per,
 
 bool tma_has_multistep(int tile_cfg) { return tile_cfg == TILE_64x32_M4_2_MS; }
 
+bool tma_has_drive_reservoir(int tile_cfg) {
+  return tile_cfg == TILE_64x48 || tile_cfg == TILE_64x32 || tile_cfg == TILE_64x48_M2;
+}
+
 cudaError_t launch_rk4_tma_f32_ms(int tile_cfg, int mode, bool pot, bool per,
                                   const TileArgs& ta, cudaStream_t s, int grid) {
   if (tile_cfg == TILE_64x32_M4_2_MS) return launch_tma_cfg7_ms(mode, pot, per, ta, s, grid);

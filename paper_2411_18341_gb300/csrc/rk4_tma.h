@@ -143,6 +143,9 @@ cudaError_t launch_tma_cfg7(int mode, bool pot, bool per, bool one, const TileAr
 // Several steps per launch (single instance, mode 0 or 1; ta.done zeroed,
 // ta.ms_steps, ta.tiles_y set).  Configurations with such a variant:
 bool tma_has_multistep(int tile_cfg);
+// Configurations with the reservoir-and-drive variant (mode 3: one CTA per
+// SM, two input buffers of six planes within shared memory).
+bool tma_has_drive_reservoir(int tile_cfg);
 cudaError_t launch_rk4_tma_f32_ms(int tile_cfg, int mode, bool pot, bool per,
                                   const TileArgs& ta, cudaStream_t s, int grid);
 cudaError_t launch_tma_cfg7_ms(int mode, bool pot, bool per, const TileArgs& ta, cudaStream_t s,

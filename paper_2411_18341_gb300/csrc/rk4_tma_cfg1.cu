@@ -4,6 +4,8 @@
 
 namespace phx {
 
+static_assert(!tma::has_mode3<4, 16, 1>(), "tma_has_drive_reservoir(1)");
+
 cudaError_t launch_tma_cfg1(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid) {
   return tma::launch_variants<4, 16, 1>(mode, pot, per, one, ta, s, grid);

@@ -115,7 +115,8 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // MODE: 0 = no reservoir, 1 = reservoir (n and P planes), 2 = coherent
-// drive without reservoir (Re E and Im E planes in the n and P slots).
+// drive without reservoir (Re E and Im E planes in the n and P slots),
+// 3 = reservoir and coherent drive (n, P, Re E, Im E planes).
 template <int MODE, bool POT, int MR, int WY, int MINB = 1>
 struct Cfg {
   static constexpr int RW = 64;            // region (ring-3) columns: one warp x 2 cols
@@ -125,7 +126,7 @@ struct Cfg {
   static constexpr int PH = RH + 2;        // psi smem rows: ring, region, ring
   static constexpr int FW = RW + 4;        // n / P / V smem row (4-float aligned box)
   static constexpr int NT = 32 * WY;
-  static constexpr int NF = (MODE != 0 ? 2 : 0) + (POT ? 1 : 0);
+  static constexpr int NF = (MODE == 3 ? 4 : (MODE != 0 ? 2 : 0)) + (POT ? 1 : 0);
   static constexpr int PSI_BYTES = ((PH * PW * 8) + 127) / 128 * 128;
   static constexpr int F_BYTES = ((RH * FW * 4) + 127) / 128 * 128;
   static constexpr int BUF_BYTES = PSI_BYTES + NF * F_BYTES;
@@ -167,7 +168,7 @@ struct Cfg {
 template <int MODE, bool POT, bool PER, bool ONE, int MR, int WY, int MINB, bool MS = false>
 __global__ void __launch_bounds__(32 * WY, MINB)
 rk4_f32_tma(const TileArgs ta) {
-  constexpr bool RES = MODE == 1, DRV = MODE == 2;
+  constexpr bool RES = MODE == 1 || MODE == 3, DRV = MODE == 2 || MODE == 3;
   using C = Cfg<MODE, POT, MR, WY, MINB>;
   static_assert(!MS || (ONE && !DRV && C::NBUF == 2), "multi-step: single instance, no drive");
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -464,9 +465,10 @@ rk4_f32_tma(const TileArgs ta) {
     float2* P0 = psi_buf(b);
     const float* Nb = RES ? f_buf(b, 0) : nullptr;
     const float* Pb = RES ? f_buf(b, 1) : nullptr;
-    const float* Erb = DRV ? f_buf(b, 0) : nullptr;
-    const float* Eib = DRV ? f_buf(b, 1) : nullptr;
-    const float* Vb = POT ? f_buf(b, MODE != 0 ? 2 : 0) : nullptr;
+    // planes in load order: n, P (reservoir), Re E, Im E (drive), V
+    const float* Erb = DRV ? f_buf(b, RES ? 2 : 0) : nullptr;
+    const float* Eib = DRV ? f_buf(b, RES ? 3 : 1) : nullptr;
+    const float* Vb = POT ? f_buf(b, C::NF - 1) : nullptr;
 
     // Registers: psi0, current stage value, accumulator (+ reservoir).  Real
     // fields hold the micro-tile row's two columns as one pair (.x, .y).
@@ -794,8 +796,15 @@ cudaError_t launch_variants_ms(int mode, bool pot, bool per, const TileArgs& ta,
   return cudaErrorInvalidValue;
 }
 
+// Whether a configuration has the reservoir-and-drive variant (mode 3): one
+// CTA per SM (its registers) and two input buffers within shared memory.
+template <int MR, int WY, int MINB>
+constexpr bool has_mode3() {
+  return MINB == 1 && Cfg<3, true, MR, WY, MINB>::SMEM <= 227 * 1024;
+}
+
 // All model variants of one tile configuration (mode as in Cfg; the drive
-// variant exists for single instances only).
+// variants exist for single instances only).
 template <int MR, int WY, int MINB>
 cudaError_t launch_variants(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid) {
@@ -807,6 +816,13 @@ cudaError_t launch_variants(int mode, bool pot, bool per, bool one, const TileAr
   if (pot) return launch_cfg<M_, true, false, ONE_, MR, WY, MINB>(ta, s, grid);         \
   return launch_cfg<M_, false, false, ONE_, MR, WY, MINB>(ta, s, grid);
   if (one) {
+    if (mode == 3) {
+      if constexpr (has_mode3<MR, WY, MINB>()) {
+        PHX_TMA_V(3, true)
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    }
     if (mode == 2) {
       PHX_TMA_V(2, true)
     }
@@ -815,7 +831,7 @@ cudaError_t launch_variants(int mode, bool pot, bool per, bool one, const TileAr
     }
     PHX_TMA_V(0, true)
   }
-  if (mode == 2) return cudaErrorInvalidValue;
+  if (mode >= 2) return cudaErrorInvalidValue;
   if (mode == 1) {
     PHX_TMA_V(1, false)
   }

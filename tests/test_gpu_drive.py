@@ -71,6 +71,8 @@ def run_driven(d, prec, E, shared, steps, tile=0, t0=3.7, step0=50):
 
 
 KINDS = ["loss", "reservoir", "spinor_tetm", "spinor_res_tetm"]
+# tile configurations of the TMA-fed kernel with the reservoir-and-drive variant
+DRIVE_RES_TILES = (2, 3, 4)
 
 
 @pytest.mark.parametrize("prec", [64, 32])
@@ -104,7 +106,7 @@ def test_drive_changes_the_state_and_can_be_removed(prec):
     u_psi, _ = gp.run(psi0, n0, P, V, gp.Params(**d), 9)
     assert rel_l2(u_psi, o_psi) > 100 * TOL[prec]
     if prec == 32:
-        assert m.phx_tile(h) == 9
+        assert m.phx_tile(h) in DRIVE_RES_TILES
     m.phx_set_drive(h, None)
     real, cplx = (np.float64, np.complex128) if prec == 64 else (np.float32, np.complex64)
     m.phx_set_state(h, np.ascontiguousarray(psi0, cplx), np.ascontiguousarray(n0, real))
@@ -159,3 +161,61 @@ def test_drive_tma_with_truncated_wigner_noise(tile):
     h, (g_psi, _), (o_psi, _) = run_driven(d, 32, E, False, steps=9, tile=tile)
     assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
     assert phx().phx_tile(h) in TMA_SCALAR_TILES
+
+
+@pytest.mark.parametrize("tile", [0, 2, 3, 4])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1), (0, 1)])
+def test_drive_reservoir_tma_kernel(tile, bc):
+    """FP32 scalar field with reservoir and drive: the TMA-fed kernel stages
+    n, P, Re E, Im E and V per tile (configurations 2, 3, 4), ragged grid."""
+    m = phx()
+    d = drive_model("reservoir", 131, 77, bc=bc)
+    E = smooth_field(1, 77, 131, 10, 0.4)
+    h, (g_psi, g_n), (o_psi, o_n) = run_driven(d, 32, E, False, steps=11, tile=tile)
+    assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
+    assert rel_l2(g_n, o_n) <= 1e-4, rel_l2(g_n, o_n)
+    assert m.phx_tile(h) in DRIVE_RES_TILES
+    if tile:
+        assert m.phx_tile(h) == tile
+
+
+@pytest.mark.parametrize("tile", [1, 5, 6, 7])
+def test_drive_reservoir_fixed_tile_without_variant(tile):
+    """A fixed tile configuration without the reservoir-and-drive variant
+    steps on the generic kernel: same results, reported as tile 9."""
+    m = phx()
+    d = drive_model("reservoir", 97, 66, bc=(1, 1))
+    E = smooth_field(1, 66, 97, 11, 0.4)
+    h, (g_psi, g_n), (o_psi, o_n) = run_driven(d, 32, E, False, steps=7, tile=tile)
+    assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
+    assert rel_l2(g_n, o_n) <= 1e-4, rel_l2(g_n, o_n)
+    assert m.phx_tile(h) == 9
+
+
+def test_drive_set_after_tuning_retunes():
+    """A reservoir handle tuned without a drive (any configuration) is tuned
+    again when a drive is set, among the configurations with that variant;
+    the trajectory (undriven steps, then driven ones) matches the oracle."""
+    m = phx()
+    d = drive_model("reservoir", 301, 157, bc=(1, 1))
+    psi0, n0, P, V = synth.random_state(1, 157, 301, 13, amp=0.6, smooth=True)
+    psi0, n0, P = (rounded(x, 32) for x in (psi0, n0, P))
+    E = rounded(smooth_field(1, 157, 301, 12, 0.4), 32)
+    h = m.phx_create(m.params_from_dict(d, precision=32))
+    m.phx_set_pump(h, np.ascontiguousarray(P[0], np.float32))
+    m.phx_set_state(h, np.ascontiguousarray(psi0, np.complex64),
+                    np.ascontiguousarray(n0, np.float32))
+    m.phx_step_n(h, 5)
+    assert m.phx_tile(h) in TMA_SCALAR_TILES + [8]
+    m.phx_set_drive(h, np.ascontiguousarray(E[0], np.complex64))
+    m.phx_step_n(h, 6)
+    assert m.phx_tile(h) in DRIVE_RES_TILES
+    g_psi, g_n = get_state(h, 32)
+    p = gp.Params(**d)
+    o_psi, o_n = gp.run(psi0, n0, P, None, p, 5)
+    t5 = 0.0
+    for _ in range(5):
+        t5 += d["dt"]
+    o_psi, o_n = gp.run(o_psi, o_n, P, None, p, 6, step0=5, E=E, t0=t5)
+    assert rel_l2(g_psi, o_psi) <= 1e-4, rel_l2(g_psi, o_psi)
+    assert rel_l2(g_n, o_n) <= 1e-4, rel_l2(g_n, o_n)
