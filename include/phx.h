@@ -89,7 +89,9 @@ typedef struct phx_params {
                                 changing it, synchronising the stream once; the
                                 choice is cached per grid shape), 1..7 = a fixed
                                 shared-memory region and thread shape of the
-                                TMA-fed persistent kernel, 9 = generic kernel;
+                                TMA-fed persistent kernel, 8 = configuration 7
+                                running up to 128 steps per launch (single
+                                handles without drive), 9 = generic kernel;
                                 for the generic kernels of the FP32 spinor +
                                 reservoir + TE-TM and FP64 scalar reservoir
                                 models 10..12 select other tile shapes */
@@ -175,10 +177,11 @@ phx_status phx_set_potential(phx_handle* h, const void* V, int on_device);
  * E_- = E_+), complex interleaved, meV, one ny x nx plane per component
  * (Eq. PULSE_psi, Sec. V); the step adds E_c(r) exp(-i drive_omega t) to the
  * bracket.  E_plus = NULL removes the drive.  With a drive set, the FP32 scalar
- * field without reservoir keeps the TMA-fed kernel; FP32 fields with a
- * reservoir or two components step on the generic kernel (phx_tile reports
- * 9).  The energy and residual reductions stay those of the undriven
- * equations. */
+ * field keeps the TMA-fed kernel (with a reservoir: configurations 2, 3 and 4;
+ * an autotuned handle is tuned again when a drive is set or removed, a fixed
+ * tile without that variant steps on the generic kernel); FP32 fields with two
+ * components step on the generic kernel (phx_tile reports 9).  The energy and
+ * residual reductions stay those of the undriven equations. */
 phx_status phx_set_drive(phx_handle* h, const void* E_plus, const void* E_minus,
                          int on_device);
 
