@@ -170,16 +170,17 @@ phx_status autotune(phx_batch* b) {
   cudaEvent_t e0, e1;
   PHX_BCK(b, cudaEventCreate(&e0));
   PHX_BCK(b, cudaEventCreate(&e1));
-  // three interleaved rounds; each configuration keeps its fastest round
+  // five interleaved rounds of ten launches; each configuration keeps its
+  // fastest round
   const int nc = (int)(sizeof cands / sizeof cands[0]);
   float cfg_ms[sizeof cands / sizeof cands[0]];
   for (int c = 0; c < nc; ++c) cfg_ms[c] = 1e30f;
-  for (int round = 0; round < 3; ++round) {
+  for (int round = 0; round < 5; ++round) {
     for (int c = 0; c < nc; ++c) {
       if (build_tables(b, cands[c]) != PHX_OK) continue;
       cudaError_t e = launch_step(b, b->cur, b->parity, b->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-      for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+      for (int i = 0; i < 10 && e == cudaSuccess; ++i)
         e = launch_step(b, b->cur, b->parity, b->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);

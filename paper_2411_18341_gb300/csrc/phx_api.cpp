@@ -286,12 +286,14 @@ phx_status autotune(phx_handle* h) {
       PHX_CK(h, cudaMemcpyAsync(static_cast<char*>(saved) + psi_bytes, h->n[h->cur], n_bytes,
                                 cudaMemcpyDeviceToDevice, h->stream));
   }
-  // three interleaved rounds; each configuration keeps its fastest round
+  // five interleaved rounds of ten launches (configurations within a few per
+  // cent of each other then come out in the same order from run to run);
+  // each configuration keeps its fastest round
   // (time per step)
   const int nc = (sp || drive_res) ? 3 : (saved ? 8 : 7);
   float cfg_ms[8];
   for (int c = 0; c < nc; ++c) cfg_ms[c] = 1e30f;
-  for (int round = 0; round < 3; ++round) {
+  for (int round = 0; round < 5; ++round) {
     for (int c = 0; c < nc; ++c) {
       const int cfg = cands[c];
       h->tile_cfg = cfg;
@@ -305,7 +307,7 @@ phx_status autotune(phx_handle* h) {
       auto launch = [&]() {
         return ms_n ? launch_ms(h, ms_n, 0, false) : launch_tma(h, cfg, ta, grid);
       };
-      const int reps = ms_n ? 2 : 5;
+      const int reps = ms_n ? 4 : 10;
       const int per_rep = ms_n ? ms_n : 1;
       cudaError_t e = cudaSuccess;
       for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch();
