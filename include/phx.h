@@ -334,6 +334,17 @@ phx_status phx_batch_set_pump(phx_batch* b, int32_t i, const void* P, int on_dev
 /* V = NULL removes the member's potential; stepping requires that either all
  * members or none have a potential (ESTATE otherwise). */
 phx_status phx_batch_set_potential(phx_batch* b, int32_t i, const void* V, int on_device);
+/* Copy member i's coherent drive amplitude E(r) (complex interleaved, meV,
+ * one ny_i x nx_i plane; Eq. PULSE_psi, Sec. V): the member's step adds
+ * E(r) exp(-i drive_omega_i t_i) to the bracket, with its own frequency
+ * params[i].drive_omega and its own FP64 time.  Once any member has a drive,
+ * every member steps on the drive variant (members without one add a zero
+ * plane; the result equals the undriven step).  E = NULL sets member i's
+ * drive to zero.  With a reservoir the tile configuration is 2, 3 or 4
+ * (autotuned among them; a batch created with another fixed configuration
+ * gets EINVAL from phx_batch_step_n).  The drive planes (8 bytes per site of
+ * every member) are allocated on the first call. */
+phx_status phx_batch_set_drive(phx_batch* b, int32_t i, const void* E, int on_device);
 phx_status phx_batch_set_state(phx_batch* b, int32_t i, const void* psi, const void* n,
                                int on_device);
 phx_status phx_batch_get_state(phx_batch* b, int32_t i, void* psi, void* n, int on_device);

@@ -109,6 +109,8 @@ _SIGS = {
     "phx_batch_set_pump": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
     "phx_batch_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                ctypes.c_int]),
+    "phx_batch_set_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_int]),
     "phx_batch_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_int]),
     "phx_batch_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
@@ -476,6 +478,13 @@ def phx_batch_set_potential(b, i, V):
     nx, ny = b.sizes[i]
     a, dev, k = _ptr(V, np.float32, False, nx * ny)
     _bcheck(lib().phx_batch_set_potential(b.ptr, i, a, dev), b)
+
+
+def phx_batch_set_drive(b, i, E):
+    """E None sets member i's drive to zero."""
+    nx, ny = b.sizes[i]
+    a, dev, k = _ptr(E, np.float32, True, nx * ny)
+    _bcheck(lib().phx_batch_set_drive(b.ptr, i, a, dev if a is not None else 0), b)
 
 
 def phx_batch_set_state(b, i, psi, n=None):

@@ -26,7 +26,11 @@ struct phx_batch {
   std::vector<Geometry> geo;
   std::vector<void*> psi[2], n[2], P, V;
   std::vector<char> has_V;
+  std::vector<void*> E;          // per member: Re and Im planes of the drive
+  void* E_pool = nullptr;        // every member's drive planes, once any is set
+  bool has_E = false;            // the drive variant runs (undriven members: zeros)
   bool reservoir = false;
+  bool tile_fixed = false;       // params[0].tile named the configuration
   void* pool = nullptr;          // one allocation for every member's fields
   std::vector<void*> V_owned;    // potentials are allocated on demand
   TileInst* d_inst = nullptr;
@@ -80,6 +84,7 @@ void bfree(phx_batch* b) {
   for (void* v : b->V_owned)
     if (v) cudaFree(v);
   if (b->pool) cudaFree(b->pool);
+  if (b->E_pool) cudaFree(b->E_pool);
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_tile_info) cudaFree(b->d_tile_info);
   if (b->clock) cudaFree(b->clock);
@@ -105,7 +110,7 @@ phx_status build_tables(phx_batch* b, int cfg) {
     void* psi[2] = {b->psi[0][i], b->psi[1][i]};
     void* n[2] = {b->n[0][i], b->n[1][i]};
     if (!fill_tile_inst(b->h_inst[i], b->p[i], b->geo[i], psi, n, b->P[i],
-                        b->has_V[i] ? b->V[i] : nullptr, cfg))
+                        b->has_V[i] ? b->V[i] : nullptr, cfg, b->has_E ? b->E[i] : nullptr))
       return bfail(b, PHX_ECUDA, "cuTensorMapEncodeTiled failed");
     b->h_inst[i].tile0 = tile0;
     const int tx = b->h_inst[i].tiles_x, ty = b->h_inst[i].tiles_y;
@@ -158,22 +163,27 @@ cudaError_t launch_step(const phx_batch* b, int cur, int parity, cudaStream_t s)
   bool per = true;
   for (const phx_params& q : b->p)
     per = per && q.bc_x == PHX_BC_PERIODIC && q.bc_y == PHX_BC_PERIODIC;
-  return launch_rk4_tma_f32(b->tile_cfg, b->reservoir ? 1 : 0, b->tables_V, per,
-                            batch_args(b, cur, parity), s, grid);
+  const int mode = b->reservoir ? (b->has_E ? 3 : 1) : (b->has_E ? 2 : 0);
+  return launch_rk4_tma_f32(b->tile_cfg, mode, b->tables_V, per, batch_args(b, cur, parity), s,
+                            grid);
 }
 
 // Time each tile configuration on the batch's own state (a step reads buffer
 // cur and writes cur ^ 1, so repeating it leaves the state intact).
 phx_status autotune(phx_batch* b) {
-  const int cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64, TILE_64x32,
-                       TILE_64x32_M2_2, TILE_64x32_M4_2};
+  const int all_cands[] = {TILE_64x48_M2, TILE_64x64_M2, TILE_64x48, TILE_64x64, TILE_64x32,
+                           TILE_64x32_M2_2, TILE_64x32_M4_2};
+  // reservoir and drive: the configurations with that variant
+  const int drive_res_cands[] = {TILE_64x48, TILE_64x32, TILE_64x48_M2};
+  const bool drive_res = b->reservoir && b->has_E;
+  const int* cands = drive_res ? drive_res_cands : all_cands;
   cudaEvent_t e0, e1;
   PHX_BCK(b, cudaEventCreate(&e0));
   PHX_BCK(b, cudaEventCreate(&e1));
   // five interleaved rounds of ten launches; each configuration keeps its
   // fastest round
-  const int nc = (int)(sizeof cands / sizeof cands[0]);
-  float cfg_ms[sizeof cands / sizeof cands[0]];
+  const int nc = drive_res ? 3 : 7;
+  float cfg_ms[7];
   for (int c = 0; c < nc; ++c) cfg_ms[c] = 1e30f;
   for (int round = 0; round < 5; ++round) {
     for (int c = 0; c < nc; ++c) {
@@ -194,7 +204,7 @@ phx_status autotune(phx_batch* b) {
     }
   }
   float best_ms = 1e30f;
-  int best = TILE_64x48_M2;
+  int best = cands[0];
   for (int c = 0; c < nc; ++c)
     if (cfg_ms[c] < best_ms) {
       best_ms = cfg_ms[c];
@@ -288,10 +298,13 @@ phx_status phx_batch_create(const phx_params* params, int32_t count, phx_batch**
   b->p.assign(params, params + count);
   // params[0].tile fixes the step-kernel configuration (a TMA-fed one);
   // 0 (or any other value) leaves it to the autotuner
-  if (params[0].tile >= TILE_64x64 && params[0].tile <= TILE_64x32_M4_2)
+  if (params[0].tile >= TILE_64x64 && params[0].tile <= TILE_64x32_M4_2) {
     b->tile_cfg = params[0].tile;
+    b->tile_fixed = true;
+  }
   b->h_inst.resize(count);
   b->has_V.assign(count, 0);
+  b->E.assign(count, nullptr);
   b->V.assign(count, nullptr);
   b->V_owned.assign(count, nullptr);
   size_t total = 0;
@@ -389,6 +402,39 @@ phx_status phx_batch_set_potential(phx_batch* b, int32_t i, const void* V, int o
   return PHX_OK;
 }
 
+phx_status phx_batch_set_drive(phx_batch* b, int32_t i, const void* E, int on_device) {
+  phx_status st = check_member(b, i);
+  if (st != PHX_OK) return st;
+  DevGuard dg(b->device);
+  if (!E) {  // a member without drive keeps zero planes
+    if (b->has_E)
+      PHX_BCK(b, cudaMemsetAsync(b->E[i], 0, 2 * (size_t)b->geo[i].plane * 4, b->stream));
+    return PHX_OK;
+  }
+  if (!b->E_pool) {
+    size_t total = 0;
+    std::vector<size_t> off(b->count);
+    for (int j = 0; j < b->count; ++j) {
+      off[j] = total;
+      total += (2 * (size_t)b->geo[j].plane * 4 + 255) & ~size_t(255);
+    }
+    PHX_BCK(b, cudaMalloc(&b->E_pool, total));
+    PHX_BCK(b, cudaMemsetAsync(b->E_pool, 0, total, b->stream));
+    for (int j = 0; j < b->count; ++j) b->E[j] = static_cast<char*>(b->E_pool) + off[j];
+  }
+  // stage the interleaved values (ghost ring filled) in the member's idle
+  // state buffer -- the next step overwrites it -- and split them into the
+  // Re / Im planes the step kernel reads
+  void* stage = b->psi[b->cur ^ 1][i];
+  PHX_BCK(b, upload_field(stage, E, 1, 8, b->geo[i], on_device, b->stream));
+  PHX_BCK(b, launch_split_complex(stage, b->E[i], 4, 1, b->geo[i], b->stream));
+  if (!b->has_E) {
+    b->has_E = true;
+    b->tables_ok = false;
+  }
+  return PHX_OK;
+}
+
 phx_status phx_batch_set_state(phx_batch* b, int32_t i, const void* psi, const void* n,
                                int on_device) {
   phx_status st = check_member(b, i);
@@ -420,6 +466,12 @@ phx_status phx_batch_step_n(phx_batch* b, int64_t nsteps) {
   DevGuard dg(b->device);
   if (any_V(b) && !all_V(b))
     return bfail(b, PHX_ESTATE, "either all members or none must have a potential");
+  if (b->reservoir && b->has_E && b->tile_cfg != 0 && !tma_has_drive_reservoir(b->tile_cfg)) {
+    if (b->tile_fixed)
+      return bfail(b, PHX_EINVAL,
+                   "reservoir with drive: tile configuration needs to be 2, 3 or 4 (or 0)");
+    b->tile_cfg = 0;  // tuned again among the configurations with that variant
+  }
   if (b->tile_cfg == 0) {
     phx_status st = autotune(b);
     if (st != PHX_OK) return st;

@@ -173,7 +173,9 @@ rk4_f32_tma(const TileArgs ta) {
   static_assert(!MS || (ONE && !DRV && C::NBUF == 2), "multi-step: single instance, no drive");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[3];
-  __shared__ float2 s_dph[4];  // drive phase exp(-i omega t_s) / hbar per stage
+  // drive phase exp(-i omega t_s) / hbar per stage: one set for a single
+  // instance; for batches the sets of the current and the next tile
+  __shared__ float2 s_dph[2][4];
   // 128-byte aligned start, by pointer arithmetic on the shared array so that
   // the compiler keeps every derived access in the shared state space
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -257,16 +259,23 @@ rk4_f32_tma(const TileArgs ta) {
     if (POT) tma_load_3d(f_buf(b, f++), &I->V, xp & ~3, yp + 1, 0, &bar[b]);
   };
 
-  // Drive phases of the four stage times t, t + dt/2, t + dt/2, t + dt
-  // (single instance; FP64 sincos on four threads, published by the barrier
-  // that opens the first tile).
-  if (DRV && tid < 4) {
-    const double ts = ta.clock->t[ta.parity] +
-                      (tid == 0 ? 0.0 : (tid == 3 ? ta.inst[0].dt64 : 0.5 * ta.inst[0].dt64));
+  // Drive phases of the four stage times t, t + dt/2, t + dt/2, t + dt of an
+  // instance (FP64 sincos on threads 0..3) into set `slot`.  A single
+  // instance computes them once, published by the barrier that opens the
+  // first tile; a batch computes those of the CTA's next tile while the
+  // current one runs, published by the barrier that opens the next tile.
+  auto drive_phases = [&](int inst, int slot) {
+    const double t0 = ONE ? ta.clock->t[ta.parity] : ta.t_inst[ta.parity * ta.ninst + inst];
+    const double dt64 = ta.inst[inst].dt64;
+    const double ts = t0 + (tid == 0 ? 0.0 : (tid == 3 ? dt64 : 0.5 * dt64));
     double sn, cs;
-    sincos(ta.inst[0].omega * ts, &sn, &cs);
-    const float ih = ONE ? ta.one.k.inv_hbar : ta.inst[0].k.inv_hbar;
-    s_dph[tid] = f2((float)cs * ih, (float)(-sn) * ih);
+    sincos(ta.inst[inst].omega * ts, &sn, &cs);
+    const float ih = ONE ? ta.one.k.inv_hbar : ta.inst[inst].k.inv_hbar;
+    s_dph[slot][tid] = f2((float)cs * ih, (float)(-sn) * ih);
+  };
+  if (DRV && tid < 4) {
+    if (ONE) drive_phases(0, 0);
+    else if ((int)blockIdx.x < ta.ntiles) drive_phases(coord_of(blockIdx.x).inst, 0);
   }
 
   // FP64 simulated time: instance 0 in the clock, all instances in t_inst
@@ -429,6 +438,8 @@ rk4_f32_tma(const TileArgs ta) {
       }
       return;
     }
+    if (DRV && !ONE && tid < 4 && t + (int)gridDim.x < ta.ntiles)
+      drive_phases(coord_of(t + (int)gridDim.x).inst, (k + 1) & 1);
     // refill the buffer the previous tile used
     if (MS) {
       if (warp == 0 && t + G < nitems) {
@@ -521,7 +532,7 @@ rk4_f32_tma(const TileArgs ta) {
       const float w = (s == 0 || s == 3) ? 1.f : 2.f;
       const float cs = (s == 2) ? dt : 0.5f * dt;
       const float2 w2 = f2(w, w), cs2 = f2(cs, cs);
-      const float2 dph = DRV ? s_dph[s] : f2(0.f, 0.f);
+      const float2 dph = DRV ? s_dph[ONE ? 0 : (k & 1)][s] : f2(0.f, 0.f);
       // neighbours of the micro-tile
       const float4 tv = *reinterpret_cast<const float4*>(&src[(r0)*C::PW + c0 + 2]);
       const float4 bv = *reinterpret_cast<const float4*>(&src[(r0 + MR + 1) * C::PW + c0 + 2]);
@@ -803,8 +814,7 @@ constexpr bool has_mode3() {
   return MINB == 1 && Cfg<3, true, MR, WY, MINB>::SMEM <= 227 * 1024;
 }
 
-// All model variants of one tile configuration (mode as in Cfg; the drive
-// variants exist for single instances only).
+// All model variants of one tile configuration (mode as in Cfg).
 template <int MR, int WY, int MINB>
 cudaError_t launch_variants(int mode, bool pot, bool per, bool one, const TileArgs& ta,
                             cudaStream_t s, int grid) {
@@ -831,7 +841,16 @@ cudaError_t launch_variants(int mode, bool pot, bool per, bool one, const TileAr
     }
     PHX_TMA_V(0, true)
   }
-  if (mode >= 2) return cudaErrorInvalidValue;
+  if (mode == 3) {
+    if constexpr (has_mode3<MR, WY, MINB>()) {
+      PHX_TMA_V(3, false)
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
+  if (mode == 2) {
+    PHX_TMA_V(2, false)
+  }
   if (mode == 1) {
     PHX_TMA_V(1, false)
   }

@@ -133,3 +133,79 @@ def test_batch_validation():
     with pytest.raises(m.PhxError) as e:
         m.phx_batch_create([m.params_from_dict(dict(d, nx=4))])
     assert e.value.status == 1
+
+
+def drive_plane(nx, ny, seed, amp=0.4):
+    rng = np.random.default_rng(seed)
+    y = np.arange(ny)[:, None] / ny
+    x = np.arange(nx)[None, :] / nx
+    a, b2, ph = rng.uniform(1, 3, 3)
+    return (amp * (np.cos(2 * np.pi * a * x + ph) + 0.5j * np.sin(2 * np.pi * b2 * y))
+            ).astype(np.complex64)
+
+
+def driven_members(reservoir, sizes=SIZES, bc=(0, 0)):
+    """Members with their own drive frequencies; member 2 has no drive."""
+    ms = members(sizes, reservoir, bc=bc)
+    E = {}
+    for k, (d, *_) in enumerate(ms):
+        d["drive_omega"] = 0.5 + 0.3 * k
+        if k != 2:
+            E[k] = drive_plane(d["nx"], d["ny"], 70 + k)
+    return ms, E
+
+
+@pytest.mark.parametrize("tile", [0, 3, 4])
+@pytest.mark.parametrize("reservoir", [True, False])
+def test_batch_drive_members_match_oracle(tile, reservoir):
+    """Coherent drive E_i(r) exp(-i omega_i t_i) per member (Eq. PULSE_psi)
+    in the batched persistent kernel: each member's own frequency and FP64
+    time, a member without drive among driven ones, graph and single-launch
+    steps (23 = one replay of 20 + 3)."""
+    m = phx()
+    ms, E = driven_members(reservoir)
+    b = make_batch(ms, tile=tile)
+    for i, Ei in E.items():
+        m.phx_batch_set_drive(b, i, Ei)
+    m.phx_batch_step_n(b, 23)
+    if reservoir:
+        assert m.phx_batch_tile(b) in (2, 3, 4)
+    for i, (d, psi0, n0, P) in enumerate(ms):
+        g_psi, g_n = member_state(b, i, d)
+        o_psi, o_n = gp.run(psi0, n0, P, None, gp.Params(**d), 23,
+                            E=E[i].astype(np.complex128) if i in E else None)
+        assert rel_l2(g_psi, o_psi) <= 1e-4, (i, rel_l2(g_psi, o_psi))
+        if reservoir:
+            assert rel_l2(g_n, o_n) <= 1e-4, (i, rel_l2(g_n, o_n))
+
+
+def test_batch_drive_equals_single_handles():
+    """Batch members with a drive against driven single handles (zero x
+    boundary, reservoir), and a member whose drive is set and then removed
+    against an undriven handle."""
+    m = phx()
+    ms, E = driven_members(True, SIZES[:4], bc=(1, 0))
+    b = make_batch(ms)
+    for i, Ei in E.items():
+        m.phx_batch_set_drive(b, i, Ei)
+    m.phx_batch_set_drive(b, 3, None)
+    m.phx_batch_step_n(b, 31)
+    for i, (d, psi0, n0, P) in enumerate(ms):
+        h = make_handle(d, 32, psi0, n0, P)
+        if i in E and i != 3:
+            m.phx_set_drive(h, E[i])
+        m.phx_step_n(h, 31)
+        s_psi, s_n = get_state(h, 32)
+        g_psi, g_n = member_state(b, i, d)
+        assert rel_l2(g_psi, s_psi) <= 1e-6, (i, rel_l2(g_psi, s_psi))
+        assert rel_l2(g_n, s_n) <= 1e-6
+
+
+def test_batch_drive_fixed_tile_without_variant():
+    m = phx()
+    ms, E = driven_members(True, SIZES[:2])
+    b = make_batch(ms, tile=7)
+    m.phx_batch_set_drive(b, 0, E[0])
+    with pytest.raises(m.PhxError) as e:
+        m.phx_batch_step_n(b, 2)
+    assert e.value.status == 1
