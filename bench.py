@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--workload", default="reservoir_2048",
                     choices=["reservoir_2048", "reservoir_1024", "reservoir", "spinor_2048",
                              "conservative_64", "ensemble", "twa_ensemble", "driven_9000",
-                             "steady_256", "fno_train"])
+                             "drive_sweep", "steady_256", "fno_train"])
     ap.add_argument("--grid", type=int, default=1024,
                     help="grid size of the 'reservoir' workload (100 um box, config-2 physics)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -425,6 +425,10 @@ def run_reference(args, world, rank):
         import synth
         cfg = synth.crop(workload("driven_9000")[0], 512)
         desc = "512x512 corner window of the driven 9000x9000 lattice"
+    elif args.workload == "drive_sweep":
+        import synth
+        cfg = synth.drive_sweep(count=1)[0]
+        desc = "one 512x512 member of the drive-frequency sweep"
     else:
         cfg, kind, desc = workload(args.workload, grid=args.grid)
     d = cfg["params"]
@@ -464,7 +468,10 @@ def run_ensemble(args, world, rank, local, pg):
     twa_ensemble: 150 truncated-Wigner realisations (256^2, 200 um,
     super-Gaussian pump w = 65 um at 2 P_thr, nu = 1, Wigner vacuum start);
     per step 10 samples, each 5 ps of RK4 steps followed by the per-member
-    FP64 norm/energy read back to the host (the sampled observable)."""
+    FP64 norm/energy read back to the host (the sampled observable).
+    drive_sweep: 64 coherently driven scalar fields (512^2, 100 um, loss and
+    Kerr, no reservoir), one drive spot at 64 frequencies; per step 500 RK4
+    steps, then per-member FP64 norm/energy and residual."""
     import torch
     import synth
     import paper_2411_18341_gb300 as phx
@@ -473,11 +480,17 @@ def run_ensemble(args, world, rank, local, pg):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     twa = args.workload == "twa_ensemble"
+    sweep = args.workload == "drive_sweep"
+    res = not sweep  # members with a reservoir
     if twa:
         members = synth.twa_ensemble(seed=7 + rank)
         dt = members[0]["params"]["dt"]
         per_sample = args.rk4_steps or int(round(TWA_SAMPLE_PS / dt))
         samples = TWA_SAMPLES
+    elif sweep:
+        members = synth.drive_sweep(seed0=3000 + 10000 * rank)
+        per_sample = args.rk4_steps or 500
+        samples = 1
     else:
         members = synth.ensemble(seed0=1000 + 10000 * rank)
         per_sample = args.rk4_steps or 500
@@ -487,14 +500,19 @@ def run_ensemble(args, world, rank, local, pg):
     b = phx.phx_batch_create([phx.params_from_dict(m["params"], precision=32,
                                                    stream=stream.cuda_stream) for m in members])
     psi_d, n_d = [], []
-    P_d = [torch.tensor(m["P"][0], dtype=torch.float32, device=dev) for m in members]
+    P_d = [torch.tensor(m["P"][0], dtype=torch.float32, device=dev) for m in members] if res else []
+    E_d = [torch.tensor(m["E"][0], dtype=torch.complex64, device=dev) for m in members] \
+        if sweep else []
     # the copies run on torch's stream; the batch reads them on its own
     torch.cuda.synchronize()
     for i, m in enumerate(members):
-        phx.phx_batch_set_pump(b, i, P_d[i])
+        if res:
+            phx.phx_batch_set_pump(b, i, P_d[i])
+        if sweep:
+            phx.phx_batch_set_drive(b, i, E_d[i])
         psi_d.append(torch.tensor(m["psi0"][0], dtype=torch.complex64, device=dev))
-        n_d.append(torch.tensor(m["n0"][0], dtype=torch.float32, device=dev))
-    del P_d
+        n_d.append(torch.tensor(m["n0"][0], dtype=torch.float32, device=dev) if res else None)
+    del P_d, E_d
     sites = sum(m["params"]["nx"] * m["params"]["ny"] for m in members)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -546,15 +564,21 @@ def run_ensemble(args, world, rank, local, pg):
 
     # end to end: pinned host inputs in, every member's state out
     psi_h = [t.cpu().pin_memory() for t in psi_d]
-    n_h = [t.cpu().pin_memory() for t in n_d]
-    P_h = [torch.tensor(m["P"][0], dtype=torch.float32).pin_memory() for m in members]
+    n_h = [t.cpu().pin_memory() if t is not None else None for t in n_d]
+    P_h = [torch.tensor(m["P"][0], dtype=torch.float32).pin_memory() for m in members] \
+        if res else []
+    E_h = [torch.tensor(m["E"][0], dtype=torch.complex64).pin_memory() for m in members] \
+        if sweep else []
     out_psi = [torch.empty_like(t).pin_memory() for t in psi_h]
-    out_n = [torch.empty_like(t).pin_memory() for t in n_h]
+    out_n = [torch.empty_like(t).pin_memory() if t is not None else None for t in n_h]
     torch.cuda.synchronize()
     barrier(pg)
     t0 = time.perf_counter()
     for i in range(len(members)):
-        phx.phx_batch_set_pump(b, i, P_h[i])
+        if res:
+            phx.phx_batch_set_pump(b, i, P_h[i])
+        if sweep:
+            phx.phx_batch_set_drive(b, i, E_h[i])
         phx.phx_batch_set_state(b, i, psi_h[i], n_h[i])
     if twa:
         for k in range(samples):
@@ -584,8 +608,15 @@ def run_ensemble(args, world, rank, local, pg):
         prec_err.append(e)
         del psi32, n32, psi64, n64
     pk, pk_kind = peaks()
-    achieved = 28 * sites / kern_s / 1e9
-    if twa:
+    bps = 24 if sweep else 28  # psi in/out + (n in/out, P) or (Re E, Im E)
+    achieved = bps * sites / kern_s / 1e9
+    if sweep:
+        desc = ("64 coherently driven scalar fields, 512^2, 100 um periodic, loss 0.15 /ps, "
+                "g = 6e-3 meV um^2, one Gaussian drive spot (0.05 meV, w = 20 um) at 64 "
+                "frequencies in [-1, 2] /ps, each member its own frequency and FP64 time")
+        per_step = ("set_state x64 + %d batched RK4 steps + per-member FP64 norm/energy + "
+                    "residual" % rk4_steps)
+    elif twa:
         desc = ("150 truncated-Wigner realisations (nu = 1), 256^2, 200 um periodic, "
                 "super-Gaussian pump w = 65 um at 2 P_thr, Wigner vacuum start")
         per_step = ("set_state x150 + %d samples, each %d batched RK4 steps (%.2f ps) + "
@@ -604,16 +635,17 @@ def run_ensemble(args, world, rank, local, pg):
         "config": {"workload": args.workload, "description": desc,
                    "sites": sites, "rk4_steps_per_step": rk4_steps, "tile": phx.phx_batch_tile(b),
                    "per_step": per_step,
-                   "l2": "inputs (%.2f GB) larger than L2" % (28 * sites / 1e9),
+                   "l2": "inputs (%.2f GB) larger than L2" % (bps * sites / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": world * sites * rk4_steps / e2e_s, "unit": "site-updates/s",
-                "h2d_bytes_per_step": sites * 16, "d2h_bytes_per_step": sites * 12},
+                "h2d_bytes_per_step": sites * 16,
+                "d2h_bytes_per_step": sites * (8 if sweep else 12)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
                      "traffic": recorded_traffic(args.workload, 32, phx.phx_batch_tile(b)),
                      "kernel": step_kernel_name(phx.phx_batch_tile(b)) + ", all members per launch",
-                     "algorithmic_bytes_per_site": 28, "avg_launch_us": kern_s * 1e6,
+                     "algorithmic_bytes_per_site": bps, "avg_launch_us": kern_s * 1e6,
                      "peak_source": pk_kind,
                      **({"note": "per-site Philox + Box-Muller noise every step: the kernel is "
                                  "bound by instruction issue, not by HBM"} if twa else {})},
@@ -929,7 +961,7 @@ def main():
         if pg is not None:
             pg.destroy_process_group()
         return
-    if args.workload in ("ensemble", "twa_ensemble"):
+    if args.workload in ("ensemble", "twa_ensemble", "drive_sweep"):
         run_ensemble(args, world, rank, local, pg)
         if pg is not None:
             pg.destroy_process_group()

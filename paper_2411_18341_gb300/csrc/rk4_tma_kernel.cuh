@@ -268,10 +268,22 @@ rk4_f32_tma(const TileArgs ta) {
     const double t0 = ONE ? ta.clock->t[ta.parity] : ta.t_inst[ta.parity * ta.ninst + inst];
     const double dt64 = ta.inst[inst].dt64;
     const double ts = t0 + (tid == 0 ? 0.0 : (tid == 3 ? dt64 : 0.5 * dt64));
-    double sn, cs;
-    sincos(ta.inst[inst].omega * ts, &sn, &cs);
     const float ih = ONE ? ta.one.k.inv_hbar : ta.inst[inst].k.inv_hbar;
-    s_dph[slot][tid] = f2((float)cs * ih, (float)(-sn) * ih);
+    if (ONE) {
+      double sn, cs;
+      sincos(ta.inst[inst].omega * ts, &sn, &cs);
+      s_dph[slot][tid] = f2((float)cs * ih, (float)(-sn) * ih);
+    } else {
+      // once per tile on the critical path of warp 0: the angle is reduced
+      // to [-pi, pi] in FP64 (few operations on the narrow FP64 pipe) and
+      // its sine and cosine taken in FP32 (error ~1e-7, the stencil's own
+      // precision)
+      const double a = ta.inst[inst].omega * ts;
+      const double r = fma(-rint(a * 0.15915494309189535), 6.283185307179586, a);
+      float sn, cs;
+      sincosf((float)r, &sn, &cs);
+      s_dph[slot][tid] = f2(cs * ih, -sn * ih);
+    }
   };
   if (DRV && tid < 4) {
     if (ONE) drive_phases(0, 0);

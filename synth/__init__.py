@@ -21,6 +21,8 @@ files are not available, so these stand in for them):
 * ``ensemble``         -- 256 reservoir instances, 64 each at 128^2 .. 1024^2,
   100 um, ring pumps at U[0.8, 3] P_thr.
 * ``steady_256``       -- 256x256, 128 um, sums of 1-4 Gaussian pumps.
+* ``drive_sweep``      -- 64 coherently driven scalar fields, 512x512, 100 um,
+  the same drive spot at 64 frequencies (one batch).
 """
 import json
 import os
@@ -231,6 +233,28 @@ def driven_lattice(n=9000, dx=0.1, seed=11, wells=272, a1=2.8, a2=3.8, depth=4.0
     psi0 = complex_normal((1, n, n), 1e-3, seed).astype(np.complex64)
     return dict(name="driven_%d" % n, params=p, psi0=psi0, n0=None, P=None, V=V, E=E,
                 steps=None)
+
+
+def drive_sweep(count=64, n=512, length=100.0, seed0=3000, omega_lo=-1.0, omega_hi=2.0,
+                e0=0.05, spot=20.0):
+    """Drive-frequency sweep of a coherently driven scalar field (the scan
+    that maps a driven condensate's response against detuning): `count`
+    members on n x n grids over `length` um, periodic, Kerr g = 6e-3 meV um^2,
+    loss gamma_c = 0.15 ps^-1, no reservoir; member i is driven by the same
+    Gaussian spot (amplitude e0 meV, waist `spot` um, centred) at frequency
+    omega_i, evenly spaced over [omega_lo, omega_hi] ps^-1; psi0 = complex
+    normal noise of std 1e-3, seed seed0 + i."""
+    c = load_constants()
+    E = gaussian(n, n, length, length, e0, spot).astype(np.complex64)[None]
+    out = []
+    for i, om in enumerate(np.linspace(omega_lo, omega_hi, count)):
+        p = base_params(n, n, length, length, g=G_C, gamma_c=GAMMA_C,
+                        dt=c["drive_%d_L%g" % (n, length)]["dt"], drive_omega=float(om),
+                        seed=seed0 + i, instance=i)
+        psi0 = complex_normal((1, n, n), 1e-3, seed0 + i).astype(np.complex64)
+        out.append(dict(name="sweep_%d" % i, params=p, psi0=psi0, n0=None, P=None, V=None,
+                        E=E, steps=None))
+    return out
 
 
 def crop(cfg, m):

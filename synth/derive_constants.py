@@ -47,6 +47,9 @@ def main():
     # driven lattice: 9000^2 cells of 0.1 um, scalar with loss and g
     out["driven_9000_L900"] = {"dt": half_limit(nx=9000, ny=9000, lx=900.0, ly=900.0,
                                                 kappa=KAPPA, g=6e-3, gamma_c=0.15)}
+    # drive-frequency sweep: 512^2 over 100 um, scalar with loss and g
+    out["drive_512_L100"] = {"dt": half_limit(nx=512, ny=512, lx=100.0, ly=100.0,
+                                              kappa=KAPPA, g=6e-3, gamma_c=0.15)}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
                         "constants.json")
     with open(path, "w") as f:

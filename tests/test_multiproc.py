@@ -75,7 +75,7 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert rec["e2e"]["h2d_bytes_per_step"] == 0
 
 
-@pytest.mark.parametrize("workload", ["ensemble", "twa_ensemble"])
+@pytest.mark.parametrize("workload", ["ensemble", "twa_ensemble", "drive_sweep"])
 def test_reference_arm_for_batched_workloads(workload):
     """The reference arm (the oracle, timed on the host) runs on a bounded
     sample of each batched workload and prints the contract's JSON line."""
