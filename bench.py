@@ -797,11 +797,15 @@ def steady_experiment(n_train=2000, n_test=200, gen_steps=40000, epochs=40, cap=
     return rep, net
 
 
-def quick_rate(phx, torch, name, steps=500, warmup=50):
+def quick_rate(phx, torch, name, steps=500, warmup=50, drive=None):
     """Site-updates/s of one workload's step kernel (CUDA events around
-    `steps` steps after `warmup`), for an extra key of the default line."""
+    `steps` steps after `warmup`), for an extra key of the default line.
+    drive: (E plane, omega) added to the workload (a coherent drive on top
+    of its own terms)."""
     cfg, kind, desc = workload(name)
-    d = cfg["params"]
+    d = dict(cfg["params"])
+    if drive is not None:
+        d["drive_omega"] = drive[1]
     stream = torch.cuda.Stream()
     h = phx.phx_create(phx.params_from_dict(d, precision=32, stream=stream.cuda_stream))
     real, cplx = torch.float32, torch.complex64
@@ -812,6 +816,8 @@ def quick_rate(phx, torch, name, steps=500, warmup=50):
     torch.cuda.synchronize()  # the handle reads the copies on its own stream
     if P is not None:
         phx.phx_set_pump(h, P)
+    if drive is not None:
+        phx.phx_set_drive(h, np.ascontiguousarray(drive[0], np.complex64))
     phx.phx_set_state(h, psi0, n0)
     phx.phx_step_n(h, warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -823,7 +829,9 @@ def quick_rate(phx, torch, name, steps=500, warmup=50):
     us = e0.elapsed_time(e1) * 1e3 / steps
     sites = d["nx"] * d["ny"]
     pk, _ = peaks()
-    bps = BYTES_PER_SITE[(32, kind)]
+    bps = BYTES_PER_SITE[(32, kind)] + (8 if drive is not None else 0)
+    if drive is not None:
+        desc += "; plus a coherent drive (plane wave, 0.05 meV, omega = %g /ps)" % drive[1]
     out = {"workload": name, "description": desc, "site_updates_per_s": sites / (us * 1e-6),
            "us_per_step": us, "tile": phx.phx_tile(h),
            "roofline_frac": bps * sites / (us * 1e-6) / 1e9 / pk["hbm_gbs"],
@@ -1158,6 +1166,13 @@ def main():
     if rank == 0 and world == 1 and args.workload == "reservoir_2048":
         # the two-component TE-TM workload's step (noise every step), timed briefly
         line["spinor_2048"] = quick_rate(phx, torch, "spinor_2048")
+        # the same workload with a coherent drive on top (reservoir + drive
+        # variant of the TMA-fed kernel)
+        n = d["nx"]
+        xx = np.arange(n)[None, :] / n
+        yy = np.arange(n)[:, None] / n
+        E = (0.05 * np.exp(2j * np.pi * (3 * xx + 2 * yy))).astype(np.complex64)
+        line["drive_reservoir_2048"] = quick_rate(phx, torch, "reservoir_2048", drive=(E, -0.3))
     if rank == 0 and world == 1 and not args.no_steady and args.workload == "reservoir_2048":
         # reduced warm-vs-cold time to steady state (the metric's second part)
         rep, _ = steady_experiment(n_train=1024, n_test=128, gen_steps=30000, epochs=12,
