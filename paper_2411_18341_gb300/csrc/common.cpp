@@ -109,6 +109,7 @@ Coeffs make_coeffs(const phx_params& p) {
   k.ty = p.delta_lt / (HBAR * dy * dy);
   k.txy = p.delta_lt / (2.0 * HBAR * dx * dy);
   k.dt = p.dt;
+  k.dt6 = p.dt / 6.0;
   if (p.wigner_nu > 0.0) {
     // truncated-Wigner renormalisation |psi|^2 -> |psi|^2 - 1/dV in the Kerr,
     // cross-Kerr and depletion terms: constant shifts of the diagonal

@@ -50,6 +50,7 @@ struct CoeffsT {
   R R_, gamma_r;
   R tx, ty, txy;     // Delta/(h dx^2), Delta/(h dy^2), Delta/(2 h dx dy)
   R dt;
+  R dt6;             // dt/6 in this precision (the final RK4 combination)
 };
 using Coeffs = CoeffsT<double>;
 
@@ -63,6 +64,7 @@ inline CoeffsT<R> cast_coeffs(const Coeffs& c) {
   o.R_ = (R)c.R_; o.gamma_r = (R)c.gamma_r;
   o.tx = (R)c.tx; o.ty = (R)c.ty; o.txy = (R)c.txy;
   o.dt = (R)c.dt;
+  o.dt6 = o.dt / (R)6;  // IEEE division in R: the value a kernel would compute
   return o;
 }
 

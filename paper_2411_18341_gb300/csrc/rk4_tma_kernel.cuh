@@ -482,7 +482,7 @@ rk4_f32_tma(const TileArgs ta) {
     const float2 ncR2 = f2(-q.R_, -q.R_), ncgam2 = f2(-q.gamma_r, -q.gamma_r);
     const float2 a02 = f2(q.a0, q.a0);
     const float dt = q.dt;
-    const float dt6 = dt / 6.0f;
+    const float dt6 = q.dt6;  // dt / 6, divided once on the host
     const int xp = kx * C::TX;
     const int foff = xp & 3;
     float2* P0 = psi_buf(b);
@@ -679,9 +679,11 @@ rk4_f32_tma(const TileArgs ta) {
     const bool interior = ox0 >= HALO && ox0 + C::TX <= g.nx - HALO && oy0 >= HALO &&
                           oy0 + C::TY <= g.ny - HALO;
     if (interior) {
-      // my two columns inside the output columns [3, 3 + TX) of the region
+      // my two columns inside the output columns [3, 3 + TX) of the region:
+      // both (lanes 2..29), one (lanes 1 and 30: column `one`), or none
       const bool lo = c0 >= 3 && c0 < 3 + C::TX;
       const bool hi = c0 + 1 >= 3 && c0 + 1 < 3 + C::TX;
+      const int one = lo ? 0 : 1;
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
         const int r = r0 + j;
@@ -691,12 +693,9 @@ rk4_f32_tma(const TileArgs ta) {
           *reinterpret_cast<float4*>(psi_out + roff) =
               make_float4(o[j][0].x, o[j][0].y, o[j][1].x, o[j][1].y);
           if (RES) *reinterpret_cast<float2*>(n_out + roff) = on[j];
-        } else if (lo) {
-          psi_out[roff] = o[j][0];
-          if (RES) n_out[roff] = on[j].x;
-        } else if (hi) {
-          psi_out[roff + 1] = o[j][1];
-          if (RES) n_out[roff + 1] = on[j].y;
+        } else if (lo || hi) {  // one path for both edge lanes
+          psi_out[roff + one] = lo ? o[j][0] : o[j][1];
+          if (RES) n_out[roff + one] = lo ? on[j].x : on[j].y;
         }
       }
     } else {

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
     const float2 dg2 = f2(2.f * (q.ty - q.tx), 2.f * (q.ty - q.tx));
     const float2 m12 = f2(-1.f, -1.f);
     const float txy = q.txy;
-    const float dt6 = dt / 6.0f;
+    const float dt6 = q.dt6;  // dt / 6, divided once on the host
     const int xp = cc.kx * C::TX;
     const int foff = xp & 3;
     float2* P0 = psi_buf(b);
@@ -383,12 +383,10 @@ __global__ void __launch_bounds__(32 * WY, 1) rk4_f32_tma_spinor(const TileArgs 
             *reinterpret_cast<float4*>(po) =
                 make_float4(o[j][0][c].x, o[j][0][c].y, o[j][1][c].x, o[j][1][c].y);
             *reinterpret_cast<float2*>(pn) = on[j][c];
-          } else if (lo) {
-            po[0] = o[j][0][c];
-            pn[0] = on[j][c].x;
-          } else if (hi) {
-            po[1] = o[j][1][c];
-            pn[1] = on[j][c].y;
+          } else if (lo || hi) {  // one path for both edge lanes
+            const int one = lo ? 0 : 1;
+            po[one] = lo ? o[j][0][c] : o[j][1][c];
+            pn[one] = lo ? on[j][c].x : on[j][c].y;
           }
         }
       }
