@@ -137,6 +137,13 @@ struct Cfg {
   static constexpr int NBUF =
       (MINB == 1 && 3 * BUF_BYTES + PSI_BYTES + 128 <= 227 * 1024) ? 3 : 2;
   static constexpr int SMEM = NBUF * BUF_BYTES + PSI_BYTES + 128;
+  // A second stage-exchange buffer, where shared memory allows it (per CTA,
+  // and for the CTAs that share an SM): consecutive tiles of a CTA then use
+  // different exchange buffers, which lets the kernel drop the barrier at a
+  // tile's start (see the kernel).
+  static constexpr int SMEM_YY = SMEM + PSI_BYTES;
+  static constexpr bool YY_FITS =
+      SMEM_YY <= 227 * 1024 && MINB * (SMEM_YY + 1024) <= 228 * 1024;
 };
 
 // PER: both axes periodic (every ring cell holds a periodic image, so no
@@ -171,6 +178,13 @@ rk4_f32_tma(const TileArgs ta) {
   constexpr bool RES = MODE == 1 || MODE == 3, DRV = MODE == 2 || MODE == 3;
   using C = Cfg<MODE, POT, MR, WY, MINB>;
   static_assert(!MS || (ONE && !DRV && C::NBUF == 2), "multi-step: single instance, no drive");
+  // YY: two stage-exchange buffers, alternating between consecutive tiles.
+  // Then no barrier opens a tile: the first stage barrier also carries the
+  // bounded waits' failure vote, and a tile's input buffer is refilled (with
+  // the tile NBUF positions later) right after its last stage barrier, the
+  // last point that reads it; warps that finish a tile's stores go on to the
+  // next tile while others still store.
+  constexpr bool YY = !MS && C::YY_FITS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[3];
   // drive phase exp(-i omega t_s) / hbar per stage: one set for a single
@@ -179,7 +193,8 @@ rk4_f32_tma(const TileArgs ta) {
   // 128-byte aligned start, by pointer arithmetic on the shared array so that
   // the compiler keeps every derived access in the shared state space
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  float2* Y = reinterpret_cast<float2*>(base + C::NBUF * C::BUF_BYTES);
+  float2* const Ybase = reinterpret_cast<float2*>(base + C::NBUF * C::BUF_BYTES);
+  constexpr int Y_STRIDE = C::PSI_BYTES / 8;  // float2 elements per exchange buffer
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c0 = 2 * lane;   // region column of the micro-tile's first column
@@ -190,10 +205,12 @@ rk4_f32_tma(const TileArgs ta) {
   };
 
   // Y ring cells are never written by the stages: give them a defined value.
-  for (int i = tid; i < C::PH * C::PW; i += C::NT) {
-    int r = i / C::PW, c = i - r * C::PW;
-    if (r == 0 || r == C::PH - 1 || c < 2 || c >= C::RW + 2) Y[i] = f2(0.f, 0.f);
-  }
+  for (int yb = 0; yb < (YY ? 2 : 1); ++yb)
+    for (int i = tid; i < C::PH * C::PW; i += C::NT) {
+      int r = i / C::PW, c = i - r * C::PW;
+      if (r == 0 || r == C::PH - 1 || c < 2 || c >= C::RW + 2)
+        Ybase[yb * Y_STRIDE + i] = f2(0.f, 0.f);
+    }
   if (tid == 0) {
     for (int b = 0; b < C::NBUF; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
@@ -401,8 +418,8 @@ rk4_f32_tma(const TileArgs ta) {
         else ms_issue_pending();
       }
     }
-  } else if (tid == 0) {  // prologue: the first NBUF-1 tiles
-    for (int i = 0; i < C::NBUF - 1; ++i) {
+  } else if (tid == 0) {  // prologue: the first NBUF-1 tiles (NBUF with YY)
+    for (int i = 0; i < C::NBUF - (YY ? 0 : 1); ++i) {
       const int ti = t + i * (int)gridDim.x;
       if (ti < ta.ntiles && !(i == 0 && ta.inject_timeout)) issue(cn, i, ta.cur);
       advance(cn, ti + (int)gridDim.x);
@@ -437,23 +454,32 @@ rk4_f32_tma(const TileArgs ta) {
       }
     }
     // every thread waits on the barrier (bounded); the CTA leaves together
-    // if any thread gave up, after waiting (bounded) for its other loads.
-    // This barrier also closes the previous tile: every thread has finished
-    // reading its buffers and the shared stage buffer Y.
+    // if any thread gave up, after waiting (bounded) for its other loads:
+    // those of the next NBUF-2 tiles (NBUF-1 with YY, whose vote is taken at
+    // the first stage barrier).
     const int fail = dep_fail || !mbar_wait_bounded(&bar[b], par);
-    if (__syncthreads_or(fail)) {
+    auto leave = [&]() {
       if (tid == 0) {
         atomicExch(ta.err, 1);
-        for (int j = k + 1; j < k + C::NBUF - 1; ++j)
+        for (int j = k + 1; j < k + C::NBUF - (YY ? 0 : 1); ++j)
           if (t + (j - k) * (int)gridDim.x < ta.ntiles)
             mbar_wait_bounded(&bar[j % C::NBUF], (uint32_t)((j / C::NBUF) & 1));
       }
-      return;
+    };
+    if (!YY) {
+      // This barrier also closes the previous tile: every thread has
+      // finished reading its buffers and the shared stage buffer Y.
+      if (__syncthreads_or(fail)) {
+        leave();
+        return;
+      }
+      if (DRV && !ONE && tid < 4 && t + (int)gridDim.x < ta.ntiles)
+        drive_phases(coord_of(t + (int)gridDim.x).inst, (k + 1) & 1);
     }
-    if (DRV && !ONE && tid < 4 && t + (int)gridDim.x < ta.ntiles)
-      drive_phases(coord_of(t + (int)gridDim.x).inst, (k + 1) & 1);
-    // refill the buffer the previous tile used
-    if (MS) {
+    // refill the buffer the previous tile used (YY: after this tile's last
+    // stage barrier)
+    if (YY) {
+    } else if (MS) {
       if (warp == 0 && t + G < nitems) {
         set_pend(t + G);
         if (t + G < ta.ntiles) ms_issue_pending();  // step 0 reads the launch's input
@@ -539,6 +565,7 @@ rk4_f32_tma(const TileArgs ta) {
 
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
+      float2* const Y = Ybase + (YY ? (k & 1) * Y_STRIDE : 0);
       const float2* src = (s & 1) ? Y : P0;
       float2* dst = (s & 1) ? P0 : Y;
       const float w = (s == 0 || s == 3) ? 1.f : 2.f;
@@ -624,7 +651,30 @@ rk4_f32_tma(const TileArgs ta) {
             *reinterpret_cast<float4*>(&dst[(r0 + j + 1) * C::PW + c0 + 2]) =
                 make_float4(ny[j][0].x, ny[j][0].y, ny[j][1].x, ny[j][1].y);
         }
-        __syncthreads();  // the last stage reads but writes no shared memory
+        // the last stage reads but writes no shared memory
+        if (YY && s == 0) {
+          // every thread is past the previous tile (whose last stage read
+          // the other exchange buffer); the failure vote of this tile's wait
+          if (__syncthreads_or(fail)) {
+            leave();
+            return;
+          }
+          // the next tile's drive phases (read after this tile's next barrier)
+          if (DRV && !ONE && tid < 4 && t + (int)gridDim.x < ta.ntiles)
+            drive_phases(coord_of(t + (int)gridDim.x).inst, (k + 1) & 1);
+        } else {
+          __syncthreads();
+        }
+        if (YY && s == 2 && tid == 0) {
+          // stage 3 reads only Y and registers: this tile's input buffer is
+          // free for the tile NBUF positions later
+          const int tY = t + C::NBUF * (int)gridDim.x;
+          if (tY < ta.ntiles) {
+            fence_proxy_async();  // its generic accesses before the async-proxy write
+            issue(cn, b, ta.cur);
+            advance(cn, tY + (int)gridDim.x);
+          }
+        }
         if (MS && warp == 0) ms_point(s == 0, t);
       }
     }
@@ -741,19 +791,20 @@ template <int MODE, bool POT, bool PER, bool ONE, int MR, int WY, int MINB>
 cudaError_t launch_cfg(const TileArgs& ta, cudaStream_t s, int grid) {
   using C = Cfg<MODE, POT, MR, WY, MINB>;
   auto kern = rk4_f32_tma<MODE, POT, PER, ONE, MR, WY, MINB>;
+  constexpr int SMEM = C::YY_FITS ? C::SMEM_YY : C::SMEM;
   static int configured_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured_dev != dev) {
     cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e != cudaSuccess) return e;
     configured_dev = dev;
   }
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(grid);
   lc.blockDim = dim3(C::NT);
-  lc.dynamicSmemBytes = C::SMEM;
+  lc.dynamicSmemBytes = SMEM;
   lc.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
